@@ -1,0 +1,206 @@
+"""Pins of the oracle's bead-spring chain and its dissipative coupling to the fluid
+(Sec. II A Eqs. 1-2; Sec. II B last paragraph; Sec. II D Eq. 7)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lbchain as o
+from paper_0903_5067_gb300 import inputs
+
+
+def _chain_params(**kw):
+    base = dict(N=6, m=1.0, zeta=20.8, k_fene=30.0, R0=1.5, eps=1.0, sigma=1.0)
+    base.update(kw)
+    return o.ChainParams(**base)
+
+
+def test_forces_are_minus_gradient_of_fene_plus_wca():
+    cp = _chain_params()
+    box = 10.0
+    # a folded chain: bonds between 0.9 and 1.3, non-bonded pairs (1,4) and (0,5) inside the
+    # WCA range, plus one pair across the periodic boundary
+    X = np.array([[9.6, 5.0, 5.0], [0.5, 5.1, 5.0], [1.3, 5.8, 5.2], [1.0, 6.6, 5.9],
+                  [0.3, 5.9, 5.4], [9.4, 5.9, 5.3]])
+    d = np.linalg.norm(o.min_image(X[:, None] - X[None], box), axis=-1)
+    assert d[1, 4] < 2 ** (1 / 6) and d[0, 5] < 2 ** (1 / 6)
+    assert all(d[i, i + 1] < cp.R0 for i in range(5))
+    F = o.chain_forces(X, cp, box)
+    h = 1e-5
+    for b in range(6):
+        for al in range(3):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[b, al] += h
+            Xm[b, al] -= h
+            fd = -(o.chain_energy(Xp, cp, box) - o.chain_energy(Xm, cp, box)) / (2 * h)
+            assert F[b, al] == pytest.approx(fd, rel=1e-6, abs=1e-6)
+    assert np.allclose(F.sum(axis=0), 0.0, atol=1e-10)  # pairwise: Newton's third law
+
+
+def test_wca_is_cut_and_shifted_at_two_to_the_sixth():
+    rc = 2 ** (1 / 6)
+    assert float(o.v_wca(np.array(rc), 1.0, 1.0)) == pytest.approx(0.0, abs=1e-15)
+    assert float(o.v_wca(np.array(rc * 1.0001), 1.0, 1.0)) == 0.0
+    assert float(o.v_wca(np.array(1.0), 1.0, 1.0)) == pytest.approx(1.0)  # 4(1 - 1 + 1/4)
+    cp = _chain_params(N=3)
+    X = np.array([[0.0, 0, 0], [0.97, 0, 0], [rc + 0.2, 0.9, 0]])
+    F1 = o.chain_forces(X, cp, 50.0)
+    X2 = X.copy()
+    X2[2] = [0.97 + rc + 1e-9, 0, 0]  # bead 2 just outside the WCA range of bead 1 along x
+    cpn = _chain_params(N=2)
+    assert np.allclose(o.chain_forces(X2[:2], cpn, 50.0), o.chain_forces(X[:2], cpn, 50.0))
+    assert np.all(np.isfinite(F1))
+
+
+def test_fene_beyond_max_extension_is_an_error():
+    cp = _chain_params(N=2)
+    with pytest.raises(o.FeneBroken):
+        o.chain_forces(np.array([[0.0, 0, 0], [1.5, 0, 0]]), cp, 20.0)
+
+
+def test_minimum_image_for_pairs_across_the_box():
+    cp = _chain_params(N=2)
+    L = 8.0
+    a = np.array([[0.2, 4.0, 4.0], [L - 0.6, 4.0, 4.0]])  # 0.8 apart through the boundary
+    b = np.array([[4.2, 4.0, 4.0], [3.4, 4.0, 4.0]])
+    assert np.allclose(o.chain_forces(a, cp, L), o.chain_forces(b, cp, L))
+
+
+def test_trilinear_interpolation_reproduces_linear_fields():
+    fp = o.FluidParams(L=12, a=0.5)
+    L = fp.L
+    zz, yy, xx = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    G = np.array([[0.3, -1.1, 0.7], [2.0, 0.1, -0.4], [-0.5, 0.9, 1.3]])
+    c = np.array([0.1, -0.2, 0.3])
+    pos = np.stack([xx, yy, zz]) * fp.a  # node positions (3, z, y, x)
+    field = c[:, None, None, None] + np.einsum("ab,bzyx->azyx", G, pos)
+    rng = np.random.default_rng(0)
+    X = fp.a * (2 + (L - 5) * rng.random((20, 3)))
+    got = o.interp_field(field, X, fp)
+    assert np.allclose(got, c[None] + X @ G.T, rtol=1e-12, atol=1e-12)
+    # a bead exactly on a node sees exactly that node's value
+    node = np.array([[3 * fp.a, 7 * fp.a, 5 * fp.a]])
+    assert np.array_equal(o.interp_field(field, node, fp)[0], field[:, 5, 7, 3])
+
+
+def test_spreading_is_minus_the_transpose_of_interpolation():
+    """Momentum given to the fluid equals minus the momentum taken from the beads, with the
+    same weights: sum_r f(r).u(r) a^3 = -sum_b F_b.u(x_b) for any field u."""
+    fp = o.FluidParams(L=7, a=1.3)
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal((3, 7, 7, 7))
+    X = rng.random((9, 3)) * 30 - 10  # unwrapped, outside the primary box too
+    Fc = rng.standard_normal((9, 3))
+    f = o.spread(Fc, X, fp)
+    lhs = (f * u).sum() * fp.a ** 3
+    rhs = -(Fc * o.interp_field(u, X, fp)).sum()
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+    assert np.allclose(f.reshape(3, -1).sum(axis=1) * fp.a ** 3, -Fc.sum(axis=0), atol=1e-12)
+
+
+def test_bead_velocity_variance_in_frozen_fluid_is_exactly_kT_over_m():
+    """Velocity-Verlet Langevin with friction at the half-step velocity: for u = 0 the
+    stationary variance of v is kT/m exactly and that of v_half kT/(m (1 - alpha)),
+    alpha = h zeta / 2m (fluctuation-dissipation, Sec. II B)."""
+    nb = 2000
+    fp = o.FluidParams(L=4, kT=1.3, h=0.01, seed=5)
+    cp = _chain_params(N=nb, m=1.7, zeta=20.8)
+    X = np.zeros((nb, 3))
+    V = np.zeros((nb, 3))
+    F = np.zeros((nb, 3))
+    vs, vhs = [], []
+    for k in range(400):
+        X, Vh = o.bead_kick_drift(X, V, F, cp, fp.h)
+        F = o.coupling_force(Vh, np.zeros_like(Vh), cp, fp, k)
+        V = o.bead_kick(Vh, F, cp, fp.h)
+        if k >= 60:
+            vs.append(V.copy())
+            vhs.append(Vh.copy())
+    alpha = fp.h * cp.zeta / (2 * cp.m)
+    assert np.var(vs) == pytest.approx(fp.kT / cp.m, rel=0.015)
+    assert np.var(vhs) == pytest.approx(fp.kT / (cp.m * (1 - alpha)), rel=0.015)
+
+
+def _c1_like(L=8, N=8, seed=1, kT=1.0):
+    fp = o.FluidParams(L=L, rho=1.0, eta=3.0, eta_b=3.0, kT=kT, h=0.01, a=1.0, seed=seed)
+    cp = o.ChainParams(N=N, m=1.0, zeta=20.8, k_fene=30.0, R0=1.5, eps=1.0, sigma=1.0)
+    X0 = inputs.chain_walk(N, L=L, bond=0.97, seed=seed, self_avoiding=True)
+    return fp, cp, o.init_state(fp, cp, X0)
+
+
+def test_mass_and_total_momentum_are_exactly_conserved():
+    """Collision conserves mass and momentum (Sec. II B); the coupling subtracts from the
+    fluid exactly the momentum it gives the beads; FENE/WCA forces are pairwise.  So
+    a^3 sum j + sum m v + (h/2) sum F_c is invariant to round-off."""
+    fp, cp, st = _c1_like()
+    M0 = o.total_mass(st, fp)
+    P0 = o.total_momentum(st, fp, cp)
+    scale = fp.L ** 3 * fp.a ** 3 * fp.rho * fp.a / fp.h
+    for _ in range(4):
+        st = o.run(st, fp, cp, 25)
+        assert o.total_mass(st, fp) == pytest.approx(M0, rel=1e-13)
+        assert np.allclose(o.total_momentum(st, fp, cp), P0, rtol=0, atol=1e-13 * scale)
+    assert np.abs(st.V).max() > 0.1  # the beads did move
+
+
+def test_single_dragged_bead_reaches_stokes_velocity():
+    """A constant force F on one bead, balanced by a uniform counter-force on the fluid:
+    in steady state the friction balances F exactly (v - u_b = F / zeta_bare) and the bead
+    moves through the fluid at F / zeta_eff with 1/zeta_eff = 1/zeta_bare + 1/(g eta a),
+    g ~ 25 for linear interpolation (Eq. 7), corrected for the periodic images
+    (Hasimoto: -2.837/(6 pi eta L))."""
+    L = 10
+    F = np.array([0.02, 0.0, 0.0])
+    fp = o.FluidParams(L=L, rho=1.0, eta=3.0, eta_b=3.0, kT=0.0, h=0.01, noise_fluid=False,
+                       body_force=tuple(-F / L ** 3))
+    cp = o.ChainParams(N=1, m=1.0, zeta=20.8, noise_beads=False, ext_force=tuple(F))
+    st = o.init_state(fp, cp, X0=np.array([[4.3, 5.6, 5.2]]))
+    st = o.run(st, fp, cp, 1500)
+    Vh = st.V - fp.h * st.F / (2 * cp.m)  # (F = F_cons + F_c of the last step)
+    ub = o.interpolate_u(o.stream(st.n), fp, st.X)
+    # force balance at the (quasi-)steady state, F_c = -F_ext; the bead drifts slowly
+    # across its cell so the balance is approached to ~1e-6, not to round-off
+    assert np.allclose(st.Fc[0], -F, rtol=1e-4, atol=1e-9)
+    assert np.allclose(-cp.zeta * (Vh[0] - ub[0]), -F, rtol=1e-4, atol=1e-9)
+    # mobility relative to the mean fluid velocity
+    ubar = o.fluid_momentum(st, fp) / (fp.rho * L ** 3 * fp.a ** 3)
+    v_rel = st.V[0, 0] - ubar[0]
+    inv_zeta_eff = 1 / cp.zeta + 1 / (25 * fp.eta * fp.a) - 2.837 / (6 * math.pi * fp.eta * L * fp.a)
+    assert v_rel == pytest.approx(F[0] * inv_zeta_eff, rel=0.10)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_cell_index_edge_cases(dtype):
+    """Cell of a coordinate = floor(x/a) mod L into [0, L), in the precision of the stored
+    coordinate; checked against exact integer arithmetic."""
+    L = 16
+    one = dtype(1.0)
+    cases = [0.0, -0.0, 1.0, 15.0, 16.0, -1.0, -16.0, 31.999, 1e4 * L, -1e4 * L - 0.5]
+    xs = [dtype(v) for v in cases]
+    for k in (1, 5, 15, 16, 17, -1, -16, 160000):
+        xk = dtype(k)
+        xs += [np.nextafter(xk, dtype(np.inf)), np.nextafter(xk, dtype(-np.inf))]
+    xs = np.array(xs, dtype=dtype)
+    got = o.cell_index(xs, one, L)
+    for x, g in zip(xs, got):
+        fl = math.floor(float(x))  # a = 1: x/a = x exactly
+        assert g == fl % L and 0 <= g < L
+    # general spacing: the quotient is rounded once in the stored precision
+    a = dtype(0.7)
+    q = (xs / a).astype(dtype)
+    want = np.array([math.floor(float(v)) % L for v in q])
+    assert np.array_equal(o.cell_index(xs, a, L), want)
+
+
+def test_bead_in_fluctuating_fluid_is_at_the_fluid_temperature():
+    """Fluctuation-dissipation of the coupled system (Sec. II B): a bead coupled to the
+    thermalized fluid reaches <v^2>/3 = kT/m (statistical tolerance)."""
+    fp = o.FluidParams(L=6, rho=1.0, eta=3.0, eta_b=3.0, kT=1.0, h=0.01, seed=3)
+    cp = o.ChainParams(N=1, m=1.0, zeta=20.8)
+    st = o.init_state(fp, cp, X0=np.array([[3.3, 2.2, 4.1]]))
+    vs = []
+    for k in range(4000):
+        st = o.step(st, fp, cp)
+        if k > 200:
+            vs.append(st.V[0].copy())
+    assert np.var(vs) == pytest.approx(fp.kT / cp.m, rel=0.08)

@@ -1,0 +1,150 @@
+"""Pins of the oracle's random numbers and of the fluctuating LB: Philox4x32-10 against an
+independent library implementation (Triton's, run by its CPU interpreter), the uniform and
+Gaussian transforms against their distributions, and equipartition of every thermalized
+mode and of the fluid velocity (Sec. II B: noise on all non-conserved modes)."""
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import lbchain as o
+
+_TRITON_SCRIPT = textwrap.dedent(
+    """
+    import os, sys, json
+    os.environ["TRITON_INTERPRET"] = "1"
+    import numpy as np, torch, triton, triton.language as tl
+
+    @triton.jit
+    def kern(c_ptr, out_ptr, seed, BLOCK: tl.constexpr):
+        i = tl.arange(0, BLOCK)
+        c0 = tl.load(c_ptr + 4 * i + 0)
+        c1 = tl.load(c_ptr + 4 * i + 1)
+        c2 = tl.load(c_ptr + 4 * i + 2)
+        c3 = tl.load(c_ptr + 4 * i + 3)
+        r0, r1, r2, r3 = tl.philox(seed, c0, c1, c2, c3, 10)
+        tl.store(out_ptr + 4 * i + 0, r0)
+        tl.store(out_ptr + 4 * i + 1, r1)
+        tl.store(out_ptr + 4 * i + 2, r2)
+        tl.store(out_ptr + 4 * i + 3, r3)
+
+    spec = json.loads(sys.argv[1])
+    res = {}
+    for seed in spec["seeds"]:
+        ctr = np.array(spec["ctr"], dtype=np.uint32).reshape(-1)
+        c = torch.from_numpy(ctr.view(np.int32).copy())
+        out = torch.zeros_like(c)
+        kern[(1,)](c, out, seed, BLOCK=len(spec["ctr"]))
+        res[str(seed)] = out.numpy().view(np.uint32).tolist()
+    print(json.dumps(res))
+    """
+)
+
+
+def test_philox_matches_independent_library_implementation():
+    pytest.importorskip("triton")
+    import json
+
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(16, 4), dtype=np.uint64)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    ctr[2] = (7, 123456, 3, 0)  # a (step, node, call, 0) counter of the fluid layout
+    seeds = [0, 1, 0x1234ABCD, (0x00000102 << 32) | 0xDEADBEEF, 2 ** 64 - 1]
+    spec = {"seeds": seeds, "ctr": ctr.tolist()}
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    r = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT, json.dumps(spec)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + r.stderr[-300:])
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    for seed in seeds:
+        k0, k1 = seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF
+        got = np.stack(o.philox4x32_10(ctr[:, 0], ctr[:, 1], ctr[:, 2], ctr[:, 3], k0, k1), axis=1)
+        want = np.array(res[str(seed)], dtype=np.uint32).reshape(-1, 4)
+        assert np.array_equal(got, want), seed
+
+
+def test_philox_output_bits_are_balanced():
+    x = np.stack(o.philox4x32_10(np.arange(20000), 5, 0, 0, 17, 3))
+    bits = np.unpackbits(x.view(np.uint8)).reshape(-1)
+    assert abs(bits.mean() - 0.5) < 4 * 0.5 / np.sqrt(bits.size)
+    # consecutive counters give uncorrelated words
+    u = o.uniform01(x[0]) - 0.5
+    assert abs(np.corrcoef(u[:-1], u[1:])[0, 1]) < 0.05
+
+
+def test_uniform_transform_is_exact_in_float32_and_open():
+    x = np.array([0, 1, 511, 512, 2 ** 31, 2 ** 32 - 1], dtype=np.uint32)
+    u = o.uniform01(x)
+    assert np.all(u > 0) and np.all(u < 1)
+    assert np.array_equal(u.astype(np.float32).astype(np.float64), u)
+    assert u[0] == 2.0 ** -24 and u[-1] == 1.0 - 2.0 ** -24
+    k = np.arange(0, 2 ** 23, 4099, dtype=np.uint64)
+    assert np.array_equal(o.uniform01((k << np.uint64(9)).astype(np.uint32)), (k + 0.5) * 2.0 ** -23)
+
+
+def test_box_muller_is_standard_normal():
+    g = o.gaussians16(seed=3, tag=o.TAG_FLUID, replica=0, step=11, index=np.arange(20000))
+    flat = g.reshape(-1)
+    assert stats.kstest(flat, "norm").pvalue > 1e-3
+    assert abs(flat.mean()) < 4 / np.sqrt(flat.size)
+    assert abs(flat.var() - 1) < 4 * np.sqrt(2 / flat.size)
+    c = np.corrcoef(g[:, :5000])
+    assert np.max(np.abs(c - np.eye(16))) < 0.07
+
+
+def test_noise_streams_depend_on_every_key_and_counter_field():
+    base = o.gaussians16(1, o.TAG_FLUID, 0, 5, np.arange(8))
+    for args in [(2, o.TAG_FLUID, 0, 5), (1, o.TAG_BEAD, 0, 5), (1, o.TAG_FLUID, 1, 5), (1, o.TAG_FLUID, 0, 6)]:
+        assert not np.allclose(o.gaussians16(*args, np.arange(8)), base)
+
+
+def _equilibrium_run(L, nsteps, warm, fp, every=2):
+    n = o.fluid_at_rest(fp)
+    ms, us = [], []
+    for k in range(nsteps):
+        nps = o.stream(n)
+        if k >= warm and k % every == 0:
+            m = o.M @ nps.reshape(19, -1)
+            ms.append(m)
+        n = o.collide(nps, fp, step=k)
+    return np.stack(ms, axis=0)  # (samples, 19, L^3)
+
+
+def test_equipartition_of_modes_and_velocity():
+    """Full thermalization: every mode fluctuates with variance mu rho b_k (the conserved
+    ones reduced by the global constraint (1 - 1/L^3)), so var(u) = kT/(rho a^3) and
+    var(rho) = mu rho."""
+    L = 8
+    fp = o.FluidParams(L=L, rho=1.0, eta=3.0, eta_b=3.0, kT=1.0, h=0.01, a=1.0, seed=21)
+    m = _equilibrium_run(L, 1400, 100, fp)
+    mu = o.mu_thermal(fp)
+    corr = 1.0 - 1.0 / L ** 3
+    var = m.var(axis=(0, 2))
+    assert var[0] == pytest.approx(mu * fp.rho * corr, rel=0.05)
+    for k in (1, 2, 3):
+        assert var[k] == pytest.approx(mu * fp.rho * o.B[k] * corr, rel=0.05)
+    for k in range(4, 19):
+        assert var[k] == pytest.approx(mu * fp.rho * o.B[k], rel=0.05), k
+    ux = m[:, 1] / m[:, 0] * fp.a / fp.h
+    assert ux.var() == pytest.approx(fp.kT / (fp.rho * fp.a ** 3) * corr, rel=0.05)
+
+
+def test_stress_only_thermalization_leaves_kinetic_modes_silent():
+    """Ahlrichs-Duenweg variant (Table 1, note b): noise only on the stress modes 4..9; the
+    kinetic modes leave the collision at exactly zero."""
+    L = 4
+    fp = o.FluidParams(L=L, kT=1.0, seed=2, stress_only=True)
+    rng = np.random.default_rng(1)
+    n = o.fluid_at_rest(fp) * (1 + 0.01 * rng.random((19, L, L, L)))
+    ns = o.collide(n, fp, step=0)
+    m = o.M @ ns.reshape(19, -1)
+    assert np.allclose(m[10:], 0.0, atol=1e-15)
+    fp_off = o.FluidParams(L=L, kT=0.0, noise_fluid=False)
+    m_off = o.M @ o.collide(n, fp_off, step=0).reshape(19, -1)
+    assert not np.allclose(m[4:10], m_off[4:10])
