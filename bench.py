@@ -1,0 +1,373 @@
+"""Benchmark: fused FP32 fluctuating D3Q19 LB + bead-spring chain step on GB300, in MLUPS
+(million lattice-node updates per second) and as a fraction of the HBM roofline, beside the
+plain FP64 path on the same GPU and the FP64 CPU oracle.
+
+Workload: L = 128 periodic box (2,097,152 nodes), rho = 1, eta = eta_b = 3, kT = 1, a = 1,
+h = 0.01, one chain of N = 128 beads (m = 1, FENE k = 30, R0 = 1.5, WCA eps = sigma = 1,
+zeta = 20.8) started as a self-avoiding walk with bond 0.97, fluid at rest, full
+thermalization, seed 3.  The two population buffers (2 x 159 MB in FP32) are larger than
+the 129 MB L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank runs an independent replica of the
+workload (own seed): the method has no exchange between independent boxes, so the job
+scales weakly with no data-path collective; the MAX of the ranks' timed regions is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline: fused FP32 LB+chain vs plain FP64, same GPU"
+L_BENCH, N_BENCH, SEED = 128, 128, 3
+PARAMS = dict(rho=1.0, eta=3.0, eta_b=3.0, kT=1.0, h=0.01, a=1.0)
+CHAIN = dict(m=1.0, zeta=20.8, k_fene=30.0, R0=1.5, eps=1.0, sigma=1.0)
+BYTES_PER_NODE = {"f32": 19 * 4 * 2, "f64": 19 * 8 * 2}  # algorithmic: 19 reads + 19 writes
+KERNEL_SOURCES = ["paper_0903_5067_gb300/csrc/lb_device.cuh", "paper_0903_5067_gb300/csrc/d3q19.cuh",
+                  "paper_0903_5067_gb300/csrc/philox.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "lb_step_f32_L128_traffic.json")
+
+
+def workload_name(L=L_BENCH, N=N_BENCH):
+    return (f"fluctuating D3Q19 LB, periodic L={L} box ({L ** 3:,} nodes) + FENE/WCA chain N={N}, "
+            f"full thermalization, 1 coupled step = 1 LB + 1 MD step")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the FP32 LB kernel from the committed ncu summary, or None
+    when the kernel sources changed since it was taken."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    with open(TRAFFIC_FILE) as fh:
+        d = json.load(fh)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch_full_size")
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason sampling while the timed work runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+                except ValueError:
+                    continue
+        if not rows:
+            return None
+        powered = [r for r in rows if r[2] > 0.5 * max(x[2] for x in rows)] or rows
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, flag in zip(names, r[3]):
+                if flag.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[0] for r in powered), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(powered)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value: float, ws: int, device=None) -> float:
+    """MAX of a per-rank scalar over the job (identity when ws == 1)."""
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(units_per_rank: float, seconds: float, ws: int, device=None):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    tmax = max_over_ranks(seconds, ws, device)
+    return units_per_rank * ws / tmax, tmax
+
+
+def cpu_oracle_sample(L: int, N: int, steps: int, seed: int, timeout: float = 900.0):
+    """Time the FP64 oracle (single thread) for `steps` coupled steps of the workload on an
+    L^3 box, in a fresh process; returns seconds per step."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+from oracle import lbchain as o
+from paper_0903_5067_gb300 import inputs
+fp = o.FluidParams(L={L}, seed={seed}, **{PARAMS!r})
+cp = o.ChainParams(N={N}, **{CHAIN!r})
+st = o.init_state(fp, cp, inputs.chain_walk({N}, L={L}, bond=0.97, seed={seed}, self_avoiding=True))
+t = time.perf_counter()
+st = o.run(st, fp, cp, {steps})
+print(json.dumps({{"s_per_step": (time.perf_counter() - t) / {steps}}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])["s_per_step"]
+
+
+def run_reference(args):
+    """The FP64 oracle on the host cores, same workload/metric/unit (each step a sample)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    budget = 150.0 / max(1, args.steps + args.warmup)  # seconds per step so the run ends in minutes
+
+    def chain_for(Ls):
+        return N_BENCH if Ls >= 64 else (64 if Ls >= 32 else 8)
+
+    L = L_BENCH
+    probe = cpu_oracle_sample(L, N_BENCH, 1, SEED)
+    sample = f"full L={L} workload, 1 coupled step per step"
+    if probe > budget:
+        for Ls in (96, 64, 48, 32, 24, 16):
+            L = Ls
+            probe = cpu_oracle_sample(L, chain_for(L), 1, SEED)
+            if probe <= budget:
+                break
+        sample = f"L={L} sub-box of the workload (same fluid, chain N={chain_for(L)}), 1 coupled step per step"
+    per = cpu_oracle_sample(L, chain_for(L), args.steps + args.warmup, SEED, timeout=3600)
+    value = L ** 3 / per / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(), "L": L_BENCH, "N": N_BENCH, "seed": SEED},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_0903_5067_gb300 import inputs, lb
+
+    # CPU baseline first (a fresh process, before this process does GPU work)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        s = cpu_oracle_sample(L_BENCH, N_BENCH, 1, SEED)
+        cpu = {"value": L_BENCH ** 3 / s / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"1 coupled step of the full L={L_BENCH}, N={N_BENCH} workload, FP64, single thread"}
+
+    L, N, seed = L_BENCH, N_BENCH, SEED + 1000 * rank
+    X0 = inputs.chain_walk(N, L=L, bond=0.97, seed=seed, self_avoiding=True)
+
+    def make(prec):
+        sim = lb.Simulation(L=L, seed=seed, precision=prec, **PARAMS)
+        sim.add_chain(N, x0=X0, **CHAIN)
+        return sim
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    sim = make(lb.LB_FP32)
+    sim.step(args.warmup)
+    sim.sync()
+
+    clocks = ClockSampler(local)
+    with clocks:
+        # timed region: K fused steps, inputs resident in HBM
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        barrier()
+        t32 = e0.elapsed_time(e1) / 1e3
+        sim.sync()
+        # roofline pass: events around every LB launch (same stream)
+        lb.lb_set_timing(sim.ctx, True)
+        sim.step(args.steps)
+        ms_k, nk = lb.lb_get_timing(sim.ctx)
+        lb.lb_set_timing(sim.ctx, False)
+        sim.sync()
+        # plain FP64 path on the same GPU, same workload
+        k64 = max(3, args.steps // 20)
+        s64 = make(lb.LB_FP64)
+        s64.step(max(1, args.warmup // 20))
+        s64.sync()
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s64.step(k64)
+        f1.record(stream)
+        barrier()
+        t64 = f0.elapsed_time(f1) / 1e3
+        s64.sync()
+        s64.close()
+    obs = sim.observables()
+    sim.close()
+
+    value, tmax = aggregate_throughput(L ** 3 * args.steps / 1e6, t32, ws, dev)
+    v64, _ = aggregate_throughput(L ** 3 * k64 / 1e6, t64, ws, dev)
+
+    # end to end through the C ABI with host buffers: upload the initial state, K steps each
+    # followed by a read-back of the beads, download the final populations
+    n0 = torch.empty((19, L, L, L), dtype=torch.float64, pin_memory=True).numpy()
+    nout = torch.empty((19, L, L, L), dtype=torch.float64, pin_memory=True).numpy()
+    xb = torch.empty((N, 3), dtype=torch.float64, pin_memory=True).numpy()
+    vb = torch.empty((N, 3), dtype=torch.float64, pin_memory=True).numpy()
+    ctx = lb.lb_create(L, PARAMS["rho"], PARAMS["eta"], PARAMS["eta_b"], PARAMS["kT"], PARAMS["h"], PARAMS["a"],
+                       seed, lb.LB_FP32)
+    lb.lb_add_chain(ctx, N, CHAIN["m"], CHAIN["zeta"], CHAIN["k_fene"], CHAIN["R0"], CHAIN["eps"], CHAIN["sigma"],
+                    x0=X0)
+    lb.lb_set_stream(ctx, stream.cuda_stream)
+    lb.lb_get_populations(ctx, n0)  # the initial (rest) state, as host input; allocates the workspace
+    ke = args.steps
+    barrier()
+    t0 = time.perf_counter()
+    lb.lb_set_populations(ctx, n0)
+    for _ in range(ke):
+        lb.lb_step(ctx, 1)
+        lb.lb_get_beads(ctx, xb, vb, 3 * N)
+    lb.lb_get_populations(ctx, nout)
+    barrier()
+    te = time.perf_counter() - t0
+    lb.lb_destroy(ctx)
+    e2e_val, _ = aggregate_throughput(L ** 3 * ke / 1e6, te, ws, dev)
+    h2d = n0.nbytes / ke
+    d2h = nout.nbytes / ke + xb.nbytes + vb.nbytes
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    peak, peak_kind = measured_peaks()
+    avg_kernel_s = ms_k / max(nk, 1) / 1e3
+    achieved = BYTES_PER_NODE["f32"] * L ** 3 / avg_kernel_s / 1e9
+    launches_per_step = 3  # bead kernel, LB kernel, force-correction kernel
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(), "L": L, "N": N, "seed": SEED, "precision": "FP32 deviations",
+                   "noise": "full thermalization + bead Langevin", "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (2 x 159 MB population buffers > 129 MB), no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": ncu_traffic(), "kernel": "k_lb_step<float,float,DEV,NOISE>",
+                     "algorithmic_bytes_per_node": BYTES_PER_NODE["f32"], "avg_launch_ms": avg_kernel_s * 1e3,
+                     "peak_kind": f"{peak_kind} (STREAM copy, burst)"},
+        "fp64_plain": {"value": v64, "unit": "MLUPS", "steps": k64, "ms_per_step": t64 / k64 * 1e3,
+                       "roofline_frac": BYTES_PER_NODE["f64"] * L ** 3 / (t64 / k64) / 1e9 / peak,
+                       "fp32_over_fp64": value / v64},
+        "bead_steps_per_s": N * args.steps * ws / tmax,
+        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "path": "C ABI, pinned host buffers: set_populations, K x (step + get_beads), get_populations"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks.summary(),
+        "cpu_baseline": cpu,
+        "check": {"mass": obs[1], "bead_temperature": obs[15]},
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

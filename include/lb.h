@@ -1,0 +1,159 @@
+/*
+ * lb.h — C ABI of the GB300 fluctuating D3Q19 lattice-Boltzmann + bead-spring chain library
+ * (libgblb.so).
+ *
+ * The method is the explicit-solvent model of Pham, Schiller, Prakash & Duenweg,
+ * "Implicit and explicit solvent models for the simulation of a single polymer chain in
+ * solution: Lattice Boltzmann vs Brownian dynamics" (arXiv:0903.5067), Sec. II:
+ *   - fluid: fluctuating lattice Boltzmann equation (Sec. II B, Eq. 3) on D3Q19 with the
+ *     second-order equilibrium (Eq. 4), moment-space relaxation and noise on every
+ *     non-conserved mode ("full thermalization"), periodic cubic box of L^3 nodes;
+ *   - chain: N beads, FENE bonds and WCA (Lennard-Jones cut at 2^(1/6) sigma, shifted) between
+ *     all monomers (Sec. II A, Eqs. 1-2);
+ *   - coupling: flow velocity interpolated from the 8 surrounding nodes, Stokes friction
+ *     -zeta_bare (v - u) plus a balancing Langevin force, reaction spread back onto the same
+ *     nodes so that momentum is conserved (Sec. II B, last paragraph).
+ *
+ * Units: all physical arguments are in the caller's (MD) unit system; nodes sit at
+ * positions a*(x, y, z), x, y, z in [0, L).  Populations are partial mass densities.
+ *
+ * Conventions for every call:
+ *   - returns an lb_status (0 = LB_OK); lb_strerror() names it;
+ *   - host buffers are caller-owned; every output buffer comes with its capacity in
+ *     elements and the call fails with LB_ERR_ARG when it is too small;
+ *   - device work is enqueued on the context's stream (lb_set_stream; default: the legacy
+ *     default stream); calls that return data to the host synchronise that stream;
+ *   - errors found on the device (broken FENE bond, non-finite state) are latched in a
+ *     device status word and returned by the next synchronising call (lb_sync, lb_get_*).
+ *   - one context = one fluid box + at most one chain, used from one host thread at a time.
+ */
+#ifndef GBLB_LB_H
+#define GBLB_LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx; /* opaque, library-owned */
+
+enum lb_status {
+  LB_OK = 0,
+  LB_ERR_ARG = 1,       /* invalid argument or buffer too small */
+  LB_ERR_CUDA = 2,      /* a CUDA runtime call failed */
+  LB_ERR_OOM = 3,       /* device allocation failed */
+  LB_ERR_FENE = 4,      /* a FENE bond reached r >= R0 (Sec. II A, Eq. 1 diverges) */
+  LB_ERR_NONFINITE = 5, /* NaN/Inf in the fluid or bead state */
+  LB_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
+  LB_ERR_STATE = 7      /* call not valid in the context's current state */
+};
+
+/* Storage/arithmetic precision of a context.
+ * LB_FP64: populations stored as full n_i in FP64, FP64 arithmetic (the plain path).
+ * LB_FP32: populations stored as deviations n_i - w_i rho0 in FP32, FP32 arithmetic.
+ * LB_BF16 / LB_FP16: deviations stored in 16 bits, FP32 arithmetic. */
+enum lb_precision { LB_FP64 = 0, LB_FP32 = 1, LB_BF16 = 2, LB_FP16 = 3 };
+
+/* Create a fluid box (Sec. II B).  L >= 4 nodes per side; rho (background mass density
+ * rho0), eta (shear viscosity), eta_b (bulk viscosity), h (time step, LB and MD) and a
+ * (lattice spacing) > 0; kT >= 0.  The relaxation eigenvalues gamma_s, gamma_b derived from
+ * eta, eta_b must lie in (-1, 1) (always true for positive viscosities).  seed keys the
+ * Philox noise streams (its low 32 bits).  The fluid starts at rest, n_i = w_i rho0.
+ * No device memory is touched until the first device call.  *out receives the context. */
+int lb_create(lb_ctx** out, int L, double rho, double eta, double eta_b, double kT, double h,
+              double a, uint64_t seed, int precision);
+
+/* Add the bead-spring chain (Sec. II A-B): N beads of mass m, friction zeta (zeta_bare),
+ * FENE (k_fene, R0), WCA (eps, sigma).  x0: 3N positions (bead-major x,y,z; unwrapped) or
+ * NULL to let the library generate a walk of step `bond` starting at the box centre
+ * (self-avoiding when saw != 0: no bead closer than sigma to an earlier non-adjacent one);
+ * v0: 3N velocities or NULL for zero.  1 <= N <= 1024.  Must precede the first device
+ * call.  Bonds initially at r >= R0 give LB_ERR_FENE. */
+int lb_add_chain(lb_ctx* ctx, int N, double m, double zeta, double k_fene, double R0, double eps,
+                 double sigma, const double* x0, const double* v0, double bond, int saw);
+
+/* Run-time options.  noise_fluid / noise_beads switch the fluctuating terms (both also off
+ * when kT = 0); stress_only restricts fluid noise to the six stress modes (the original
+ * Ahlrichs-Duenweg thermalization, Table 1 note b); ext_bead_force (3 doubles or NULL) is a
+ * constant force on every bead; counter_force_fluid != 0 adds the uniform force density
+ * -N ext_bead_force / (L a)^3 to every node so that total momentum stays conserved. */
+int lb_set_options(lb_ctx* ctx, int noise_fluid, int noise_beads, int stress_only,
+                   const double ext_bead_force[3], int counter_force_fluid);
+
+/* Device stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream); NULL =
+ * legacy default stream.  Must name a stream of the current device. */
+int lb_set_stream(lb_ctx* ctx, void* stream);
+
+/* Device workspace: size in bytes (valid after lb_add_chain, if any) and binding of a
+ * caller-owned device buffer of at least that size, 256-byte aligned, on the current
+ * device, that the caller keeps alive until lb_destroy.  Without a binding the library
+ * allocates (cudaMalloc) and frees the workspace itself. */
+int lb_workspace_size(lb_ctx* ctx, size_t* bytes);
+int lb_bind_workspace(lb_ctx* ctx, void* device_ptr, size_t bytes);
+
+/* Advance n >= 0 coupled steps (Sec. II B, Eq. 3 for the fluid; velocity Verlet for the
+ * beads, friction at the half-step velocity).  Asynchronous on the context stream. */
+int lb_step(lb_ctx* ctx, int64_t n);
+
+/* Wait for the context stream and return the latched device status. */
+int lb_sync(lb_ctx* ctx);
+
+/* Full populations n_i (FP64, mass densities), layout [i][z][y][x], 19 L^3 values, in the
+ * ABI velocity order (0; +x,-x,+y,-y,+z,-z; (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0),(1,0,1),
+ * (-1,0,-1),(1,0,-1),(-1,0,1),(0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1)), post-collision and
+ * force-corrected, as they stand between two steps.  Synchronising. */
+int lb_get_populations(lb_ctx* ctx, double* out, size_t cap);
+/* Replace the populations (same layout, 19 L^3 doubles).  Enqueued on the stream. */
+int lb_set_populations(lb_ctx* ctx, const double* in, size_t count);
+
+/* Bead positions (unwrapped) and velocities, 3N each (bead-major).  Either pointer may be
+ * NULL.  Synchronising.  Before the first device call it returns the staged initial chain
+ * (given or generated by lb_add_chain) without touching the device. */
+int lb_get_beads(lb_ctx* ctx, double* x, double* v, size_t cap);
+
+/* FP64 observables (Sec. III A-B), cap >= LB_NOBS:
+ *  [0] step  [1] mass a^3 sum n  [2..4] total momentum (fluid + beads + h/2 sum F_c)
+ *  [5..7] fluid momentum  [8] R_g^2  [9] R_e^2  [10..12] centre of mass (unwrapped)
+ *  [13] g1: mean |r_i(t) - r_i(t0)|^2 of the two innermost beads  [14] g3: |R_cm(t) -
+ *  R_cm(t0)|^2  [15] bead kinetic temperature m<v^2>/3  [16] count of non-positive node
+ *  densities met by the noise  [17] number of accumulated samples  [18] <R_g^2> and
+ *  [19] <R_e^2> over the samples.  t0 is the chain's state when it was added (or at the
+ *  last lb_reset_reference).  Synchronising. */
+#define LB_NOBS 20
+int lb_get_observables(lb_ctx* ctx, double* out, size_t cap);
+/* Accumulate <R_g^2>, <R_e^2> every `stride` steps inside lb_step (0 = off). */
+int lb_set_obs_stride(lb_ctx* ctx, int stride);
+/* Take the current bead positions as the reference t0 of g1 and g3; clear accumulators. */
+int lb_reset_reference(lb_ctx* ctx);
+
+/* Checkpoint / resume: parameters, options, step counter, populations (storage precision),
+ * bead state.  Noise is counter-based, so a resumed run continues bit-identically. */
+int lb_save(lb_ctx* ctx, const char* path);
+int lb_load(lb_ctx* ctx, const char* path);
+
+/* Step counter and device kernel timing: when enabled, lb_step records CUDA events around
+ * every fused LB launch; lb_get_timing returns their summed duration (ms) and count. */
+int64_t lb_get_step(lb_ctx* ctx);
+int lb_set_timing(lb_ctx* ctx, int enable);
+int lb_get_timing(lb_ctx* ctx, double* total_ms, int64_t* launches);
+
+void lb_destroy(lb_ctx* ctx);
+const char* lb_strerror(int status);
+
+/* --- test hooks on raw device buffers (enqueued on `stream`, no context) --------------- */
+
+/* Philox4x32-10 on n counters: ctr_dev[4n] -> out_dev[4n] (uint32), key (k0, k1). */
+int lb_philox4x32_10(const uint32_t* ctr_dev, int64_t n, uint32_t k0, uint32_t k1,
+                     uint32_t* out_dev, void* stream);
+
+/* Cell index of FP32 coordinates: out_dev[i] = floor(x_dev[i] / a) mod L in [0, L), the
+ * quotient rounded once in FP32 (the bead kernel's own index function). */
+int lb_cell_index_f32(const float* x_dev, int64_t n, float a, int L, int32_t* out_dev,
+                      void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBLB_LB_H */

@@ -1,0 +1,785 @@
+// Device code of the fluctuating D3Q19 LB + bead-spring chain step.
+//
+// Storage: populations in structure-of-arrays planes pop[i][z][y][x] (plane stride
+// `plane` elements), two buffers A/B.  FP32/BF16/FP16 contexts store the deviation
+// n_i - w_i rho0 (DEV = true), the FP64 context the full n_i.  A step reads buffer A
+// (post-collision populations of the previous step, "pull" storage) and writes B.
+//
+// One step = k_bead_step (one CTA: velocity Verlet, FENE/WCA, interpolation, friction +
+// noise, spreading -> sparse list of per-node population corrections), k_lb_step (every
+// node: pull-stream, moments, relaxation + noise, back-transform) and k_apply_pending (adds
+// the force corrections to B).  The bead kernel and the LB kernel read only A, so they are
+// independent; the correction is additive on the post-collision populations because the
+// collision conserves the density and momentum it depends on.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "d3q19.cuh"
+#include "philox.cuh"
+
+namespace gblb {
+
+enum : unsigned { ST_FENE = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u };
+
+// ---------------------------------------------------------------------------------------
+// storage <-> arithmetic conversions
+// ---------------------------------------------------------------------------------------
+template <class S, class R>
+__device__ __forceinline__ R ld(const S* p) { return (R)(*p); }
+template <>
+__device__ __forceinline__ float ld<__nv_bfloat16, float>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+template <>
+__device__ __forceinline__ float ld<__half, float>(const __half* p) { return __half2float(*p); }
+
+template <class S, class R>
+__device__ __forceinline__ void st(S* p, R v) { *p = (S)v; }
+template <>
+__device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ void st<__half, float>(__half* p, float v) { *p = __float2half_rn(v); }
+
+// ---------------------------------------------------------------------------------------
+// kernel parameter blocks (passed by value)
+// ---------------------------------------------------------------------------------------
+template <class R>
+struct FluidK {
+  unsigned L;
+  unsigned long long plane;  // elements between population planes
+  R rho0;
+  R gs, gb;        // relaxation eigenvalues: shear modes 5..9, bulk mode 4 (kinetic modes: 0)
+  R cnoise[Q];     // sqrt(mu b_k (1 - gamma_k^2)), mode k's noise per sqrt(rho); 0 if silent
+  uint32_t k0, k1; // Philox key of the fluid stream
+  int ncalls;      // Philox calls per node: 0 (noise off), 2 (stress modes only), 4 (all)
+  int body_on;     // uniform body force
+  R body_dJ[3];    // lattice momentum it adds per step and node: f h^2 / a
+  unsigned long long* nonpos;  // counter of non-positive densities met by the noise
+};
+
+template <class R>
+struct ChainK {
+  int N;
+  R m, zeta, kfene, R0sq, eps, sig2, rc2;
+  R h, a, box, inv_box;
+  R amp;            // sqrt(2 kT zeta / h), 0 without bead noise
+  uint32_t k0, k1;  // Philox key of the bead stream
+  R ext[3];         // constant external force on each bead
+  R u_scale;        // a / h: lattice -> physical velocity
+  R inv_a3;         // 1 / a^3
+  R dJ_scale;       // h^2 / a: force density -> lattice momentum per step
+  // bead state (global, 3N each, bead-major)
+  R* x;    // wrapped positions in [0, box)
+  int* img;  // periodic image counters
+  R* v;
+  R* F;    // total force of the last step (F_cons + F_c)
+  R* Fc;   // coupling force of the last step
+  // scratch (global)
+  R* vh;       // 3N half-step velocities
+  R* fcons;    // 3N conservative forces
+  int* e_node;  // 8N corner nodes
+  R* e_w;      // 8N trilinear weights
+  R* e_mom;    // 4 x 8N: post-stream rho, Jx, Jy, Jz at the corner node
+  int* p_node; // pending force corrections: node, and 19 population deltas [i][cap]
+  R* p_dn;
+  int* p_count;
+  int cap;     // 8N
+  unsigned* status;
+};
+
+// ---------------------------------------------------------------------------------------
+// moment algebra
+// ---------------------------------------------------------------------------------------
+// scaled moments a_k = m_k / b_k  ->  populations n_i = w_i sum_k e_k(c_i) a_k
+template <class R>
+__device__ __forceinline__ void modes_to_pops(const R a[Q], R out[Q]) {
+  {
+    R acc = R(0);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const int c = basis(k, 0);
+      if (c != 0) acc += R(c) * a[k];
+    }
+    out[0] = acc * (R(w36(0)) / R(36));
+  }
+#pragma unroll
+  for (int p = 0; p < NPAIR; ++p) {
+    const int i = 2 * p + 1;
+    R S = R(0), D = R(0);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const int c = basis(k, i);
+      if (c == 0) continue;
+      if (odd_mode(k))
+        D += R(c) * a[k];
+      else
+        S += R(c) * a[k];
+    }
+    const R w = R(w36(i)) / R(36);
+    out[i] = w * (S + D);
+    out[i + 1] = w * (S - D);
+  }
+}
+
+template <int K>
+struct InvB {
+  static constexpr double v = 36.0 / (double)norm36(K);
+};
+
+// Moment increments (modes 1..9) of a force adding lattice momentum dJ at a node of
+// density rho and pre-collision momentum J (second-order forcing reading):
+//   dm_1..3 = dJ;  dPi = (1+g_s)/2 (U'dJ + dJU' - 2/3 1 U'.dJ) + (1+g_b)/3 1 U'.dJ,
+//   U' = (J + dJ/2)/rho, mapped onto modes 4..9.
+template <class R>
+__device__ __forceinline__ void force_moments(R rho, R jx, R jy, R jz, R dx, R dy, R dz, R gs,
+                                              R gb, R dm[10]) {
+  const R ir = R(1) / rho;
+  const R ux = (jx + R(0.5) * dx) * ir, uy = (jy + R(0.5) * dy) * ir, uz = (jz + R(0.5) * dz) * ir;
+  const R ud = ux * dx + uy * dy + uz * dz;
+  const R cs = R(0.5) * (R(1) + gs);
+  const R diag = ((R(1) + gb) / R(3) - R(2) / R(3) * cs) * ud;
+  const R pxx = R(2) * cs * ux * dx + diag;
+  const R pyy = R(2) * cs * uy * dy + diag;
+  const R pzz = R(2) * cs * uz * dz + diag;
+  dm[0] = R(0);
+  dm[1] = dx;
+  dm[2] = dy;
+  dm[3] = dz;
+  dm[4] = pxx + pyy + pzz;
+  dm[5] = R(2) * pxx - pyy - pzz;
+  dm[6] = pyy - pzz;
+  dm[7] = cs * (ux * dy + uy * dx);
+  dm[8] = cs * (uy * dz + uz * dy);
+  dm[9] = cs * (ux * dz + uz * dx);
+}
+
+// population deltas of moment increments dm_0..9
+template <class R>
+__device__ __forceinline__ void dmoments_to_dpops(const R dm[10], R out[Q]) {
+  R a[Q];
+  a[0] = dm[0];
+  a[1] = dm[1] * R(InvB<1>::v);
+  a[2] = dm[2] * R(InvB<2>::v);
+  a[3] = dm[3] * R(InvB<3>::v);
+  a[4] = dm[4] * R(InvB<4>::v);
+  a[5] = dm[5] * R(InvB<5>::v);
+  a[6] = dm[6] * R(InvB<6>::v);
+  a[7] = dm[7] * R(InvB<7>::v);
+  a[8] = dm[8] * R(InvB<8>::v);
+  a[9] = dm[9] * R(InvB<9>::v);
+#pragma unroll
+  for (int k = 10; k < Q; ++k) a[k] = R(0);
+  modes_to_pops(a, out);
+}
+
+// ---------------------------------------------------------------------------------------
+// LB kernel: pull-stream + collide for every node (Sec. II B, Eq. 3)
+// ---------------------------------------------------------------------------------------
+template <class S, class R, bool DEV, bool NOISE>
+__global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* __restrict__ dst,
+                                                  const FluidK<R> P, const uint32_t step) {
+  const unsigned L = P.L;
+  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned y = blockIdx.y * blockDim.y + threadIdx.y;
+  const unsigned z = blockIdx.z;
+  if (x >= L || y >= L) return;
+  const unsigned xm = x ? x - 1 : L - 1, xp = (x + 1 < L) ? x + 1 : 0;
+  const unsigned ym = y ? y - 1 : L - 1, yp = (y + 1 < L) ? y + 1 : 0;
+  const unsigned zm = z ? z - 1 : L - 1, zp = (z + 1 < L) ? z + 1 : 0;
+  const unsigned LL = L * L;
+  // row offsets of the source rows: [dy+1][dz+1] for a pull from y - dy, z - dz
+  const unsigned ry[3] = {yp * L, y * L, ym * L};
+  const unsigned rz[3] = {zp * LL, z * LL, zm * LL};
+  const unsigned sxs[3] = {xp, x, xm};
+  const unsigned long long plane = P.plane;
+
+  R n[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const unsigned idx = sxs[cx(i) + 1] + ry[cy(i) + 1] + rz[cz(i) + 1];
+    n[i] = ld<S, R>(src + (unsigned long long)i * plane + idx);
+  }
+  const unsigned node = x + y * L + z * LL;
+
+  // moments 0..9 from pair sums / differences (kinetic modes relax to zero: not needed)
+  R s[NPAIR], d[NPAIR];
+#pragma unroll
+  for (int p = 0; p < NPAIR; ++p) {
+    s[p] = n[2 * p + 1] + n[2 * p + 2];
+    d[p] = n[2 * p + 1] - n[2 * p + 2];
+  }
+  R m[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    R acc = (basis(k, 0) != 0) ? R(basis(k, 0)) * n[0] : R(0);
+#pragma unroll
+    for (int p = 0; p < NPAIR; ++p) {
+      const int c = basis(k, 2 * p + 1);
+      if (c != 0) acc += R(c) * (odd_mode(k) ? d[p] : s[p]);
+    }
+    m[k] = acc;
+  }
+
+  const R rho = DEV ? P.rho0 + m[0] : m[0];
+  const R jx = m[1], jy = m[2], jz = m[3];
+  const R ir = R(1) / rho;
+  const R xx = jx * jx * ir, yy = jy * jy * ir, zz = jz * jz * ir;
+  R ms[Q];
+  ms[0] = m[0];
+  ms[1] = jx;
+  ms[2] = jy;
+  ms[3] = jz;
+  {
+    const R e4 = xx + yy + zz, e5 = R(2) * xx - yy - zz, e6 = yy - zz;
+    const R e7 = jx * jy * ir, e8 = jy * jz * ir, e9 = jx * jz * ir;
+    ms[4] = e4 + P.gb * (m[4] - e4);
+    ms[5] = e5 + P.gs * (m[5] - e5);
+    ms[6] = e6 + P.gs * (m[6] - e6);
+    ms[7] = e7 + P.gs * (m[7] - e7);
+    ms[8] = e8 + P.gs * (m[8] - e8);
+    ms[9] = e9 + P.gs * (m[9] - e9);
+  }
+#pragma unroll
+  for (int k = 10; k < Q; ++k) ms[k] = R(0);
+
+  if (NOISE) {
+    R sr = R(0);
+    if (rho > R(0)) {
+      sr = sqrt(rho);
+    } else {
+      atomicAdd(P.nonpos, 1ull);
+    }
+    R g[4];
+    gauss4<R>(step, node, 0u, P.k0, P.k1, g);
+    ms[4] += P.cnoise[4] * sr * g[0];
+    ms[5] += P.cnoise[5] * sr * g[1];
+    ms[6] += P.cnoise[6] * sr * g[2];
+    ms[7] += P.cnoise[7] * sr * g[3];
+    gauss4<R>(step, node, 1u, P.k0, P.k1, g);
+    ms[8] += P.cnoise[8] * sr * g[0];
+    ms[9] += P.cnoise[9] * sr * g[1];
+    if (P.ncalls > 2) {
+      ms[10] = P.cnoise[10] * sr * g[2];
+      ms[11] = P.cnoise[11] * sr * g[3];
+      gauss4<R>(step, node, 2u, P.k0, P.k1, g);
+      ms[12] = P.cnoise[12] * sr * g[0];
+      ms[13] = P.cnoise[13] * sr * g[1];
+      ms[14] = P.cnoise[14] * sr * g[2];
+      ms[15] = P.cnoise[15] * sr * g[3];
+      gauss4<R>(step, node, 3u, P.k0, P.k1, g);
+      ms[16] = P.cnoise[16] * sr * g[0];
+      ms[17] = P.cnoise[17] * sr * g[1];
+      ms[18] = P.cnoise[18] * sr * g[2];
+    }
+  }
+
+  if (P.body_on) {
+    R dm[10];
+    force_moments(rho, jx, jy, jz, P.body_dJ[0], P.body_dJ[1], P.body_dJ[2], P.gs, P.gb, dm);
+#pragma unroll
+    for (int k = 1; k < 10; ++k) ms[k] += dm[k];
+  }
+
+  R a[Q];
+  a[0] = ms[0];
+  a[1] = ms[1] * R(InvB<1>::v);
+  a[2] = ms[2] * R(InvB<2>::v);
+  a[3] = ms[3] * R(InvB<3>::v);
+  a[4] = ms[4] * R(InvB<4>::v);
+  a[5] = ms[5] * R(InvB<5>::v);
+  a[6] = ms[6] * R(InvB<6>::v);
+  a[7] = ms[7] * R(InvB<7>::v);
+  a[8] = ms[8] * R(InvB<8>::v);
+  a[9] = ms[9] * R(InvB<9>::v);
+  a[10] = ms[10] * R(InvB<10>::v);
+  a[11] = ms[11] * R(InvB<11>::v);
+  a[12] = ms[12] * R(InvB<12>::v);
+  a[13] = ms[13] * R(InvB<13>::v);
+  a[14] = ms[14] * R(InvB<14>::v);
+  a[15] = ms[15] * R(InvB<15>::v);
+  a[16] = ms[16] * R(InvB<16>::v);
+  a[17] = ms[17] * R(InvB<17>::v);
+  a[18] = ms[18] * R(InvB<18>::v);
+  R out[Q];
+  modes_to_pops(a, out);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) st<S, R>(dst + (unsigned long long)i * plane + node, out[i]);
+}
+
+// ---------------------------------------------------------------------------------------
+// bead / coupling kernel (one CTA)
+// ---------------------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R rnd_nearest(R v);
+template <>
+__device__ __forceinline__ float rnd_nearest<float>(float v) { return rintf(v); }
+template <>
+__device__ __forceinline__ double rnd_nearest<double>(double v) { return rint(v); }
+
+// cell of a coordinate: floor(x/a) mod L into [0, L); frac = x/a - floor(x/a)
+template <class R>
+__device__ __forceinline__ int cell_of(R x, R a, int L, R& frac) {
+  const R s = x / a;
+  const R f = floor(s);
+  frac = s - f;
+  long long c = (long long)f;
+  long long r = c % L;
+  if (r < 0) r += L;
+  return (int)r;
+}
+
+template <class R>
+__device__ __forceinline__ void add_pair_force(const R* __restrict__ sx, int b, int j, const ChainK<R>& C,
+                                               R f[3], bool bonded, unsigned* status) {
+  R d[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    R dd = sx[3 * b + q] - sx[3 * j + q];
+    dd -= C.box * rnd_nearest<R>(dd * C.inv_box);
+    d[q] = dd;
+  }
+  const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  R coef = R(0);
+  if (r2 < C.rc2) {
+    const R s2 = C.sig2 / r2;
+    const R s6 = s2 * s2 * s2;
+    coef += R(24) * C.eps / r2 * (R(2) * s6 * s6 - s6);
+  }
+  if (bonded) {
+    if (r2 >= C.R0sq) {
+      atomicOr(status, ST_FENE);
+    } else {
+      coef -= C.kfene / (R(1) - r2 / C.R0sq);
+    }
+  }
+  f[0] += coef * d[0];
+  f[1] += coef * d[1];
+  f[2] += coef * d[2];
+}
+
+// post-stream populations at node (qx,qy,qz): rho and lattice momentum
+template <class S, class R, bool DEV>
+__device__ __forceinline__ void gather_node(const S* __restrict__ pop, const FluidK<R>& P, int qx, int qy,
+                                            int qz, R mom[4]) {
+  const int L = (int)P.L;
+  R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    int sx = qx - cx(i), sy = qy - cy(i), sz = qz - cz(i);
+    sx = sx < 0 ? sx + L : (sx >= L ? sx - L : sx);
+    sy = sy < 0 ? sy + L : (sy >= L ? sy - L : sy);
+    sz = sz < 0 ? sz + L : (sz >= L ? sz - L : sz);
+    const unsigned idx = (unsigned)sx + (unsigned)L * ((unsigned)sy + (unsigned)L * (unsigned)sz);
+    const R v = ld<S, R>(pop + (unsigned long long)i * P.plane + idx);
+    rho += v;
+    if (cx(i)) jx += R(cx(i)) * v;
+    if (cy(i)) jy += R(cy(i)) * v;
+    if (cz(i)) jz += R(cz(i)) * v;
+  }
+  mom[0] = DEV ? P.rho0 + rho : rho;
+  mom[1] = jx;
+  mom[2] = jy;
+  mom[3] = jz;
+}
+
+template <class S, class R, bool DEV>
+__global__ void __launch_bounds__(512) k_bead_step(const S* __restrict__ pop, const FluidK<R> P,
+                                                    const ChainK<R> C, const uint32_t step) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = C.N;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int L = (int)P.L;
+  const R h = C.h;
+  R* sx = reinterpret_cast<R*>(smem);
+
+  // 1. first half kick and drift: v_half = v + h F/2m, x' = x + h v_half (wrapped)
+  for (int t = tid; t < 3 * N; t += nt) {
+    const R vh = C.v[t] + h * C.F[t] / (R(2) * C.m);
+    R xn = C.x[t] + h * vh;
+    int im = C.img[t];
+    if (xn < R(0)) {
+      xn += C.box;
+      --im;
+    }
+    if (xn >= C.box) {
+      xn -= C.box;
+      ++im;
+    }
+    C.vh[t] = vh;
+    C.x[t] = xn;
+    C.img[t] = im;
+    sx[t] = xn;
+  }
+  __syncthreads();
+
+  // 2. conservative forces at x': FENE on bonds, WCA on all pairs, minimum image
+  for (int b = tid; b < N; b += nt) {
+    R f[3] = {C.ext[0], C.ext[1], C.ext[2]};
+    for (int j = 0; j < N; ++j) {
+      if (j == b) continue;
+      const bool bonded = (j == b - 1) || (j == b + 1);
+      add_pair_force<R>(sx, b, j, C, f, bonded, C.status);
+    }
+    C.fcons[3 * b + 0] = f[0];
+    C.fcons[3 * b + 1] = f[1];
+    C.fcons[3 * b + 2] = f[2];
+  }
+
+  // 3. corners of every bead: cell, trilinear weight, post-stream rho and J at the node
+  for (int e = tid; e < 8 * N; e += nt) {
+    const int b = e >> 3, c = e & 7;
+    const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+    R fr[3];
+    int cl[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) cl[q] = cell_of<R>(sx[3 * b + q], C.a, L, fr[q]);
+    const int qx = (cl[0] + dx) % L, qy = (cl[1] + dy) % L, qz = (cl[2] + dz) % L;
+    const R w = (dx ? fr[0] : R(1) - fr[0]) * (dy ? fr[1] : R(1) - fr[1]) * (dz ? fr[2] : R(1) - fr[2]);
+    R mom[4];
+    gather_node<S, R, DEV>(pop, P, qx, qy, qz, mom);
+    C.e_node[e] = qx + L * (qy + L * qz);
+    C.e_w[e] = w;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) C.e_mom[q * C.cap + e] = mom[q];
+  }
+  __syncthreads();
+
+  // 4. friction + Langevin force, second half kick
+  for (int b = tid; b < N; b += nt) {
+    R ub[3] = {R(0), R(0), R(0)};
+    for (int c = 0; c < 8; ++c) {
+      const int e = 8 * b + c;
+      const R w = C.e_w[e];
+      const R ir = R(1) / C.e_mom[e];
+      ub[0] += w * C.e_mom[1 * C.cap + e] * ir;
+      ub[1] += w * C.e_mom[2 * C.cap + e] * ir;
+      ub[2] += w * C.e_mom[3 * C.cap + e] * ir;
+    }
+    R g[4] = {R(0), R(0), R(0), R(0)};
+    if (C.amp != R(0)) gauss4<R>(step, (uint32_t)b, 0u, C.k0, C.k1, g);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int t = 3 * b + q;
+      const R vh = C.vh[t];
+      const R fc = -C.zeta * (vh - ub[q] * C.u_scale) + C.amp * g[q];
+      const R Ft = C.fcons[t] + fc;
+      C.Fc[t] = fc;
+      C.F[t] = Ft;
+      C.v[t] = vh + h * Ft / (R(2) * C.m);
+    }
+  }
+  __syncthreads();
+
+  // 5. deterministic spreading: sort (node, entry) keys, sum each node's contributions in
+  //    entry order, then turn the node force into population corrections
+  const int ne = 8 * N;
+  int M = 1;
+  while (M < ne) M <<= 1;
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem);
+  for (int i = tid; i < M; i += nt)
+    keys[i] = (i < ne) ? (((unsigned long long)(unsigned)C.e_node[i] << 32) | (unsigned)i) : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= M; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < M; i += nt) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long ka = keys[i], kb = keys[ixj];
+          const bool up = (i & k) == 0;
+          if ((ka > kb) == up) {
+            keys[i] = kb;
+            keys[ixj] = ka;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // leaders: first entry of each node run; slot = number of leaders before it
+  // (serial scan by one warp over chunks: ne <= 8192)
+  int* slot = reinterpret_cast<int*>(keys + M);
+  if (tid < 32) {
+    int base = 0;
+    for (int c0 = 0; c0 < ne; c0 += 32) {
+      const int i = c0 + tid;
+      int lead = 0;
+      if (i < ne) lead = (i == 0) || ((keys[i] >> 32) != (keys[i - 1] >> 32));
+      const unsigned mask = __ballot_sync(0xffffffffu, lead);
+      if (i < ne) slot[i] = lead ? base + __popc(mask & ((1u << tid) - 1u)) : -1;
+      base += __popc(mask);
+    }
+    if (tid == 0) *C.p_count = base;
+  }
+  __syncthreads();
+  for (int i = tid; i < ne; i += nt) {
+    const int u = slot[i];
+    if (u < 0) continue;
+    const int node = (int)(keys[i] >> 32);
+    const int e0 = (int)(keys[i] & 0xffffffffu);
+    R f[3] = {R(0), R(0), R(0)};
+    for (int r = i; r < ne && (int)(keys[r] >> 32) == node; ++r) {
+      const int e = (int)(keys[r] & 0xffffffffu);
+      const R w = C.e_w[e];
+      const int b = e >> 3;
+      f[0] -= w * C.Fc[3 * b + 0] * C.inv_a3;
+      f[1] -= w * C.Fc[3 * b + 1] * C.inv_a3;
+      f[2] -= w * C.Fc[3 * b + 2] * C.inv_a3;
+    }
+    const R rho = C.e_mom[e0], jx = C.e_mom[C.cap + e0], jy = C.e_mom[2 * C.cap + e0],
+            jz = C.e_mom[3 * C.cap + e0];
+    R dJ[3] = {f[0] * C.dJ_scale, f[1] * C.dJ_scale, f[2] * C.dJ_scale};
+    R dm[10];
+    if (P.body_on) {
+      // the LB kernel applies the body-force correction on every node; here add the
+      // difference between the correction for the total force and the body-only one
+      R dmb[10];
+      force_moments(rho, jx, jy, jz, P.body_dJ[0], P.body_dJ[1], P.body_dJ[2], P.gs, P.gb, dmb);
+      force_moments(rho, jx, jy, jz, dJ[0] + P.body_dJ[0], dJ[1] + P.body_dJ[1], dJ[2] + P.body_dJ[2],
+                    P.gs, P.gb, dm);
+#pragma unroll
+      for (int k = 0; k < 10; ++k) dm[k] -= dmb[k];
+    } else {
+      force_moments(rho, jx, jy, jz, dJ[0], dJ[1], dJ[2], P.gs, P.gb, dm);
+    }
+    R dn[Q];
+    dmoments_to_dpops(dm, dn);
+    C.p_node[u] = node;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) C.p_dn[q * C.cap + u] = dn[q];
+  }
+}
+
+// B[i][node] += dn_i at every pending node (each node appears once in the list)
+template <class S, class R>
+__global__ void __launch_bounds__(256) k_apply_pending(S* __restrict__ pop, const FluidK<R> P,
+                                                        const int* __restrict__ p_node,
+                                                        const R* __restrict__ p_dn,
+                                                        const int* __restrict__ p_count, int cap) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= *p_count) return;
+  const unsigned node = (unsigned)p_node[u];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    S* p = pop + (unsigned long long)i * P.plane + node;
+    st<S, R>(p, ld<S, R>(p) + p_dn[i * cap + u]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// initial state, conversions, reductions
+// ---------------------------------------------------------------------------------------
+template <class S, class R, bool DEV>
+__global__ void k_init_rest(S* __restrict__ pop, unsigned long long nnodes, unsigned long long plane, R rho0) {
+  const unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+  if (t >= nnodes) return;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const R v = DEV ? R(0) : rho0 * (R(w36(i)) / R(36));
+    st<S, R>(pop + (unsigned long long)i * plane + t, v);
+  }
+}
+
+// one population plane: full FP64 values <-> storage
+template <class S, class R, bool DEV>
+__global__ void k_plane_from_f64(S* __restrict__ dst, const double* __restrict__ src, unsigned long long n,
+                                 double wrho) {
+  const unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double v = DEV ? src[t] - wrho : src[t];
+  st<S, R>(dst + t, (R)v);
+}
+template <class S, class R, bool DEV>
+__global__ void k_plane_to_f64(double* __restrict__ dst, const S* __restrict__ src, unsigned long long n,
+                               double wrho) {
+  const unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double v = (double)ld<S, R>(src + t);
+  dst[t] = DEV ? v + wrho : v;
+}
+
+// per-block FP64 partial sums of (sum n, Jx, Jy, Jz) of the stored populations
+template <class S, class R, bool DEV>
+__global__ void __launch_bounds__(256) k_fluid_partials(const S* __restrict__ pop, unsigned long long nnodes,
+                                                         unsigned long long plane, double* __restrict__ part) {
+  const unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+  double v[4] = {0, 0, 0, 0};
+  if (t < nnodes) {
+    R r = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R n = ld<S, R>(pop + (unsigned long long)i * plane + t);
+      r += n;
+      if (cx(i)) jx += R(cx(i)) * n;
+      if (cy(i)) jy += R(cy(i)) * n;
+      if (cz(i)) jz += R(cz(i)) * n;
+    }
+    v[0] = (double)r;
+    v[1] = (double)jx;
+    v[2] = (double)jy;
+    v[3] = (double)jz;
+  }
+  __shared__ double sh[4][8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double a = v[q];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double a = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sh[threadIdx.x][w];
+    part[4ull * blockIdx.x + threadIdx.x] = a;
+  }
+}
+
+// observables: fluid sums from the partials, bead quantities from the chain state (FP64)
+template <class R>
+struct ObsK {
+  const double* part;
+  int nparts;
+  double mass_rest;   // rho0 L^3 for deviation storage (0 for full storage)
+  double a3, u_scale;  // a^3, a/h
+  int N;
+  const R* x;
+  const int* img;
+  const R* v;
+  const R* Fc;
+  double box, m, h;
+  const double* xref;  // 3N reference positions
+  double* acc;         // [samples, sum Rg2, sum Re2]
+  const unsigned long long* nonpos;
+  double* out;         // LB_NOBS values
+  long long step;
+  int accumulate;      // 1: add this sample to the accumulators
+};
+
+template <class R>
+__global__ void __launch_bounds__(256) k_observables(const ObsK<R> O) {
+  __shared__ double sh[16][8];
+  const int tid = threadIdx.x;
+  // fluid: fixed-order reduction of the partials
+  double f[4] = {0, 0, 0, 0};
+  for (int p = tid; p < O.nparts; p += blockDim.x)
+    for (int q = 0; q < 4; ++q) f[q] += O.part[4ll * p + q];
+  // beads
+  double cm[3] = {0, 0, 0}, mv[3] = {0, 0, 0}, fc[3] = {0, 0, 0}, v2 = 0;
+  for (int b = tid; b < O.N; b += blockDim.x) {
+    for (int q = 0; q < 3; ++q) {
+      const double xu = (double)O.x[3 * b + q] + (double)O.img[3 * b + q] * O.box;
+      cm[q] += xu;
+      const double vv = (double)O.v[3 * b + q];
+      mv[q] += O.m * vv;
+      v2 += vv * vv;
+      fc[q] += (double)O.Fc[3 * b + q];
+    }
+  }
+  double vals[14] = {f[0], f[1], f[2], f[3], cm[0], cm[1], cm[2], mv[0], mv[1], mv[2], fc[0], fc[1], fc[2], v2};
+  for (int q = 0; q < 14; ++q) {
+    double a = vals[q];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if ((tid & 31) == 0) sh[q][tid >> 5] = a;
+  }
+  __syncthreads();
+  __shared__ double tot[14];
+  if (tid < 14) {
+    double a = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sh[tid][w];
+    tot[tid] = a;
+  }
+  __syncthreads();
+  // second pass: R_g^2 about the centre of mass, R_e^2, MSDs
+  const int N = O.N;
+  double rg = 0;
+  for (int b = tid; b < N; b += blockDim.x) {
+    for (int q = 0; q < 3; ++q) {
+      const double xu = (double)O.x[3 * b + q] + (double)O.img[3 * b + q] * O.box;
+      const double d = xu - tot[4 + q] / N;
+      rg += d * d;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) rg += __shfl_down_sync(0xffffffffu, rg, o);
+  __syncthreads();
+  if ((tid & 31) == 0) sh[15][tid >> 5] = rg;
+  __syncthreads();
+  if (tid == 0) {
+    double rgt = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) rgt += sh[15][w];
+    double* o = O.out;
+    o[0] = (double)O.step;
+    o[1] = (O.mass_rest + tot[0]) * O.a3;
+    const double s = O.u_scale * O.a3;
+    o[5] = tot[1] * s;
+    o[6] = tot[2] * s;
+    o[7] = tot[3] * s;
+    o[2] = o[5] + tot[7] + 0.5 * O.h * tot[10];
+    o[3] = o[6] + tot[8] + 0.5 * O.h * tot[11];
+    o[4] = o[7] + tot[9] + 0.5 * O.h * tot[12];
+    double Rg2 = 0, Re2 = 0, g1 = 0, g3 = 0;
+    if (N > 0) {
+      Rg2 = rgt / N;
+      double cmr[3] = {0, 0, 0};
+      for (int b = 0; b < N; ++b)
+        for (int q = 0; q < 3; ++q) cmr[q] += O.xref[3 * b + q];
+      const int i0 = (N - 1) / 2, i1 = N / 2;
+      for (int q = 0; q < 3; ++q) {
+        const double xe = (double)O.x[3 * (N - 1) + q] + (double)O.img[3 * (N - 1) + q] * O.box;
+        const double xs = (double)O.x[q] + (double)O.img[q] * O.box;
+        Re2 += (xe - xs) * (xe - xs);
+        const double a0 = (double)O.x[3 * i0 + q] + (double)O.img[3 * i0 + q] * O.box - O.xref[3 * i0 + q];
+        const double a1 = (double)O.x[3 * i1 + q] + (double)O.img[3 * i1 + q] * O.box - O.xref[3 * i1 + q];
+        g1 += 0.5 * (a0 * a0 + a1 * a1);
+        const double dc = (tot[4 + q] - cmr[q]) / N;
+        g3 += dc * dc;
+      }
+      o[10] = tot[4] / N;
+      o[11] = tot[5] / N;
+      o[12] = tot[6] / N;
+      o[15] = O.m * tot[13] / (3.0 * N);
+    } else {
+      o[10] = o[11] = o[12] = 0;
+      o[15] = 0;
+    }
+    o[8] = Rg2;
+    o[9] = Re2;
+    o[13] = g1;
+    o[14] = g3;
+    o[16] = (double)*O.nonpos;
+    if (O.accumulate) {
+      O.acc[0] += 1.0;
+      O.acc[1] += Rg2;
+      O.acc[2] += Re2;
+    }
+    o[17] = O.acc[0];
+    o[18] = O.acc[0] > 0 ? O.acc[1] / O.acc[0] : 0.0;
+    o[19] = O.acc[0] > 0 ? O.acc[2] / O.acc[0] : 0.0;
+  }
+}
+
+}  // namespace gblb
+
+namespace gblb {
+
+// Forces of the initial configuration: F = F_cons(x0) (+ external), F_c = 0.
+template <class R>
+__global__ void __launch_bounds__(256) k_chain_init_forces(const ChainK<R> C) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  R* sx = reinterpret_cast<R*>(smem);
+  const int N = C.N;
+  for (int t = threadIdx.x; t < 3 * N; t += blockDim.x) sx[t] = C.x[t];
+  __syncthreads();
+  for (int b = threadIdx.x; b < N; b += blockDim.x) {
+    R f[3] = {C.ext[0], C.ext[1], C.ext[2]};
+    for (int j = 0; j < N; ++j) {
+      if (j == b) continue;
+      add_pair_force<R>(sx, b, j, C, f, (j == b - 1) || (j == b + 1), C.status);
+    }
+    for (int q = 0; q < 3; ++q) {
+      C.F[3 * b + q] = f[q];
+      C.Fc[3 * b + q] = R(0);
+    }
+  }
+}
+
+}  // namespace gblb

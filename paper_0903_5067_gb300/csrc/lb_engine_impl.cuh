@@ -1,0 +1,402 @@
+// Engine implementation, templated on the population storage type S, the arithmetic type
+// R and whether populations are stored as deviations from w_i rho0 (DEV).
+#pragma once
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "lb_device.cuh"
+#include "lb_engine.h"
+
+namespace gblb {
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+template <class S, class R, bool DEV>
+class EngineT final : public Engine {
+ public:
+  explicit EngineT(const Config& c) : cfg_(c) {
+    L_ = c.L;
+    nnodes_ = (unsigned long long)L_ * L_ * L_;
+    plane_ = align_up(nnodes_, 64);
+    N_ = c.N;
+    cap_ = 8 * (N_ > 0 ? N_ : 1);
+    nparts_ = (int)((nnodes_ + 255) / 256);
+    layout(nullptr);
+  }
+
+  size_t workspace_bytes() const override { return bytes_; }
+
+  void bind(void* base) override { layout(static_cast<unsigned char*>(base)); }
+
+  void set_config(const Config& c) override { cfg_ = c; }
+
+  void initialise(const double* x0, const double* v0, cudaStream_t s) override {
+    if (bead_smem() > 48 * 1024)
+      cuda_check(cudaFuncSetAttribute(k_bead_step<S, R, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)bead_smem()),
+                 "bead kernel shared memory");
+    const unsigned long long nb = (nnodes_ + 255) / 256;
+    k_init_rest<S, R, DEV><<<(unsigned)nb, 256, 0, s>>>(pop_[0], nnodes_, plane_, (R)cfg_.rho);
+    cuda_check(cudaGetLastError(), "init populations");
+    cur_ = 0;
+    cuda_check(cudaMemsetAsync(status_, 0, sizeof(unsigned), s), "memset status");
+    cuda_check(cudaMemsetAsync(nonpos_, 0, sizeof(unsigned long long), s), "memset counter");
+    cuda_check(cudaMemsetAsync(acc_, 0, 4 * sizeof(double), s), "memset accumulators");
+    if (N_ > 0) {
+      const double box = cfg_.L * cfg_.a;
+      std::vector<R> xw(3 * N_), vv(3 * N_);
+      std::vector<int> im(3 * N_);
+      for (int t = 0; t < 3 * N_; ++t) {
+        const double xu = x0[t];
+        double k = floor(xu / box);
+        double xr = xu - k * box;
+        R xs = (R)xr;
+        if (xs >= (R)box) {
+          xs = (R)0;
+          k += 1;
+        }
+        if (xs < (R)0) xs = (R)0;
+        xw[t] = xs;
+        im[t] = (int)k;
+        vv[t] = v0 ? (R)v0[t] : (R)0;
+      }
+      cuda_check(cudaMemcpyAsync(x_, xw.data(), 3 * N_ * sizeof(R), cudaMemcpyHostToDevice, s), "upload x");
+      cuda_check(cudaMemcpyAsync(img_, im.data(), 3 * N_ * sizeof(int), cudaMemcpyHostToDevice, s), "upload img");
+      cuda_check(cudaMemcpyAsync(v_, vv.data(), 3 * N_ * sizeof(R), cudaMemcpyHostToDevice, s), "upload v");
+      cuda_check(cudaMemcpyAsync(xref_, x0, 3 * N_ * sizeof(double), cudaMemcpyHostToDevice, s), "upload xref");
+      cuda_check(cudaStreamSynchronize(s), "sync upload");
+      const ChainK<R> C = chain();
+      k_chain_init_forces<R><<<1, 256, 3 * N_ * sizeof(R), s>>>(C);
+      cuda_check(cudaGetLastError(), "init forces");
+    }
+    cuda_check(cudaMemsetAsync(p_count_, 0, sizeof(int), s), "memset pending");
+  }
+
+  void step(uint32_t k, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) override {
+    const FluidK<R> P = fluid();
+    const S* A = pop_[cur_];
+    S* Bo = pop_[cur_ ^ 1];
+    if (N_ > 0) {
+      const ChainK<R> C = chain();
+      k_bead_step<S, R, DEV><<<1, 512, bead_smem(), s>>>(A, P, C, k);
+      cuda_check(cudaGetLastError(), "bead kernel");
+    }
+    dim3 blk, grd;
+    lb_launch_shape(blk, grd);
+    if (ev0) cudaEventRecord(ev0, s);
+    if (P.ncalls > 0)
+      k_lb_step<S, R, DEV, true><<<grd, blk, 0, s>>>(A, Bo, P, k);
+    else
+      k_lb_step<S, R, DEV, false><<<grd, blk, 0, s>>>(A, Bo, P, k);
+    if (ev1) cudaEventRecord(ev1, s);
+    cuda_check(cudaGetLastError(), "LB kernel");
+    if (N_ > 0) {
+      k_apply_pending<S, R><<<(cap_ + 255) / 256, 256, 0, s>>>(Bo, P, p_node_, p_dn_, p_count_, cap_);
+      cuda_check(cudaGetLastError(), "apply kernel");
+    }
+    cur_ ^= 1;
+  }
+
+  void get_populations(double* out, cudaStream_t s) override {
+    double* stage = reinterpret_cast<double*>(pop_[cur_ ^ 1]);
+    const unsigned nb = (unsigned)((nnodes_ + 255) / 256);
+    for (int i = 0; i < Q; ++i) {
+      const double wr = cfg_.rho * (double)w36(i) / 36.0;
+      k_plane_to_f64<S, R, DEV><<<nb, 256, 0, s>>>(stage, pop_[cur_] + (size_t)i * plane_, nnodes_, wr);
+      cuda_check(cudaGetLastError(), "plane to f64");
+      cuda_check(cudaMemcpyAsync(out + (size_t)i * nnodes_, stage, nnodes_ * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s),
+                 "download plane");
+    }
+    cuda_check(cudaStreamSynchronize(s), "sync download");
+  }
+
+  void set_populations(const double* in, cudaStream_t s) override {
+    double* stage = reinterpret_cast<double*>(pop_[cur_ ^ 1]);
+    const unsigned nb = (unsigned)((nnodes_ + 255) / 256);
+    for (int i = 0; i < Q; ++i) {
+      const double wr = cfg_.rho * (double)w36(i) / 36.0;
+      cuda_check(cudaMemcpyAsync(stage, in + (size_t)i * nnodes_, nnodes_ * sizeof(double),
+                                 cudaMemcpyHostToDevice, s),
+                 "upload plane");
+      k_plane_from_f64<S, R, DEV><<<nb, 256, 0, s>>>(pop_[cur_] + (size_t)i * plane_, stage, nnodes_, wr);
+      cuda_check(cudaGetLastError(), "plane from f64");
+    }
+    cuda_check(cudaMemsetAsync(p_count_, 0, sizeof(int), s), "memset pending");
+    cuda_check(cudaStreamSynchronize(s), "sync upload");
+  }
+
+  void get_beads(double* x, double* v, cudaStream_t s) override {
+    if (N_ == 0) return;
+    std::vector<R> xw(3 * N_), vv(3 * N_);
+    std::vector<int> im(3 * N_);
+    cuda_check(cudaMemcpyAsync(xw.data(), x_, 3 * N_ * sizeof(R), cudaMemcpyDeviceToHost, s), "dl x");
+    cuda_check(cudaMemcpyAsync(im.data(), img_, 3 * N_ * sizeof(int), cudaMemcpyDeviceToHost, s), "dl img");
+    cuda_check(cudaMemcpyAsync(vv.data(), v_, 3 * N_ * sizeof(R), cudaMemcpyDeviceToHost, s), "dl v");
+    cuda_check(cudaStreamSynchronize(s), "sync beads");
+    const double box = cfg_.L * cfg_.a;
+    for (int t = 0; t < 3 * N_; ++t) {
+      if (x) x[t] = (double)xw[t] + (double)im[t] * box;
+      if (v) v[t] = (double)vv[t];
+    }
+  }
+
+  void observables(double* out, int64_t step, int accumulate, cudaStream_t s) override {
+    ObsK<R> O = obs(step, accumulate);
+    if (!accumulate) {
+      k_fluid_partials<S, R, DEV><<<nparts_, 256, 0, s>>>(pop_[cur_], nnodes_, plane_, parts_);
+      cuda_check(cudaGetLastError(), "fluid partials");
+      O.nparts = nparts_;
+    }
+    k_observables<R><<<1, 256, 0, s>>>(O);
+    cuda_check(cudaGetLastError(), "observables");
+    if (out) {
+      cuda_check(cudaMemcpyAsync(out, obs_, kNObs * sizeof(double), cudaMemcpyDeviceToHost, s), "dl obs");
+      cuda_check(cudaStreamSynchronize(s), "sync obs");
+    }
+  }
+
+  void reset_reference(cudaStream_t s) override {
+    if (N_ == 0) return;
+    std::vector<double> xu(3 * N_);
+    get_beads(xu.data(), nullptr, s);
+    cuda_check(cudaMemcpyAsync(xref_, xu.data(), 3 * N_ * sizeof(double), cudaMemcpyHostToDevice, s), "xref");
+    cuda_check(cudaMemsetAsync(acc_, 0, 4 * sizeof(double), s), "acc");
+    cuda_check(cudaStreamSynchronize(s), "sync ref");
+  }
+
+  unsigned read_status(cudaStream_t s) override {
+    unsigned st = 0;
+    cuda_check(cudaMemcpyAsync(&st, status_, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "status");
+    cuda_check(cudaStreamSynchronize(s), "sync status");
+    return st;
+  }
+
+  // checkpoint: populations (storage type, L^3 per plane), bead arrays, xref, acc, counter
+  size_t state_bytes() const override {
+    return 19 * nnodes_ * sizeof(S) + (size_t)N_ * 3 * (4 * sizeof(R) + sizeof(int) + sizeof(double)) +
+           4 * sizeof(double) + sizeof(unsigned long long);
+  }
+  void save_state(void* host, cudaStream_t s) override {
+    unsigned char* p = static_cast<unsigned char*>(host);
+    for (int i = 0; i < Q; ++i) {
+      cuda_check(cudaMemcpyAsync(p, pop_[cur_] + (size_t)i * plane_, nnodes_ * sizeof(S), cudaMemcpyDeviceToHost, s),
+                 "save pop");
+      p += nnodes_ * sizeof(S);
+    }
+    p = copy_beads(p, true, s);
+    cuda_check(cudaStreamSynchronize(s), "sync save");
+  }
+  void load_state(const void* host, cudaStream_t s) override {
+    unsigned char* p = const_cast<unsigned char*>(static_cast<const unsigned char*>(host));
+    for (int i = 0; i < Q; ++i) {
+      cuda_check(cudaMemcpyAsync(pop_[cur_] + (size_t)i * plane_, p, nnodes_ * sizeof(S), cudaMemcpyHostToDevice, s),
+                 "load pop");
+      p += nnodes_ * sizeof(S);
+    }
+    p = copy_beads(p, false, s);
+    cuda_check(cudaMemsetAsync(p_count_, 0, sizeof(int), s), "memset pending");
+    cuda_check(cudaStreamSynchronize(s), "sync load");
+  }
+
+ private:
+  unsigned char* copy_beads(unsigned char* p, bool save, cudaStream_t s) {
+    auto mv = [&](void* dev, size_t bytes) {
+      if (bytes == 0) return;
+      if (save)
+        cuda_check(cudaMemcpyAsync(p, dev, bytes, cudaMemcpyDeviceToHost, s), "save state");
+      else
+        cuda_check(cudaMemcpyAsync(dev, p, bytes, cudaMemcpyHostToDevice, s), "load state");
+      p += bytes;
+    };
+    const size_t n3 = 3 * (size_t)N_;
+    mv(x_, n3 * sizeof(R));
+    mv(img_, n3 * sizeof(int));
+    mv(v_, n3 * sizeof(R));
+    mv(F_, n3 * sizeof(R));
+    mv(Fc_, n3 * sizeof(R));
+    mv(xref_, n3 * sizeof(double));
+    mv(acc_, 4 * sizeof(double));
+    mv(nonpos_, sizeof(unsigned long long));
+    return p;
+  }
+
+  void lb_launch_shape(dim3& blk, dim3& grd) const {
+    unsigned bx = ((unsigned)L_ + 31) / 32 * 32;
+    if (bx > 256) bx = 256;
+    const unsigned by = 256 / bx;
+    blk = dim3(bx, by, 1);
+    grd = dim3(((unsigned)L_ + bx - 1) / bx, ((unsigned)L_ + by - 1) / by, (unsigned)L_);
+  }
+
+  size_t bead_smem() const {
+    const size_t ne = 8 * (size_t)N_;
+    size_t M = 1;
+    while (M < ne) M <<= 1;
+    const size_t sortb = M * 8 + ne * 4;
+    const size_t posb = 3 * (size_t)N_ * sizeof(R);
+    return sortb > posb ? sortb : posb;
+  }
+
+  FluidK<R> fluid() const {
+    FluidK<R> P;
+    memset(&P, 0, sizeof(P));
+    const Config& c = cfg_;
+    P.L = (unsigned)L_;
+    P.plane = plane_;
+    P.rho0 = (R)c.rho;
+    const double nu = c.eta * c.h / (c.rho * c.a * c.a);
+    const double nub = c.eta_b * c.h / (c.rho * c.a * c.a);
+    const double gs = 1.0 - 2.0 / (6.0 * nu + 1.0);
+    const double gb = 1.0 - 2.0 / (9.0 * nub + 1.0);
+    P.gs = (R)gs;
+    P.gb = (R)gb;
+    const bool noise = c.noise_fluid && c.kT > 0.0;
+    P.ncalls = noise ? (c.stress_only ? 2 : 4) : 0;
+    const double mu = 3.0 * c.kT * c.h * c.h / pow(c.a, 5);
+    for (int k = 0; k < Q; ++k) {
+      double g = 0.0;
+      if (k == 4) g = gb;
+      if (k >= 5 && k <= 9) g = gs;
+      const double bk = norm36(k) / 36.0;
+      const bool on = noise && k >= 4 && (k <= 9 || !c.stress_only);
+      P.cnoise[k] = on ? (R)sqrt(mu * bk * (1.0 - g * g)) : (R)0;
+    }
+    P.k0 = (uint32_t)(c.seed & 0xffffffffu);
+    P.k1 = (uint32_t)(0u | ((uint32_t)c.replica << 8));
+    double body[3] = {0, 0, 0};
+    if (c.counter_force && c.N > 0) {
+      const double vol = pow(c.L * c.a, 3);
+      for (int q = 0; q < 3; ++q) body[q] = -c.N * c.ext[q] / vol;
+    }
+    P.body_on = (body[0] != 0 || body[1] != 0 || body[2] != 0) ? 1 : 0;
+    for (int q = 0; q < 3; ++q) P.body_dJ[q] = (R)(body[q] * c.h * c.h / c.a);
+    P.nonpos = nonpos_;
+    return P;
+  }
+
+  ChainK<R> chain() const {
+    ChainK<R> C;
+    memset(&C, 0, sizeof(C));
+    const Config& c = cfg_;
+    C.N = N_;
+    C.m = (R)c.m;
+    C.zeta = (R)c.zeta;
+    C.kfene = (R)c.kfene;
+    C.R0sq = (R)(c.R0 * c.R0);
+    C.eps = (R)c.eps;
+    C.sig2 = (R)(c.sigma * c.sigma);
+    C.rc2 = (R)(pow(2.0, 1.0 / 3.0) * c.sigma * c.sigma);
+    C.h = (R)c.h;
+    C.a = (R)c.a;
+    C.box = (R)(c.L * c.a);
+    C.inv_box = (R)(1.0 / (c.L * c.a));
+    const bool noise = c.noise_beads && c.kT > 0.0;
+    C.amp = noise ? (R)sqrt(2.0 * c.kT * c.zeta / c.h) : (R)0;
+    C.k0 = (uint32_t)(c.seed & 0xffffffffu);
+    C.k1 = (uint32_t)(1u | ((uint32_t)c.replica << 8));
+    for (int q = 0; q < 3; ++q) C.ext[q] = (R)c.ext[q];
+    C.u_scale = (R)(c.a / c.h);
+    C.inv_a3 = (R)(1.0 / (c.a * c.a * c.a));
+    C.dJ_scale = (R)(c.h * c.h / c.a);
+    C.x = x_;
+    C.img = img_;
+    C.v = v_;
+    C.F = F_;
+    C.Fc = Fc_;
+    C.vh = vh_;
+    C.fcons = fcons_;
+    C.e_node = e_node_;
+    C.e_w = e_w_;
+    C.e_mom = e_mom_;
+    C.p_node = p_node_;
+    C.p_dn = p_dn_;
+    C.p_count = p_count_;
+    C.cap = cap_;
+    C.status = status_;
+    return C;
+  }
+
+  ObsK<R> obs(int64_t step, int accumulate) const {
+    ObsK<R> O;
+    memset(&O, 0, sizeof(O));
+    const Config& c = cfg_;
+    O.part = parts_;
+    O.nparts = 0;
+    O.mass_rest = DEV ? c.rho * (double)nnodes_ : 0.0;
+    O.a3 = c.a * c.a * c.a;
+    O.u_scale = c.a / c.h;
+    O.N = N_;
+    O.x = x_;
+    O.img = img_;
+    O.v = v_;
+    O.Fc = Fc_;
+    O.box = c.L * c.a;
+    O.m = c.m;
+    O.h = c.h;
+    O.xref = xref_;
+    O.acc = acc_;
+    O.nonpos = nonpos_;
+    O.out = obs_;
+    O.step = step;
+    O.accumulate = accumulate;
+    return O;
+  }
+
+  // carve the workspace; with base == nullptr only computes the size
+  void layout(unsigned char* base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> unsigned char* {
+      off = align_up(off, 256);
+      unsigned char* p = base ? base + off : nullptr;
+      off += bytes;
+      return p;
+    };
+    const size_t popb = Q * plane_ * sizeof(S);
+    pop_[0] = reinterpret_cast<S*>(take(popb));
+    pop_[1] = reinterpret_cast<S*>(take(popb));
+    const size_t n3 = 3 * (size_t)(N_ > 0 ? N_ : 1);
+    x_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
+    img_ = reinterpret_cast<int*>(take(n3 * sizeof(int)));
+    v_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
+    F_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
+    Fc_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
+    vh_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
+    fcons_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
+    xref_ = reinterpret_cast<double*>(take(n3 * sizeof(double)));
+    e_node_ = reinterpret_cast<int*>(take(cap_ * sizeof(int)));
+    e_w_ = reinterpret_cast<R*>(take(cap_ * sizeof(R)));
+    e_mom_ = reinterpret_cast<R*>(take(4 * cap_ * sizeof(R)));
+    p_node_ = reinterpret_cast<int*>(take(cap_ * sizeof(int)));
+    p_dn_ = reinterpret_cast<R*>(take((size_t)Q * cap_ * sizeof(R)));
+    p_count_ = reinterpret_cast<int*>(take(sizeof(int)));
+    status_ = reinterpret_cast<unsigned*>(take(sizeof(unsigned)));
+    nonpos_ = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long)));
+    acc_ = reinterpret_cast<double*>(take(4 * sizeof(double)));
+    obs_ = reinterpret_cast<double*>(take(kNObs * sizeof(double)));
+    parts_ = reinterpret_cast<double*>(take(4 * (size_t)nparts_ * sizeof(double)));
+    bytes_ = align_up(off, 256);
+  }
+
+  Config cfg_;
+  int L_ = 0, N_ = 0, cap_ = 8, nparts_ = 0;
+  unsigned long long nnodes_ = 0, plane_ = 0;
+  size_t bytes_ = 0;
+  int cur_ = 0;
+  S* pop_[2] = {nullptr, nullptr};
+  R *x_ = nullptr, *v_ = nullptr, *F_ = nullptr, *Fc_ = nullptr, *vh_ = nullptr, *fcons_ = nullptr;
+  int* img_ = nullptr;
+  double* xref_ = nullptr;
+  int* e_node_ = nullptr;
+  R *e_w_ = nullptr, *e_mom_ = nullptr;
+  int* p_node_ = nullptr;
+  R* p_dn_ = nullptr;
+  int* p_count_ = nullptr;
+  unsigned* status_ = nullptr;
+  unsigned long long* nonpos_ = nullptr;
+  double *acc_ = nullptr, *obs_ = nullptr, *parts_ = nullptr;
+};
+
+}  // namespace gblb

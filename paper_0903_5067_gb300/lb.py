@@ -1,0 +1,264 @@
+"""ctypes binding of libgblb (C ABI in include/lb.h).
+
+Functions keep the C names and only marshal arguments; every numerical step runs in the
+CUDA library.  ``Simulation`` is a convenience wrapper that binds a torch-owned device
+workspace and torch's current stream to a context.  Importing this module raises if the
+library has not been built (``python -c "import __graft_entry__ as g; g.build()"``): there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libgblb.so")
+if not os.path.exists(_LIBPATH):
+    raise ImportError(f"{_LIBPATH} is missing: build it with __graft_entry__.build() (needs nvcc)")
+_lib = C.CDLL(_LIBPATH)
+
+LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_OOM, LB_ERR_FENE, LB_ERR_NONFINITE, LB_ERR_TIMEOUT, LB_ERR_STATE = range(8)
+LB_FP64, LB_FP32, LB_BF16, LB_FP16 = range(4)
+LB_NOBS = 20
+
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+_SIGS = {
+    "lb_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                            C.c_double, C.c_double, C.c_uint64, C.c_int]),
+    "lb_add_chain": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                               C.c_double, _dp, _dp, C.c_double, C.c_int]),
+    "lb_set_options": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _dp, C.c_int]),
+    "lb_set_stream": (C.c_int, [_vp, _vp]),
+    "lb_workspace_size": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
+    "lb_bind_workspace": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "lb_step": (C.c_int, [_vp, C.c_int64]),
+    "lb_sync": (C.c_int, [_vp]),
+    "lb_get_populations": (C.c_int, [_vp, _dp, C.c_size_t]),
+    "lb_set_populations": (C.c_int, [_vp, _dp, C.c_size_t]),
+    "lb_get_beads": (C.c_int, [_vp, _dp, _dp, C.c_size_t]),
+    "lb_get_observables": (C.c_int, [_vp, _dp, C.c_size_t]),
+    "lb_set_obs_stride": (C.c_int, [_vp, C.c_int]),
+    "lb_reset_reference": (C.c_int, [_vp]),
+    "lb_save": (C.c_int, [_vp, C.c_char_p]),
+    "lb_load": (C.c_int, [_vp, C.c_char_p]),
+    "lb_get_step": (C.c_int64, [_vp]),
+    "lb_set_timing": (C.c_int, [_vp, C.c_int]),
+    "lb_get_timing": (C.c_int, [_vp, _dp, C.POINTER(C.c_int64)]),
+    "lb_destroy": (None, [_vp]),
+    "lb_strerror": (C.c_char_p, [C.c_int]),
+    "lb_philox4x32_10": (C.c_int, [_vp, C.c_int64, C.c_uint32, C.c_uint32, _vp, _vp]),
+    "lb_cell_index_f32": (C.c_int, [_vp, C.c_int64, C.c_float, C.c_int, _vp, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+class LBError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {lb_strerror(code)} (status {code})")
+        self.code = code
+
+
+def _check(code: int, where: str) -> None:
+    if code != LB_OK:
+        raise LBError(code, where)
+
+
+def _dbuf(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+# --- C functions, same names -----------------------------------------------------------
+def lb_strerror(code: int) -> str:
+    return _lib.lb_strerror(code).decode()
+
+
+def lb_create(L, rho, eta, eta_b, kT, h, a, seed, precision):
+    ctx = _vp()
+    _check(_lib.lb_create(C.byref(ctx), int(L), rho, eta, eta_b, kT, h, a, int(seed), int(precision)), "lb_create")
+    return ctx
+
+
+def lb_add_chain(ctx, N, m, zeta, k_fene, R0, eps, sigma, x0=None, v0=None, bond=0.97, saw=1):
+    x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).reshape(-1)
+    v0 = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float64).reshape(-1)
+    _check(_lib.lb_add_chain(ctx, int(N), m, zeta, k_fene, R0, eps, sigma, _dbuf(x0), _dbuf(v0), bond, int(saw)),
+           "lb_add_chain")
+
+
+def lb_set_options(ctx, noise_fluid=1, noise_beads=1, stress_only=0, ext_bead_force=None, counter_force_fluid=0):
+    ext = None if ext_bead_force is None else np.ascontiguousarray(ext_bead_force, dtype=np.float64)
+    _check(_lib.lb_set_options(ctx, int(noise_fluid), int(noise_beads), int(stress_only), _dbuf(ext),
+                               int(counter_force_fluid)), "lb_set_options")
+
+
+def lb_set_stream(ctx, stream_handle: int):
+    _check(_lib.lb_set_stream(ctx, _vp(stream_handle) if stream_handle else None), "lb_set_stream")
+
+
+def lb_workspace_size(ctx) -> int:
+    n = C.c_size_t()
+    _check(_lib.lb_workspace_size(ctx, C.byref(n)), "lb_workspace_size")
+    return n.value
+
+
+def lb_bind_workspace(ctx, device_ptr: int, nbytes: int):
+    _check(_lib.lb_bind_workspace(ctx, _vp(device_ptr), nbytes), "lb_bind_workspace")
+
+
+def lb_step(ctx, n: int):
+    _check(_lib.lb_step(ctx, int(n)), "lb_step")
+
+
+def lb_sync(ctx):
+    _check(_lib.lb_sync(ctx), "lb_sync")
+
+
+def lb_get_populations(ctx, out: np.ndarray):
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _check(_lib.lb_get_populations(ctx, _dbuf(out), out.size), "lb_get_populations")
+
+
+def lb_set_populations(ctx, arr: np.ndarray):
+    arr = np.ascontiguousarray(arr, dtype=np.float64)
+    _check(_lib.lb_set_populations(ctx, _dbuf(arr), arr.size), "lb_set_populations")
+
+
+def lb_get_beads(ctx, x: np.ndarray | None, v: np.ndarray | None, cap: int):
+    _check(_lib.lb_get_beads(ctx, _dbuf(x), _dbuf(v), cap), "lb_get_beads")
+
+
+def lb_get_observables(ctx) -> np.ndarray:
+    out = np.zeros(LB_NOBS)
+    _check(_lib.lb_get_observables(ctx, _dbuf(out), out.size), "lb_get_observables")
+    return out
+
+
+def lb_set_obs_stride(ctx, stride: int):
+    _check(_lib.lb_set_obs_stride(ctx, int(stride)), "lb_set_obs_stride")
+
+
+def lb_reset_reference(ctx):
+    _check(_lib.lb_reset_reference(ctx), "lb_reset_reference")
+
+
+def lb_save(ctx, path: str):
+    _check(_lib.lb_save(ctx, path.encode()), "lb_save")
+
+
+def lb_load(ctx, path: str):
+    _check(_lib.lb_load(ctx, path.encode()), "lb_load")
+
+
+def lb_get_step(ctx) -> int:
+    return int(_lib.lb_get_step(ctx))
+
+
+def lb_set_timing(ctx, enable: bool):
+    _check(_lib.lb_set_timing(ctx, int(enable)), "lb_set_timing")
+
+
+def lb_get_timing(ctx):
+    ms = C.c_double()
+    n = C.c_int64()
+    _check(_lib.lb_get_timing(ctx, C.byref(ms), C.byref(n)), "lb_get_timing")
+    return ms.value, n.value
+
+
+def lb_destroy(ctx):
+    _lib.lb_destroy(ctx)
+
+
+def lb_philox4x32_10(ctr_dev_ptr: int, n: int, k0: int, k1: int, out_dev_ptr: int, stream: int = 0):
+    _check(_lib.lb_philox4x32_10(_vp(ctr_dev_ptr), n, k0, k1, _vp(out_dev_ptr), _vp(stream) if stream else None),
+           "lb_philox4x32_10")
+
+
+def lb_cell_index_f32(x_dev_ptr: int, n: int, a: float, L: int, out_dev_ptr: int, stream: int = 0):
+    _check(_lib.lb_cell_index_f32(_vp(x_dev_ptr), n, a, L, _vp(out_dev_ptr), _vp(stream) if stream else None),
+           "lb_cell_index_f32")
+
+
+# --- convenience wrapper ---------------------------------------------------------------
+class Simulation:
+    """One fluid box (+ optional chain) on the current CUDA device, with its workspace in a
+    torch tensor and its work on torch's current stream."""
+
+    def __init__(self, L, rho=1.0, eta=3.0, eta_b=3.0, kT=1.0, h=0.01, a=1.0, seed=1, precision=LB_FP32,
+                 torch_workspace=True):
+        self.L = int(L)
+        self.N = 0
+        self.ctx = lb_create(L, rho, eta, eta_b, kT, h, a, seed, precision)
+        self._ws = None
+        self._torch_workspace = torch_workspace
+        self._bound = False
+
+    def add_chain(self, N, m=1.0, zeta=20.8, k_fene=30.0, R0=1.5, eps=1.0, sigma=1.0, x0=None, v0=None,
+                  bond=0.97, saw=1):
+        lb_add_chain(self.ctx, N, m, zeta, k_fene, R0, eps, sigma, x0, v0, bond, saw)
+        self.N = int(N)
+
+    def set_options(self, **kw):
+        lb_set_options(self.ctx, **kw)
+
+    def _bind(self):
+        if self._bound:
+            return
+        import torch
+
+        lb_set_stream(self.ctx, torch.cuda.current_stream().cuda_stream)
+        if self._torch_workspace:
+            nbytes = lb_workspace_size(self.ctx)
+            self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            lb_bind_workspace(self.ctx, self._ws.data_ptr(), nbytes)
+        self._bound = True
+
+    def step(self, n=1):
+        self._bind()
+        lb_step(self.ctx, n)
+
+    def sync(self):
+        self._bind()
+        lb_sync(self.ctx)
+
+    def populations(self) -> np.ndarray:
+        self._bind()
+        out = np.empty((19, self.L, self.L, self.L))
+        lb_get_populations(self.ctx, out)
+        return out
+
+    def set_populations(self, arr):
+        self._bind()
+        lb_set_populations(self.ctx, arr)
+
+    def beads(self):
+        self._bind()
+        x = np.empty((self.N, 3))
+        v = np.empty((self.N, 3))
+        lb_get_beads(self.ctx, x, v, 3 * self.N)
+        return x, v
+
+    def observables(self) -> np.ndarray:
+        self._bind()
+        return lb_get_observables(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            lb_destroy(self.ctx)
+            self.ctx = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,91 @@
+"""The C ABI on the host: the library loads, exports every entry point include/lb.h
+declares, and validates its arguments; the host-side chain generator.  None of these calls
+touches a GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            text = open(os.path.join(inc, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(lb_\w+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol(lblib):
+    names = _declared()
+    assert {"lb_create", "lb_add_chain", "lb_step", "lb_get_populations", "lb_get_beads"} <= names
+    for n in names:
+        assert hasattr(lblib._lib, n), n
+
+
+def test_create_validates_arguments(lblib):
+    bad = [dict(L=3), dict(rho=0.0), dict(eta=-1.0), dict(eta_b=0.0), dict(kT=-1.0), dict(h=0.0),
+           dict(a=0.0), dict(precision=7)]
+    base = dict(L=8, rho=1.0, eta=3.0, eta_b=3.0, kT=1.0, h=0.01, a=1.0, seed=1, precision=lblib.LB_FP32)
+    for b in bad:
+        kw = dict(base, **b)
+        with pytest.raises(lblib.LBError) as ei:
+            lblib.lb_create(**kw)
+        assert ei.value.code == lblib.LB_ERR_ARG, b
+    ctx = lblib.lb_create(**base)
+    lblib.lb_destroy(ctx)
+
+
+def test_add_chain_validates_and_generates(lblib):
+    ctx = lblib.lb_create(16, 1.0, 3.0, 3.0, 1.0, 0.01, 1.0, 7, lblib.LB_FP32)
+    try:
+        for kw in (dict(N=0), dict(N=1025), dict(N=4, m=0.0), dict(N=4, R0=-1.0)):
+            args = dict(N=4, m=1.0, zeta=20.8, k_fene=30.0, R0=1.5, eps=1.0, sigma=1.0)
+            args.update(kw)
+            with pytest.raises(lblib.LBError) as ei:
+                lblib.lb_add_chain(ctx, **args)
+            assert ei.value.code == lblib.LB_ERR_ARG
+        with pytest.raises(lblib.LBError) as ei:  # generated walk needs bond < R0
+            lblib.lb_add_chain(ctx, 4, 1.0, 20.8, 30.0, 1.5, 1.0, 1.0, bond=1.6)
+        assert ei.value.code == lblib.LB_ERR_ARG
+        with pytest.raises(lblib.LBError) as ei:  # stretched initial bond
+            lblib.lb_add_chain(ctx, 2, 1.0, 20.8, 30.0, 1.5, 1.0, 1.0, x0=[[1, 1, 1], [2.6, 1, 1]])
+        assert ei.value.code == lblib.LB_ERR_FENE
+        lblib.lb_add_chain(ctx, 64, 1.0, 20.8, 30.0, 1.5, 1.0, 1.0, bond=0.97, saw=1)
+        with pytest.raises(lblib.LBError) as ei:
+            lblib.lb_add_chain(ctx, 4, 1.0, 20.8, 30.0, 1.5, 1.0, 1.0)
+        assert ei.value.code == lblib.LB_ERR_STATE
+        x = np.empty((64, 3))
+        v = np.empty((64, 3))
+        lblib.lb_get_beads(ctx, x, v, x.size)
+        bonds = np.linalg.norm(np.diff(x, axis=0), axis=1)
+        assert np.allclose(bonds, 0.97, rtol=1e-12)
+        d = np.linalg.norm(x[:, None] - x[None], axis=-1)
+        nonadj = ~np.eye(64, dtype=bool) & ~np.eye(64, k=1, dtype=bool) & ~np.eye(64, k=-1, dtype=bool)
+        assert d[nonadj].min() >= 1.0 - 1e-12
+        assert np.allclose(x[0], 8.0) and np.all(v == 0)
+    finally:
+        lblib.lb_destroy(ctx)
+
+
+def test_workspace_size_accounts_for_precision_and_size(lblib):
+    sizes = {}
+    for prec in (lblib.LB_FP64, lblib.LB_FP32, lblib.LB_BF16):
+        ctx = lblib.lb_create(32, 1.0, 3.0, 3.0, 1.0, 0.01, 1.0, 1, prec)
+        sizes[prec] = lblib.lb_workspace_size(ctx)
+        lblib.lb_destroy(ctx)
+    pop = lambda b: 2 * 19 * 32 ** 3 * b
+    assert sizes[lblib.LB_FP64] >= pop(8) and sizes[lblib.LB_FP64] < pop(8) * 1.1
+    assert sizes[lblib.LB_FP32] >= pop(4) and sizes[lblib.LB_FP32] < pop(4) * 1.1
+    assert sizes[lblib.LB_BF16] >= pop(2) and sizes[lblib.LB_BF16] < pop(2) * 1.2
+
+
+def test_strerror_names_every_status(lblib):
+    for code in range(8):
+        assert lblib.lb_strerror(code) != "unknown status"
+    assert lblib.lb_strerror(99) == "unknown status"

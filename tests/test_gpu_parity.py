@@ -1,0 +1,228 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on identical seeded inputs
+and identical Philox noise streams.
+
+Bars: FP64 context <= 1e-12 relative per population; FP32 context <= 1e-5 relative per
+population after 100 steps (populations are O(w_i rho0), so this is also an absolute bar
+of ~1e-5 w_i rho0); bead positions relative to the box and velocities relative to the
+thermal velocity sqrt(kT/m) at the same bars."""
+import numpy as np
+import pytest
+
+from gpu_helpers import Case, bead_errs, gpu_run, gpu_sim, oracle_run, pop_rel_err
+from oracle import lbchain as o
+
+pytestmark = pytest.mark.gpu
+
+C1 = Case(L=16, N=8, steps=200, seed=1)  # plain FP64 config: L=16, N=8, 200 steps, seed 1
+C1_FP32 = Case(L=16, N=8, steps=100, seed=1)
+
+
+def test_c1_fp64_matches_oracle(lblib):
+    st = oracle_run(C1)
+    n, x, v, obs = gpu_run(lblib, C1, lblib.LB_FP64)
+    assert pop_rel_err(n, st.n) <= 1e-12
+    ex, ev = bead_errs(x, v, st, C1)
+    assert ex <= 1e-12 and ev <= 1e-11
+
+
+def test_c1_fp32_matches_oracle_after_100_steps(lblib):
+    st = oracle_run(C1_FP32)
+    n, x, v, obs = gpu_run(lblib, C1_FP32, lblib.LB_FP32)
+    assert pop_rel_err(n, st.n) <= 1e-5
+    ex, ev = bead_errs(x, v, st, C1_FP32)
+    assert ex <= 1e-5 and ev <= 1e-5
+
+
+@pytest.mark.parametrize("L", [4, 5, 7, 40])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ragged_boxes_with_forces_and_perturbed_fluid(lblib, L, prec):
+    """Box sizes that leave partial thread blocks (odd L, L not a multiple of the 32-wide
+    rows), a fluid started away from equilibrium, a constant force on the beads balanced by
+    the uniform counter-force on the fluid."""
+    N = 3 if L >= 5 else 1
+    case = Case(L=L, N=N, steps=12, seed=4 + L, perturb=0.05, ext=(0.3, -0.2, 0.1), counter=True)
+    st = oracle_run(case)
+    p = lblib.LB_FP64 if prec == "fp64" else lblib.LB_FP32
+    n, x, v, _ = gpu_run(lblib, case, p)
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert pop_rel_err(n, st.n) <= tol
+    ex, ev = bead_errs(x, v, st, case)
+    assert ex <= tol and ev <= 10 * tol
+
+
+@pytest.mark.parametrize("variant", ["stress_only", "noise_off", "beads_noise_off", "kT0"])
+def test_noise_variants(lblib, variant):
+    kw = dict(L=8, N=4, steps=30, seed=9, perturb=0.02)
+    if variant == "stress_only":
+        kw["stress_only"] = True
+    elif variant == "noise_off":
+        kw["noise_fluid"] = False
+        kw["noise_beads"] = False
+    elif variant == "beads_noise_off":
+        kw["noise_beads"] = False
+    else:
+        kw["kT"] = 0.0
+    case = Case(**kw)
+    st = oracle_run(case)
+    for prec, tol in ((lblib.LB_FP64, 1e-12), (lblib.LB_FP32, 2e-6)):
+        n, x, v, _ = gpu_run(lblib, case, prec)
+        assert pop_rel_err(n, st.n) <= tol, (variant, prec)
+
+
+def test_fluid_without_chain(lblib):
+    case = Case(L=12, N=0, steps=40, seed=3, perturb=0.03)
+    st = oracle_run(case)
+    for prec, tol in ((lblib.LB_FP64, 1e-12), (lblib.LB_FP32, 2e-6)):
+        n, _, _, _ = gpu_run(lblib, case, prec)
+        assert pop_rel_err(n, st.n) <= tol
+
+
+def test_single_bead_and_general_spacing(lblib):
+    """N = 1 and a lattice spacing a != 1 (positions, forces and velocities rescale)."""
+    case = Case(L=6, N=1, steps=25, seed=12, a=0.8, h=0.02, eta=1.7, eta_b=2.2, kT=0.7)
+    st = oracle_run(case)
+    for prec, tol in ((lblib.LB_FP64, 1e-12), (lblib.LB_FP32, 2e-6)):
+        n, x, v, _ = gpu_run(lblib, case, prec)
+        assert pop_rel_err(n, st.n) <= tol
+        ex, ev = bead_errs(x, v, st, case)
+        assert ex <= tol and ev <= 10 * tol
+
+
+def test_c2_full_size_fp32(lblib):
+    """The L = 64, N = 64 workload at full size, every population compared."""
+    case = Case(L=64, N=64, steps=8, seed=2)
+    st = oracle_run(case)
+    n, x, v, _ = gpu_run(lblib, case, lblib.LB_FP32)
+    assert pop_rel_err(n, st.n) <= 1e-5
+    ex, ev = bead_errs(x, v, st, case)
+    assert ex <= 1e-5 and ev <= 1e-5
+
+
+def test_c3_full_size_fp32_two_steps(lblib):
+    """The benchmark's L = 128, N = 128 workload, in the same kernels and launch shapes the
+    benchmark times, every population compared after two coupled steps."""
+    case = Case(L=128, N=128, steps=2, seed=3)
+    st = oracle_run(case)
+    n, x, v, _ = gpu_run(lblib, case, lblib.LB_FP32)
+    assert pop_rel_err(n, st.n) <= 1e-5
+    ex, ev = bead_errs(x, v, st, case)
+    assert ex <= 1e-5 and ev <= 1e-5
+
+
+def test_observables_match_oracle(lblib):
+    case = Case(L=16, N=8, steps=50, seed=5)
+    st = oracle_run(case)
+    fp, cp = case.fluid(), case.chain()
+    _, _, _, obs = gpu_run(lblib, case, lblib.LB_FP64)
+    assert obs[0] == case.steps
+    assert obs[1] == pytest.approx(o.total_mass(st, fp), rel=1e-13)
+    scale = fp.L ** 3 * fp.rho * fp.a ** 4 / fp.h
+    assert np.allclose(obs[2:5], o.total_momentum(st, fp, cp), rtol=0, atol=1e-12 * scale)
+    assert np.allclose(obs[5:8], o.fluid_momentum(st, fp), rtol=0, atol=1e-12 * scale)
+    assert obs[8] == pytest.approx(o.radius_of_gyration2(st.X), rel=1e-12)
+    assert obs[9] == pytest.approx(o.end_to_end2(st.X), rel=1e-12)
+    assert np.allclose(obs[10:13], st.X.mean(axis=0), rtol=1e-13)
+    X0 = case.x0()
+    g1 = 0.5 * sum(((st.X[i] - X0[i]) ** 2).sum() for i in (3, 4))
+    assert obs[13] == pytest.approx(g1, rel=1e-9)
+    g3 = ((st.X.mean(axis=0) - X0.mean(axis=0)) ** 2).sum()
+    assert obs[14] == pytest.approx(g3, rel=1e-8, abs=1e-14)
+    assert obs[15] == pytest.approx(cp.m * (st.V ** 2).sum() / (3 * cp.N), rel=1e-12)
+
+
+def test_mass_and_momentum_invariants_on_gpu(lblib):
+    """Exact invariants of the coupled step (collision and coupling conserve mass and total
+    momentum) at the full L = 64 size, FP64 and FP32."""
+    for prec, tol in ((lblib.LB_FP64, 1e-12), (lblib.LB_FP32, 2e-6)):
+        case = Case(L=64, N=64, steps=0, seed=2)
+        sim = gpu_sim(lblib, case, prec)
+        o0 = sim.observables()
+        sim.step(50)
+        o1 = sim.observables()
+        sim.close()
+        assert o1[1] == pytest.approx(o0[1], rel=tol)
+        scale = 64 ** 3 * 1.0 / 0.01  # momentum of the box at one lattice velocity unit
+        assert np.allclose(o1[2:5], o0[2:5], rtol=0, atol=tol * scale)
+
+
+def test_checkpoint_resume_is_bit_exact(lblib, tmp_path):
+    case = Case(L=12, N=6, steps=0, seed=8)
+    for prec in (lblib.LB_FP64, lblib.LB_FP32):
+        a = gpu_sim(lblib, case, prec)
+        a.step(10)
+        path = str(tmp_path / f"ck{prec}.bin")
+        lblib.lb_save(a.ctx, path)
+        a.step(10)
+        na = a.populations()
+        xa, va = a.beads()
+        b = gpu_sim(lblib, case, prec)
+        lblib.lb_load(b.ctx, path)
+        assert lblib.lb_get_step(b.ctx) == 10
+        b.step(10)
+        nb = b.populations()
+        xb, vb = b.beads()
+        assert np.array_equal(na, nb) and np.array_equal(xa, xb) and np.array_equal(va, vb)
+        a.close()
+        b.close()
+
+
+def test_runs_are_deterministic_and_workspace_owner_independent(lblib):
+    case = Case(L=16, N=16, steps=20, seed=6)
+    r1 = gpu_run(lblib, case, lblib.LB_FP32)
+    sim = gpu_sim(lblib, case, lblib.LB_FP32)
+    sim._torch_workspace = False  # library-owned cudaMalloc workspace
+    sim.step(case.steps)
+    n2 = sim.populations()
+    x2, _ = sim.beads()
+    sim.close()
+    assert np.array_equal(r1[0], n2) and np.array_equal(r1[1], x2)
+
+
+def test_fene_break_is_reported_not_faulted(lblib):
+    """A bond pulled past R0 latches LB_ERR_FENE in the device status word; the host reads
+    it at the next synchronising call and the context stays usable."""
+    ctx = lblib.lb_create(8, 1.0, 3.0, 3.0, 0.0, 0.01, 1.0, 1, lblib.LB_FP32)
+    lblib.lb_add_chain(ctx, 2, 1.0, 20.8, 30.0, 1.5, 1.0, 1.0, x0=[[3.0, 4, 4], [4.4, 4, 4]],
+                       v0=[[-60.0, 0, 0], [60.0, 0, 0]])
+    lblib.lb_step(ctx, 5)
+    with pytest.raises(lblib.LBError) as ei:
+        lblib.lb_sync(ctx)
+    assert ei.value.code == lblib.LB_ERR_FENE
+    lblib.lb_destroy(ctx)
+
+
+def test_philox_gpu_is_bit_identical_to_oracle(lblib):
+    import torch
+
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    dev = torch.from_numpy(ctr.view(np.int32)).cuda()
+    out = torch.empty_like(dev)
+    for k0, k1 in ((0, 0), (1, 0), (0xDEADBEEF, 0x102), (0xFFFFFFFF, 0xFFFFFFFF)):
+        lblib.lb_philox4x32_10(dev.data_ptr(), 4096, k0, k1, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint32)
+        want = np.stack(o.philox4x32_10(ctr[:, 0], ctr[:, 1], ctr[:, 2], ctr[:, 3], k0, k1), axis=1)
+        assert np.array_equal(got, want)
+
+
+def test_cell_index_is_bit_exact(lblib):
+    import torch
+
+    L = 16
+    xs = [0.0, -0.0, 1.0, 15.0, 16.0, -1.0, -16.0, 1e4 * L, -1e4 * L - 0.5, 31.999]
+    for k in (1, 5, 15, 16, 17, -1, -16, 160000):
+        xk = np.float32(k)
+        xs += [np.nextafter(xk, np.float32(np.inf)), np.nextafter(xk, np.float32(-np.inf))]
+    rng = np.random.default_rng(2)
+    xs += list(rng.uniform(-100, 100, 2000))
+    x = np.array(xs, dtype=np.float32)
+    for a in (1.0, 0.7, 1.3):
+        xd = torch.from_numpy(x).cuda()
+        out = torch.empty(x.size, dtype=torch.int32, device="cuda")
+        lblib.lb_cell_index_f32(xd.data_ptr(), x.size, a, L, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        want = o.cell_index(x, np.float32(a), L)
+        assert np.array_equal(out.cpu().numpy(), want), a
