@@ -62,7 +62,7 @@ template <class R>
 struct ChainK {
   int N;
   R m, zeta, kfene, R0sq, eps, sig2, rc2;
-  R h, a, box, inv_box;
+  R h, a, box, half_box;
   R amp;            // sqrt(2 kT zeta / h), 0 without bead noise
   uint32_t k0, k1;  // Philox key of the bead stream
   R ext[3];         // constant external force on each bead
@@ -70,7 +70,8 @@ struct ChainK {
   R inv_a3;         // 1 / a^3
   R dJ_scale;       // h^2 / a: force density -> lattice momentum per step
   // bead state (global, 3N each, bead-major)
-  R* x;    // wrapped positions in [0, box)
+  R* x;    // wrapped positions in [0, box): high part
+  R* xl;   // low part: position = x + xl + img * box (compensated, ~2x the precision of R)
   int* img;  // periodic image counters
   R* v;
   R* F;    // total force of the last step (F_cons + F_c)
@@ -310,13 +311,6 @@ __global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* _
 // ---------------------------------------------------------------------------------------
 // bead / coupling kernel (one CTA)
 // ---------------------------------------------------------------------------------------
-template <class R>
-__device__ __forceinline__ R rnd_nearest(R v);
-template <>
-__device__ __forceinline__ float rnd_nearest<float>(float v) { return rintf(v); }
-template <>
-__device__ __forceinline__ double rnd_nearest<double>(double v) { return rint(v); }
-
 // cell of a coordinate: floor(x/a) mod L into [0, L); frac = x/a - floor(x/a)
 template <class R>
 __device__ __forceinline__ int cell_of(R x, R a, int L, R& frac) {
@@ -329,17 +323,23 @@ __device__ __forceinline__ int cell_of(R x, R a, int L, R& frac) {
   return (int)r;
 }
 
+// Pair vector r_b - r_j under the minimum image convention from compensated positions
+// (hi in [0, box), lo): the coordinate above box/2 is moved down by the box, which is exact
+// (Sterbenz), so the difference of two nearby beads carries no rounding from their distance to
+// the origin.
 template <class R>
-__device__ __forceinline__ void add_pair_force(const R* __restrict__ sx, int b, int j, const ChainK<R>& C,
-                                               R f[3], bool bonded, unsigned* status) {
-  R d[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    R dd = sx[3 * b + q] - sx[3 * j + q];
-    dd -= C.box * rnd_nearest<R>(dd * C.inv_box);
-    d[q] = dd;
-  }
-  const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+__device__ __forceinline__ R pair_delta(R hb, R lb, R hj, R lj, R box, R half_box) {
+  const R dh = hb - hj;
+  if (dh > half_box)
+    hb -= box;
+  else if (dh < -half_box)
+    hj -= box;
+  return (hb - hj) + (lb - lj);
+}
+
+// FENE (bonded) + WCA force coefficient: force on b = coef * d
+template <class R>
+__device__ __forceinline__ R pair_coef(R r2, bool bonded, const ChainK<R>& C, unsigned* status) {
   R coef = R(0);
   if (r2 < C.rc2) {
     const R s2 = C.sig2 / r2;
@@ -353,9 +353,45 @@ __device__ __forceinline__ void add_pair_force(const R* __restrict__ sx, int b, 
       coef -= C.kfene / (R(1) - r2 / C.R0sq);
     }
   }
-  f[0] += coef * d[0];
-  f[1] += coef * d[1];
-  f[2] += coef * d[2];
+  return coef;
+}
+
+// Conservative forces (FENE + WCA + external) on every bead from positions staged in shared
+// memory; `lanes` threads per bead split the partners and combine in a fixed shuffle tree.
+template <class R>
+__device__ __forceinline__ void chain_forces_block(const R* __restrict__ sh, const R* __restrict__ sl,
+                                                   const ChainK<R>& C, R* __restrict__ out) {
+  const int N = C.N, nt = blockDim.x, tid = threadIdx.x;
+  int lanes = 1;
+  while (lanes < 32 && lanes * 2 * N <= nt) lanes *= 2;
+  const int per = nt / lanes;
+  const int lane = tid % lanes;
+  for (int base = 0; base < N; base += per) {
+    const int b = base + tid / lanes;
+    R f[3] = {R(0), R(0), R(0)};
+    if (b < N) {
+      for (int j = lane; j < N; j += lanes) {
+        if (j == b) continue;
+        R d[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          d[q] = pair_delta<R>(sh[3 * b + q], sl[3 * b + q], sh[3 * j + q], sl[3 * j + q], C.box, C.half_box);
+        const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const R coef = pair_coef<R>(r2, (j == b - 1) || (j == b + 1), C, C.status);
+        f[0] += coef * d[0];
+        f[1] += coef * d[1];
+        f[2] += coef * d[2];
+      }
+    }
+    for (int o = lanes / 2; o > 0; o /= 2) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o, lanes);
+    }
+    if (b < N && lane == 0) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) out[3 * b + q] = f[q] + C.ext[q];
+    }
+  }
 }
 
 // post-stream populations at node (qx,qy,qz): rho and lattice momentum
@@ -392,39 +428,44 @@ __global__ void __launch_bounds__(512) k_bead_step(const S* __restrict__ pop, co
   const int L = (int)P.L;
   const R h = C.h;
   R* sx = reinterpret_cast<R*>(smem);
+  R* sl = sx + 3 * N;
 
-  // 1. first half kick and drift: v_half = v + h F/2m, x' = x + h v_half (wrapped)
+  // 1. first half kick and drift: v_half = v + h F/2m, x' = x + h v_half, in compensated
+  //    (hi, lo) arithmetic, then wrapped into [0, box) with the image counter
   for (int t = tid; t < 3 * N; t += nt) {
     const R vh = C.v[t] + h * C.F[t] / (R(2) * C.m);
-    R xn = C.x[t] + h * vh;
+    const R dx = h * vh;
+    const R xh = C.x[t];
+    R hi = xh + dx;
+    const R bp = hi - xh;
+    R lo = C.xl[t] + ((xh - (hi - bp)) + (dx - bp));
+    {
+      const R s2 = hi + lo;
+      lo = lo - (s2 - hi);
+      hi = s2;
+    }
     int im = C.img[t];
-    if (xn < R(0)) {
-      xn += C.box;
+    if (hi < R(0)) {
+      const R s2 = C.box + hi;
+      lo += hi - (s2 - C.box);
+      hi = s2;
       --im;
     }
-    if (xn >= C.box) {
-      xn -= C.box;
+    if (hi >= C.box) {
+      hi -= C.box;
       ++im;
     }
     C.vh[t] = vh;
-    C.x[t] = xn;
+    C.x[t] = hi;
+    C.xl[t] = lo;
     C.img[t] = im;
-    sx[t] = xn;
+    sx[t] = hi;
+    sl[t] = lo;
   }
   __syncthreads();
 
   // 2. conservative forces at x': FENE on bonds, WCA on all pairs, minimum image
-  for (int b = tid; b < N; b += nt) {
-    R f[3] = {C.ext[0], C.ext[1], C.ext[2]};
-    for (int j = 0; j < N; ++j) {
-      if (j == b) continue;
-      const bool bonded = (j == b - 1) || (j == b + 1);
-      add_pair_force<R>(sx, b, j, C, f, bonded, C.status);
-    }
-    C.fcons[3 * b + 0] = f[0];
-    C.fcons[3 * b + 1] = f[1];
-    C.fcons[3 * b + 2] = f[2];
-  }
+  chain_forces_block<R>(sx, sl, C, C.fcons);
 
   // 3. corners of every bead: cell, trilinear weight, post-stream rho and J at the node
   for (int e = tid; e < 8 * N; e += nt) {
@@ -433,7 +474,14 @@ __global__ void __launch_bounds__(512) k_bead_step(const S* __restrict__ pop, co
     R fr[3];
     int cl[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) cl[q] = cell_of<R>(sx[3 * b + q], C.a, L, fr[q]);
+    for (int q = 0; q < 3; ++q) {
+      R unused;
+      const R xh = sx[3 * b + q];
+      cl[q] = cell_of<R>(xh, C.a, L, unused);
+      // fractional position inside the cell from the exact remainder xh - floor(xh/a) a
+      const R f = floor(xh / C.a);
+      fr[q] = (fma(-f, C.a, xh) + sl[3 * b + q]) / C.a;
+    }
     const int qx = (cl[0] + dx) % L, qy = (cl[1] + dy) % L, qz = (cl[2] + dz) % L;
     const R w = (dx ? fr[0] : R(1) - fr[0]) * (dy ? fr[1] : R(1) - fr[1]) * (dz ? fr[2] : R(1) - fr[2]);
     R mom[4];
@@ -643,6 +691,7 @@ struct ObsK {
   double a3, u_scale;  // a^3, a/h
   int N;
   const R* x;
+  const R* xl;
   const int* img;
   const R* v;
   const R* Fc;
@@ -667,7 +716,7 @@ __global__ void __launch_bounds__(256) k_observables(const ObsK<R> O) {
   double cm[3] = {0, 0, 0}, mv[3] = {0, 0, 0}, fc[3] = {0, 0, 0}, v2 = 0;
   for (int b = tid; b < O.N; b += blockDim.x) {
     for (int q = 0; q < 3; ++q) {
-      const double xu = (double)O.x[3 * b + q] + (double)O.img[3 * b + q] * O.box;
+      const double xu = (double)O.x[3 * b + q] + (double)O.xl[3 * b + q] + (double)O.img[3 * b + q] * O.box;
       cm[q] += xu;
       const double vv = (double)O.v[3 * b + q];
       mv[q] += O.m * vv;
@@ -694,7 +743,7 @@ __global__ void __launch_bounds__(256) k_observables(const ObsK<R> O) {
   double rg = 0;
   for (int b = tid; b < N; b += blockDim.x) {
     for (int q = 0; q < 3; ++q) {
-      const double xu = (double)O.x[3 * b + q] + (double)O.img[3 * b + q] * O.box;
+      const double xu = (double)O.x[3 * b + q] + (double)O.xl[3 * b + q] + (double)O.img[3 * b + q] * O.box;
       const double d = xu - tot[4 + q] / N;
       rg += d * d;
     }
@@ -724,11 +773,11 @@ __global__ void __launch_bounds__(256) k_observables(const ObsK<R> O) {
         for (int q = 0; q < 3; ++q) cmr[q] += O.xref[3 * b + q];
       const int i0 = (N - 1) / 2, i1 = N / 2;
       for (int q = 0; q < 3; ++q) {
-        const double xe = (double)O.x[3 * (N - 1) + q] + (double)O.img[3 * (N - 1) + q] * O.box;
-        const double xs = (double)O.x[q] + (double)O.img[q] * O.box;
+        const double xe = (double)O.x[3 * (N - 1) + q] + (double)O.xl[3 * (N - 1) + q] + (double)O.img[3 * (N - 1) + q] * O.box;
+        const double xs = (double)O.x[q] + (double)O.xl[q] + (double)O.img[q] * O.box;
         Re2 += (xe - xs) * (xe - xs);
-        const double a0 = (double)O.x[3 * i0 + q] + (double)O.img[3 * i0 + q] * O.box - O.xref[3 * i0 + q];
-        const double a1 = (double)O.x[3 * i1 + q] + (double)O.img[3 * i1 + q] * O.box - O.xref[3 * i1 + q];
+        const double a0 = (double)O.x[3 * i0 + q] + (double)O.xl[3 * i0 + q] + (double)O.img[3 * i0 + q] * O.box - O.xref[3 * i0 + q];
+        const double a1 = (double)O.x[3 * i1 + q] + (double)O.xl[3 * i1 + q] + (double)O.img[3 * i1 + q] * O.box - O.xref[3 * i1 + q];
         g1 += 0.5 * (a0 * a0 + a1 * a1);
         const double dc = (tot[4 + q] - cmr[q]) / N;
         g3 += dc * dc;
@@ -763,23 +812,18 @@ namespace gblb {
 
 // Forces of the initial configuration: F = F_cons(x0) (+ external), F_c = 0.
 template <class R>
-__global__ void __launch_bounds__(256) k_chain_init_forces(const ChainK<R> C) {
+__global__ void __launch_bounds__(512) k_chain_init_forces(const ChainK<R> C) {
   extern __shared__ __align__(16) unsigned char smem[];
   R* sx = reinterpret_cast<R*>(smem);
-  const int N = C.N;
-  for (int t = threadIdx.x; t < 3 * N; t += blockDim.x) sx[t] = C.x[t];
-  __syncthreads();
-  for (int b = threadIdx.x; b < N; b += blockDim.x) {
-    R f[3] = {C.ext[0], C.ext[1], C.ext[2]};
-    for (int j = 0; j < N; ++j) {
-      if (j == b) continue;
-      add_pair_force<R>(sx, b, j, C, f, (j == b - 1) || (j == b + 1), C.status);
-    }
-    for (int q = 0; q < 3; ++q) {
-      C.F[3 * b + q] = f[q];
-      C.Fc[3 * b + q] = R(0);
-    }
+  R* sl = sx + 3 * C.N;
+  for (int t = threadIdx.x; t < 3 * C.N; t += blockDim.x) {
+    sx[t] = C.x[t];
+    sl[t] = C.xl[t];
   }
+  __syncthreads();
+  chain_forces_block<R>(sx, sl, C, C.F);
+  __syncthreads();
+  for (int t = threadIdx.x; t < 3 * C.N; t += blockDim.x) C.Fc[t] = R(0);
 }
 
 }  // namespace gblb

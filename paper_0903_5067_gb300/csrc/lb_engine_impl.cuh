@@ -46,7 +46,7 @@ class EngineT final : public Engine {
     cuda_check(cudaMemsetAsync(acc_, 0, 4 * sizeof(double), s), "memset accumulators");
     if (N_ > 0) {
       const double box = cfg_.L * cfg_.a;
-      std::vector<R> xw(3 * N_), vv(3 * N_);
+      std::vector<R> xw(3 * N_), xlo(3 * N_), vv(3 * N_);
       std::vector<int> im(3 * N_);
       for (int t = 0; t < 3 * N_; ++t) {
         const double xu = x0[t];
@@ -55,33 +55,42 @@ class EngineT final : public Engine {
         R xs = (R)xr;
         if (xs >= (R)box) {
           xs = (R)0;
+          xr -= box;
           k += 1;
         }
-        if (xs < (R)0) xs = (R)0;
         xw[t] = xs;
+        xlo[t] = (R)(xr - (double)xs);
         im[t] = (int)k;
         vv[t] = v0 ? (R)v0[t] : (R)0;
       }
       cuda_check(cudaMemcpyAsync(x_, xw.data(), 3 * N_ * sizeof(R), cudaMemcpyHostToDevice, s), "upload x");
+      cuda_check(cudaMemcpyAsync(xl_, xlo.data(), 3 * N_ * sizeof(R), cudaMemcpyHostToDevice, s), "upload xl");
       cuda_check(cudaMemcpyAsync(img_, im.data(), 3 * N_ * sizeof(int), cudaMemcpyHostToDevice, s), "upload img");
       cuda_check(cudaMemcpyAsync(v_, vv.data(), 3 * N_ * sizeof(R), cudaMemcpyHostToDevice, s), "upload v");
       cuda_check(cudaMemcpyAsync(xref_, x0, 3 * N_ * sizeof(double), cudaMemcpyHostToDevice, s), "upload xref");
       cuda_check(cudaStreamSynchronize(s), "sync upload");
       const ChainK<R> C = chain();
-      k_chain_init_forces<R><<<1, 256, 3 * N_ * sizeof(R), s>>>(C);
+      k_chain_init_forces<R><<<1, 512, 6 * N_ * sizeof(R), s>>>(C);
       cuda_check(cudaGetLastError(), "init forces");
     }
     cuda_check(cudaMemsetAsync(p_count_, 0, sizeof(int), s), "memset pending");
   }
 
+  // One coupled step.  The bead kernel (one CTA) and the LB kernel both read only buffer A,
+  // so the bead kernel runs on a side stream concurrently with the LB kernel; the force
+  // correction joins them and adds the bead reaction to buffer B.
   void step(uint32_t k, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) override {
     const FluidK<R> P = fluid();
     const S* A = pop_[cur_];
     S* Bo = pop_[cur_ ^ 1];
     if (N_ > 0) {
+      ensure_side_stream();
       const ChainK<R> C = chain();
-      k_bead_step<S, R, DEV><<<1, 512, bead_smem(), s>>>(A, P, C, k);
+      cuda_check(cudaEventRecord(ev_ready_, s), "record ready");
+      cuda_check(cudaStreamWaitEvent(side_, ev_ready_, 0), "wait ready");
+      k_bead_step<S, R, DEV><<<1, 512, bead_smem(), side_>>>(A, P, C, k);
       cuda_check(cudaGetLastError(), "bead kernel");
+      cuda_check(cudaEventRecord(ev_bead_, side_), "record bead");
     }
     dim3 blk, grd;
     lb_launch_shape(blk, grd);
@@ -93,10 +102,17 @@ class EngineT final : public Engine {
     if (ev1) cudaEventRecord(ev1, s);
     cuda_check(cudaGetLastError(), "LB kernel");
     if (N_ > 0) {
+      cuda_check(cudaStreamWaitEvent(s, ev_bead_, 0), "wait bead");
       k_apply_pending<S, R><<<(cap_ + 255) / 256, 256, 0, s>>>(Bo, P, p_node_, p_dn_, p_count_, cap_);
       cuda_check(cudaGetLastError(), "apply kernel");
     }
     cur_ ^= 1;
+  }
+
+  ~EngineT() override {
+    if (side_) cudaStreamDestroy(side_);
+    if (ev_ready_) cudaEventDestroy(ev_ready_);
+    if (ev_bead_) cudaEventDestroy(ev_bead_);
   }
 
   void get_populations(double* out, cudaStream_t s) override {
@@ -130,15 +146,16 @@ class EngineT final : public Engine {
 
   void get_beads(double* x, double* v, cudaStream_t s) override {
     if (N_ == 0) return;
-    std::vector<R> xw(3 * N_), vv(3 * N_);
+    std::vector<R> xw(3 * N_), xlo(3 * N_), vv(3 * N_);
     std::vector<int> im(3 * N_);
     cuda_check(cudaMemcpyAsync(xw.data(), x_, 3 * N_ * sizeof(R), cudaMemcpyDeviceToHost, s), "dl x");
+    cuda_check(cudaMemcpyAsync(xlo.data(), xl_, 3 * N_ * sizeof(R), cudaMemcpyDeviceToHost, s), "dl xl");
     cuda_check(cudaMemcpyAsync(im.data(), img_, 3 * N_ * sizeof(int), cudaMemcpyDeviceToHost, s), "dl img");
     cuda_check(cudaMemcpyAsync(vv.data(), v_, 3 * N_ * sizeof(R), cudaMemcpyDeviceToHost, s), "dl v");
     cuda_check(cudaStreamSynchronize(s), "sync beads");
     const double box = cfg_.L * cfg_.a;
     for (int t = 0; t < 3 * N_; ++t) {
-      if (x) x[t] = (double)xw[t] + (double)im[t] * box;
+      if (x) x[t] = (double)xw[t] + (double)xlo[t] + (double)im[t] * box;
       if (v) v[t] = (double)vv[t];
     }
   }
@@ -176,7 +193,7 @@ class EngineT final : public Engine {
 
   // checkpoint: populations (storage type, L^3 per plane), bead arrays, xref, acc, counter
   size_t state_bytes() const override {
-    return 19 * nnodes_ * sizeof(S) + (size_t)N_ * 3 * (4 * sizeof(R) + sizeof(int) + sizeof(double)) +
+    return 19 * nnodes_ * sizeof(S) + (size_t)N_ * 3 * (5 * sizeof(R) + sizeof(int) + sizeof(double)) +
            4 * sizeof(double) + sizeof(unsigned long long);
   }
   void save_state(void* host, cudaStream_t s) override {
@@ -213,6 +230,7 @@ class EngineT final : public Engine {
     };
     const size_t n3 = 3 * (size_t)N_;
     mv(x_, n3 * sizeof(R));
+    mv(xl_, n3 * sizeof(R));
     mv(img_, n3 * sizeof(int));
     mv(v_, n3 * sizeof(R));
     mv(F_, n3 * sizeof(R));
@@ -221,6 +239,13 @@ class EngineT final : public Engine {
     mv(acc_, 4 * sizeof(double));
     mv(nonpos_, sizeof(unsigned long long));
     return p;
+  }
+
+  void ensure_side_stream() {
+    if (side_) return;
+    cuda_check(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking), "side stream");
+    cuda_check(cudaEventCreateWithFlags(&ev_ready_, cudaEventDisableTiming), "event");
+    cuda_check(cudaEventCreateWithFlags(&ev_bead_, cudaEventDisableTiming), "event");
   }
 
   void lb_launch_shape(dim3& blk, dim3& grd) const {
@@ -236,7 +261,7 @@ class EngineT final : public Engine {
     size_t M = 1;
     while (M < ne) M <<= 1;
     const size_t sortb = M * 8 + ne * 4;
-    const size_t posb = 3 * (size_t)N_ * sizeof(R);
+    const size_t posb = 6 * (size_t)N_ * sizeof(R);
     return sortb > posb ? sortb : posb;
   }
 
@@ -292,7 +317,7 @@ class EngineT final : public Engine {
     C.h = (R)c.h;
     C.a = (R)c.a;
     C.box = (R)(c.L * c.a);
-    C.inv_box = (R)(1.0 / (c.L * c.a));
+    C.half_box = (R)(0.5 * c.L * c.a);
     const bool noise = c.noise_beads && c.kT > 0.0;
     C.amp = noise ? (R)sqrt(2.0 * c.kT * c.zeta / c.h) : (R)0;
     C.k0 = (uint32_t)(c.seed & 0xffffffffu);
@@ -302,6 +327,7 @@ class EngineT final : public Engine {
     C.inv_a3 = (R)(1.0 / (c.a * c.a * c.a));
     C.dJ_scale = (R)(c.h * c.h / c.a);
     C.x = x_;
+    C.xl = xl_;
     C.img = img_;
     C.v = v_;
     C.F = F_;
@@ -330,6 +356,7 @@ class EngineT final : public Engine {
     O.u_scale = c.a / c.h;
     O.N = N_;
     O.x = x_;
+    O.xl = xl_;
     O.img = img_;
     O.v = v_;
     O.Fc = Fc_;
@@ -359,6 +386,7 @@ class EngineT final : public Engine {
     pop_[1] = reinterpret_cast<S*>(take(popb));
     const size_t n3 = 3 * (size_t)(N_ > 0 ? N_ : 1);
     x_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
+    xl_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
     img_ = reinterpret_cast<int*>(take(n3 * sizeof(int)));
     v_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
     F_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
@@ -385,8 +413,10 @@ class EngineT final : public Engine {
   unsigned long long nnodes_ = 0, plane_ = 0;
   size_t bytes_ = 0;
   int cur_ = 0;
+  cudaStream_t side_ = nullptr;
+  cudaEvent_t ev_ready_ = nullptr, ev_bead_ = nullptr;
   S* pop_[2] = {nullptr, nullptr};
-  R *x_ = nullptr, *v_ = nullptr, *F_ = nullptr, *Fc_ = nullptr, *vh_ = nullptr, *fcons_ = nullptr;
+  R *x_ = nullptr, *xl_ = nullptr, *v_ = nullptr, *F_ = nullptr, *Fc_ = nullptr, *vh_ = nullptr, *fcons_ = nullptr;
   int* img_ = nullptr;
   double* xref_ = nullptr;
   int* e_node_ = nullptr;

