@@ -153,6 +153,29 @@ int lb_philox4x32_10(const uint32_t* ctr_dev, int64_t n, uint32_t k0, uint32_t k
 int lb_cell_index_f32(const float* x_dev, int64_t n, float a, int L, int32_t* out_dev,
                       void* stream);
 
+/* --- allocation-free variant ---------------------------------------------------------
+ * Fluid mass and momentum of a population field, like lb_get_observables' entries [1] and
+ * [5..7], for callers that cannot allocate device memory where they need these sums: code
+ * running while a stream is captured into a CUDA graph (cudaMalloc is not permitted there),
+ * processes whose device memory is owned by another allocator, or latency-critical loops.
+ * The paper has no counterpart; this is a service of the library.
+ *
+ * pop_dev: 19 L^3 full populations (FP64, mass densities) on the current device, in the
+ * layout lb_get_populations returns ([i][z][y][x], ABI velocity order).  out_host receives
+ * 4 doubles: a^3 sum n, then (a^4/h) sum_i n_i c_i (x, y, z).  Enqueued on `stream` and
+ * synchronised before returning.
+ *
+ * Scratch: a file-scope device array of LB_NOALLOC_MAX_L^3 / 256 partial sums (2 MiB), held by
+ * every GPU that loads the library until the process exits; L > LB_NOALLOC_MAX_L returns
+ * LB_ERR_ARG.  The function calls no cudaMalloc, cudaFree or allocating library routine.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture begins.  All
+ * calls share the array (it keeps the last call's partial sums, each call overwrites every
+ * slot it reads), so calls that overlap on the GPU, from several streams or threads, race. */
+#define LB_NOALLOC_MAX_L 256
+int lb_fluid_sums_noalloc(const double* pop_dev, int L, double a, double h, double* out_host,
+                          void* stream);
+
 #ifdef __cplusplus
 }
 #endif

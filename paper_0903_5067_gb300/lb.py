@@ -51,7 +51,9 @@ _SIGS = {
     "lb_strerror": (C.c_char_p, [C.c_int]),
     "lb_philox4x32_10": (C.c_int, [_vp, C.c_int64, C.c_uint32, C.c_uint32, _vp, _vp]),
     "lb_cell_index_f32": (C.c_int, [_vp, C.c_int64, C.c_float, C.c_int, _vp, _vp]),
+    "lb_fluid_sums_noalloc": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double, _dp, _vp]),
 }
+LB_NOALLOC_MAX_L = 256
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.restype = _res
@@ -186,6 +188,15 @@ def lb_philox4x32_10(ctr_dev_ptr: int, n: int, k0: int, k1: int, out_dev_ptr: in
 def lb_cell_index_f32(x_dev_ptr: int, n: int, a: float, L: int, out_dev_ptr: int, stream: int = 0):
     _check(_lib.lb_cell_index_f32(_vp(x_dev_ptr), n, a, L, _vp(out_dev_ptr), _vp(stream) if stream else None),
            "lb_cell_index_f32")
+
+
+def lb_fluid_sums_noalloc(pop_dev_ptr: int, L: int, a: float, h: float, stream: int = 0) -> np.ndarray:
+    """Mass and momentum of a device population field (19 L^3 FP64) without any device
+    allocation: the library's fixed scratch array holds the partial sums."""
+    out = np.zeros(4)
+    _check(_lib.lb_fluid_sums_noalloc(_vp(pop_dev_ptr), int(L), a, h, _dbuf(out), _vp(stream) if stream else None),
+           "lb_fluid_sums_noalloc")
+    return out
 
 
 # --- convenience wrapper ---------------------------------------------------------------
