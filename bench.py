@@ -288,6 +288,32 @@ def run_ours(args):
     obs = sim.observables()
     sim.close()
 
+    # batched replicas: the 64-box ensemble (5,242,368 nodes per step), autotuned tile shape,
+    # 16-step CUDA graphs; whole-ensemble MLUPS
+    batch = None
+    if not args.no_batch:
+        bL, bN, bseeds, bX = inputs.c4_ensemble(base_seed=100 + 1000 * rank)
+        bt = lb.Batch(bL, bN, bseeds, bX, precision=lb.LB_FP32, **PARAMS, **CHAIN)
+        shape = lb.lb_batch_autotune(bt.b)
+        kb = max(32, (args.steps // 10) // 16 * 16)
+        bt.step(32)
+        bt.sync()
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        bt.step(kb)
+        g1.record(stream)
+        barrier()
+        tb = g0.elapsed_time(g1) / 1e3
+        bt.sync()
+        nodes = lb.lb_batch_nodes(bt.b)
+        bt.close()
+        bval, _ = aggregate_throughput(nodes * kb / 1e6, tb, ws, dev)
+        batch = {"value": bval, "unit": "MLUPS", "replicas": len(bL), "nodes_per_step": nodes, "steps": kb,
+                 "ms_per_step": tb / kb * 1e3, "threads": shape[0], "blocks_per_sm": shape[1],
+                 "hbm_frac": BYTES_PER_NODE["f32"] * nodes / (tb / kb) / 1e9 / measured_peaks()[0],
+                 "workload": "64 replicas, L in {16,24,32,48,64}, N in {8,16,32,64}, FP32, graph-captured"}
+
     value, tmax = aggregate_throughput(L ** 3 * args.steps / 1e6, t32, ws, dev)
     v64, _ = aggregate_throughput(L ** 3 * k64 / 1e6, t64, ws, dev)
 
@@ -341,6 +367,7 @@ def run_ours(args):
                        "roofline_frac": BYTES_PER_NODE["f64"] * L ** 3 / (t64 / k64) / 1e9 / peak,
                        "fp32_over_fp64": value / v64},
         "bead_steps_per_s": N * args.steps * ws / tmax,
+        "batch_c4": batch,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "C ABI, pinned host buffers: set_populations, K x (step + get_beads), get_populations"},
         "gpu_launches": launches_per_step * args.steps,
@@ -360,6 +387,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

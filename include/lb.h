@@ -153,6 +153,37 @@ int lb_philox4x32_10(const uint32_t* ctr_dev, int64_t n, uint32_t k0, uint32_t k
 int lb_cell_index_f32(const float* x_dev, int64_t n, float a, int L, int32_t* out_dev,
                       void* stream);
 
+/* --- batched replicas ------------------------------------------------------------------
+ * R independent boxes advanced in lockstep by one launch per kernel stage (the ensemble of
+ * box sizes and chain lengths the paper runs for its finite-size and cost studies, Sec. II E,
+ * Sec. III B-C).  Replica r has L[r] nodes per side (4..256), a chain of N[r] beads (0..1024)
+ * whose 3N[r] positions are concatenated in x0 (replica order; NULL only if every N[r] = 0),
+ * and its own noise stream: Philox key (seeds[r] low 32 bits, tag | r << 8).  Fluid and chain
+ * parameters as in lb_create / lb_add_chain, shared by all replicas.  precision: LB_FP32 or
+ * LB_FP64.  Workspace, stream and errors as for a context. */
+typedef struct lb_batch lb_batch;
+int lb_batch_create(lb_batch** out, int R, const int* L, const int* N, const uint64_t* seeds,
+                    double rho, double eta, double eta_b, double kT, double h, double a, double m,
+                    double zeta, double k_fene, double R0, double eps, double sigma,
+                    const double* x0, int precision);
+int lb_batch_set_stream(lb_batch* b, void* stream);
+int lb_batch_workspace_size(lb_batch* b, size_t* bytes);
+int lb_batch_bind_workspace(lb_batch* b, void* device_ptr, size_t bytes);
+/* Tile size of the batched LB kernel (128, 256 or 512 threads) and persistent thread blocks
+ * per SM (0 = one block per tile).  Results do not depend on the shape. */
+int lb_batch_set_shape(lb_batch* b, int threads, int blocks_per_sm);
+/* Measure every shape for a few steps, keep the fastest and return it; the trial steps are
+ * undone (the replicas restart from their initial state).  Only before the first step. */
+int lb_batch_autotune(lb_batch* b, int* threads, int* blocks_per_sm);
+/* Advance every replica n steps; runs of 16 steps are replayed from a captured CUDA graph. */
+int lb_batch_step(lb_batch* b, int64_t n);
+int lb_batch_sync(lb_batch* b);
+int lb_batch_get_populations(lb_batch* b, int r, double* out, size_t cap);
+int lb_batch_get_beads(lb_batch* b, int r, double* x, double* v, size_t cap);
+int lb_batch_get_observables(lb_batch* b, int r, double* out, size_t cap);
+int64_t lb_batch_nodes(lb_batch* b); /* total nodes of all replicas */
+void lb_batch_destroy(lb_batch* b);
+
 /* --- allocation-free variant ---------------------------------------------------------
  * Fluid mass and momentum of a population field, like lb_get_observables' entries [1] and
  * [5..7], for callers that cannot allocate device memory where they need these sums: code

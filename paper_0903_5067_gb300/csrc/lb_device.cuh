@@ -52,6 +52,7 @@ struct FluidK {
   R gs, gb;        // relaxation eigenvalues: shear modes 5..9, bulk mode 4 (kinetic modes: 0)
   R cnoise[Q];     // sqrt(mu b_k (1 - gamma_k^2)), mode k's noise per sqrt(rho); 0 if silent
   uint32_t k0, k1; // Philox key of the fluid stream
+  RoundKeys rk;    // its ten round keys
   int ncalls;      // Philox calls per node: 0 (noise off), 2 (stress modes only), 4 (all)
   int body_on;     // uniform body force
   R body_dJ[3];    // lattice momentum it adds per step and node: f h^2 / a
@@ -175,16 +176,92 @@ __device__ __forceinline__ void dmoments_to_dpops(const R dm[10], R out[Q]) {
 }
 
 // ---------------------------------------------------------------------------------------
+// explicit D3Q19 transforms in the ABI velocity order (pairs 2p+1, 2p+2 opposite):
+// the same linear maps as the basis tables above, with the sums shared between modes and
+// between populations written out, which the compiler cannot do itself without reassociating
+// floating-point sums.
+// ---------------------------------------------------------------------------------------
+// moments 0..9 (density, momentum, stress modes) of 19 populations
+template <class R>
+__host__ __device__ __forceinline__ void moments_0_9(const R n[Q], R m[10]) {
+  const R s0 = n[1] + n[2], d0 = n[1] - n[2];
+  const R s1 = n[3] + n[4], d1 = n[3] - n[4];
+  const R s2 = n[5] + n[6], d2 = n[5] - n[6];
+  const R s3 = n[7] + n[8], d3 = n[7] - n[8];
+  const R s4 = n[9] + n[10], d4 = n[9] - n[10];
+  const R s5 = n[11] + n[12], d5 = n[11] - n[12];
+  const R s6 = n[13] + n[14], d6 = n[13] - n[14];
+  const R s7 = n[15] + n[16], d7 = n[15] - n[16];
+  const R s8 = n[17] + n[18], d8 = n[17] - n[18];
+  const R sxy = s3 + s4, sxz = s5 + s6, syz = s7 + s8;
+  const R snn = sxy + sxz + syz;
+  m[0] = n[0] + (s0 + s1 + s2) + snn;
+  m[1] = d0 + d3 + d4 + d5 + d6;
+  m[2] = d1 + d3 - d4 + d7 + d8;
+  m[3] = d2 + d5 - d6 + d7 - d8;
+  m[4] = snn - n[0];
+  m[5] = R(2) * (s0 - syz) - s1 - s2 + sxy + sxz;
+  m[6] = s1 - s2 + sxy - sxz;
+  m[7] = s3 - s4;
+  m[8] = s7 - s8;
+  m[9] = s5 - s6;
+}
+
+// populations n_i = w_i sum_k e_k(c_i) a_k from scaled moments a_k = m_k / b_k
+template <class R>
+__host__ __device__ __forceinline__ void pops_from_scaled(const R a[Q], R n[Q]) {
+  const R w0 = R(1) / R(3), w1 = R(1) / R(18), w2 = R(1) / R(36);
+  n[0] = w0 * (a[0] - a[4] + a[16]);
+  // nearest neighbours
+  const R t = a[0] - a[5] - R(2) * a[16] + a[17];
+  const R Sx = a[0] + R(2) * (a[5] - a[16] - a[17]);
+  const R Sy = t + (a[6] - a[18]);
+  const R Sz = t - (a[6] - a[18]);
+  const R Dx = a[1] - R(2) * a[10], Dy = a[2] - R(2) * a[11], Dz = a[3] - R(2) * a[12];
+  n[1] = w1 * (Sx + Dx);
+  n[2] = w1 * (Sx - Dx);
+  n[3] = w1 * (Sy + Dy);
+  n[4] = w1 * (Sy - Dy);
+  n[5] = w1 * (Sz + Dz);
+  n[6] = w1 * (Sz - Dz);
+  // next-nearest neighbours
+  const R base = a[0] + a[4] + a[16];
+  const R P = a[5] + a[17], Qv = a[6] + a[18];
+  const R X = base + P + Qv, Y = base + P - Qv, Z = base - R(2) * P;
+  const R A = a[1] + a[10], B = a[2] + a[11], Cc = a[3] + a[12];
+  const R D3 = (A + B) + (a[13] - a[14]);
+  const R D4 = (A - B) + (a[13] + a[14]);
+  const R D5 = (A + Cc) - (a[13] - a[15]);
+  const R D6 = (A - Cc) - (a[13] + a[15]);
+  const R D7 = (B + Cc) + (a[14] - a[15]);
+  const R D8 = (B - Cc) + (a[14] + a[15]);
+  const R S3 = X + a[7], S4 = X - a[7];
+  const R S5 = Y + a[9], S6 = Y - a[9];
+  const R S7 = Z + a[8], S8 = Z - a[8];
+  n[7] = w2 * (S3 + D3);
+  n[8] = w2 * (S3 - D3);
+  n[9] = w2 * (S4 + D4);
+  n[10] = w2 * (S4 - D4);
+  n[11] = w2 * (S5 + D5);
+  n[12] = w2 * (S5 - D5);
+  n[13] = w2 * (S6 + D6);
+  n[14] = w2 * (S6 - D6);
+  n[15] = w2 * (S7 + D7);
+  n[16] = w2 * (S7 - D7);
+  n[17] = w2 * (S8 + D8);
+  n[18] = w2 * (S8 - D8);
+}
+
+// ---------------------------------------------------------------------------------------
 // LB kernel: pull-stream + collide for every node (Sec. II B, Eq. 3)
 // ---------------------------------------------------------------------------------------
+// One node of the LB step: pull the 19 populations from the neighbours in src (periodic),
+// collide, write the 19 post-collision populations of node (x, y, z) to dst.
 template <class S, class R, bool DEV, bool NOISE>
-__global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* __restrict__ dst,
-                                                  const FluidK<R> P, const uint32_t step) {
+__device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
+                                               const uint32_t step, const unsigned x, const unsigned y,
+                                               const unsigned z) {
   const unsigned L = P.L;
-  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned y = blockIdx.y * blockDim.y + threadIdx.y;
-  const unsigned z = blockIdx.z;
-  if (x >= L || y >= L) return;
   const unsigned xm = x ? x - 1 : L - 1, xp = (x + 1 < L) ? x + 1 : 0;
   const unsigned ym = y ? y - 1 : L - 1, yp = (y + 1 < L) ? y + 1 : 0;
   const unsigned zm = z ? z - 1 : L - 1, zp = (z + 1 < L) ? z + 1 : 0;
@@ -203,29 +280,15 @@ __global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* _
   }
   const unsigned node = x + y * L + z * LL;
 
-  // moments 0..9 from pair sums / differences (kinetic modes relax to zero: not needed)
-  R s[NPAIR], d[NPAIR];
-#pragma unroll
-  for (int p = 0; p < NPAIR; ++p) {
-    s[p] = n[2 * p + 1] + n[2 * p + 2];
-    d[p] = n[2 * p + 1] - n[2 * p + 2];
-  }
+  // moments 0..9 (the kinetic modes relax to zero and are not needed)
   R m[10];
-#pragma unroll
-  for (int k = 0; k < 10; ++k) {
-    R acc = (basis(k, 0) != 0) ? R(basis(k, 0)) * n[0] : R(0);
-#pragma unroll
-    for (int p = 0; p < NPAIR; ++p) {
-      const int c = basis(k, 2 * p + 1);
-      if (c != 0) acc += R(c) * (odd_mode(k) ? d[p] : s[p]);
-    }
-    m[k] = acc;
-  }
-
+  moments_0_9<R>(n, m);
   const R rho = DEV ? P.rho0 + m[0] : m[0];
   const R jx = m[1], jy = m[2], jz = m[3];
   const R ir = R(1) / rho;
   const R xx = jx * jx * ir, yy = jy * jy * ir, zz = jz * jz * ir;
+  // post-collision moments: relaxation of the stress modes towards equilibrium (Eq. 4),
+  // kinetic modes to zero, then the fluctuating part
   R ms[Q];
   ms[0] = m[0];
   ms[1] = jx;
@@ -252,26 +315,26 @@ __global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* _
       atomicAdd(P.nonpos, 1ull);
     }
     R g[4];
-    gauss4<R>(step, node, 0u, P.k0, P.k1, g);
-    ms[4] += P.cnoise[4] * sr * g[0];
-    ms[5] += P.cnoise[5] * sr * g[1];
-    ms[6] += P.cnoise[6] * sr * g[2];
-    ms[7] += P.cnoise[7] * sr * g[3];
-    gauss4<R>(step, node, 1u, P.k0, P.k1, g);
-    ms[8] += P.cnoise[8] * sr * g[0];
-    ms[9] += P.cnoise[9] * sr * g[1];
+    gauss4_rk<R>(step, node, 0u, P.rk, g);
+    ms[4] += (P.cnoise[4] * sr) * g[0];
+    ms[5] += (P.cnoise[5] * sr) * g[1];
+    ms[6] += (P.cnoise[6] * sr) * g[2];
+    ms[7] += (P.cnoise[7] * sr) * g[3];
+    gauss4_rk<R>(step, node, 1u, P.rk, g);
+    ms[8] += (P.cnoise[8] * sr) * g[0];
+    ms[9] += (P.cnoise[9] * sr) * g[1];
     if (P.ncalls > 2) {
-      ms[10] = P.cnoise[10] * sr * g[2];
-      ms[11] = P.cnoise[11] * sr * g[3];
-      gauss4<R>(step, node, 2u, P.k0, P.k1, g);
-      ms[12] = P.cnoise[12] * sr * g[0];
-      ms[13] = P.cnoise[13] * sr * g[1];
-      ms[14] = P.cnoise[14] * sr * g[2];
-      ms[15] = P.cnoise[15] * sr * g[3];
-      gauss4<R>(step, node, 3u, P.k0, P.k1, g);
-      ms[16] = P.cnoise[16] * sr * g[0];
-      ms[17] = P.cnoise[17] * sr * g[1];
-      ms[18] = P.cnoise[18] * sr * g[2];
+      ms[10] = (P.cnoise[10] * sr) * g[2];
+      ms[11] = (P.cnoise[11] * sr) * g[3];
+      gauss4_rk<R>(step, node, 2u, P.rk, g);
+      ms[12] = (P.cnoise[12] * sr) * g[0];
+      ms[13] = (P.cnoise[13] * sr) * g[1];
+      ms[14] = (P.cnoise[14] * sr) * g[2];
+      ms[15] = (P.cnoise[15] * sr) * g[3];
+      gauss4_rk<R>(step, node, 3u, P.rk, g);
+      ms[16] = (P.cnoise[16] * sr) * g[0];
+      ms[17] = (P.cnoise[17] * sr) * g[1];
+      ms[18] = (P.cnoise[18] * sr) * g[2];
     }
   }
 
@@ -303,9 +366,21 @@ __global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* _
   a[17] = ms[17] * R(InvB<17>::v);
   a[18] = ms[18] * R(InvB<18>::v);
   R out[Q];
-  modes_to_pops(a, out);
+  pops_from_scaled<R>(a, out);
 #pragma unroll
   for (int i = 0; i < Q; ++i) st<S, R>(dst + (unsigned long long)i * plane + node, out[i]);
+}
+
+// LB kernel: pull-stream + collide for every node (Sec. II B, Eq. 3); 3D grid of
+// (x-row segments) x (y rows) x z planes.
+template <class S, class R, bool DEV, bool NOISE>
+__global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* __restrict__ dst,
+                                                  const FluidK<R> P, const uint32_t step) {
+  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned y = blockIdx.y * blockDim.y + threadIdx.y;
+  const unsigned z = blockIdx.z;
+  if (x >= P.L || y >= P.L) return;
+  lb_node_update<S, R, DEV, NOISE>(src, dst, P, step, x, y, z);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -419,10 +494,13 @@ __device__ __forceinline__ void gather_node(const S* __restrict__ pop, const Flu
   mom[3] = jz;
 }
 
+// One coupled bead step for one chain, run by one thread block (any size, multiple of 32):
+// velocity Verlet, FENE/WCA, interpolation of the post-stream flow at the 8 corners, friction
+// + Langevin force, and the deterministic spreading of the reaction into a list of
+// per-node population corrections.  `smem` holds max(6N R, sort keys) bytes.
 template <class S, class R, bool DEV>
-__global__ void __launch_bounds__(512) k_bead_step(const S* __restrict__ pop, const FluidK<R> P,
-                                                    const ChainK<R> C, const uint32_t step) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const FluidK<R>& P, const ChainK<R>& C,
+                                                const uint32_t step, unsigned char* smem) {
   const int N = C.N;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int L = (int)P.L;
@@ -598,7 +676,15 @@ __global__ void __launch_bounds__(512) k_bead_step(const S* __restrict__ pop, co
   }
 }
 
-// B[i][node] += dn_i at every pending node (each node appears once in the list)
+template <class S, class R, bool DEV>
+__global__ void __launch_bounds__(512) k_bead_step(const S* __restrict__ pop, const FluidK<R> P,
+                                                    const ChainK<R> C, const uint32_t step) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bead_step_block<S, R, DEV>(pop, P, C, step, smem);
+}
+
+// B[i][node] += dn_i at every pending node (each node appears once in the list); one thread
+// per (node, population): blockIdx.y is the population
 template <class S, class R>
 __global__ void __launch_bounds__(256) k_apply_pending(S* __restrict__ pop, const FluidK<R> P,
                                                         const int* __restrict__ p_node,
@@ -606,12 +692,9 @@ __global__ void __launch_bounds__(256) k_apply_pending(S* __restrict__ pop, cons
                                                         const int* __restrict__ p_count, int cap) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= *p_count) return;
-  const unsigned node = (unsigned)p_node[u];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    S* p = pop + (unsigned long long)i * P.plane + node;
-    st<S, R>(p, ld<S, R>(p) + p_dn[i * cap + u]);
-  }
+  const int i = blockIdx.y;
+  S* p = pop + (unsigned long long)i * P.plane + (unsigned)p_node[u];
+  st<S, R>(p, ld<S, R>(p) + p_dn[i * cap + u]);
 }
 
 // ---------------------------------------------------------------------------------------

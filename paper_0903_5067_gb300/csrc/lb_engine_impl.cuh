@@ -103,11 +103,23 @@ class EngineT final : public Engine {
     cuda_check(cudaGetLastError(), "LB kernel");
     if (N_ > 0) {
       cuda_check(cudaStreamWaitEvent(s, ev_bead_, 0), "wait bead");
-      k_apply_pending<S, R><<<(cap_ + 255) / 256, 256, 0, s>>>(Bo, P, p_node_, p_dn_, p_count_, cap_);
+      k_apply_pending<S, R><<<dim3((cap_ + 255) / 256, Q), 256, 0, s>>>(Bo, P, p_node_, p_dn_, p_count_, cap_);
       cuda_check(cudaGetLastError(), "apply kernel");
     }
     cur_ ^= 1;
   }
+
+  // --- access for the batched driver (one engine per replica, stepped in lockstep) ---
+  FluidK<R> fluid_params() const { return fluid(); }
+  ChainK<R> chain_params() const { return chain(); }
+  S* buffer(int i) const { return pop_[i]; }
+  int parity() const { return cur_; }
+  void flip() { cur_ ^= 1; }
+  unsigned long long nodes() const { return nnodes_; }
+  int pending_capacity() const { return cap_; }
+  size_t bead_smem_bytes() const { return bead_smem(); }
+  int chain_length() const { return N_; }
+  const Config& config() const { return cfg_; }
 
   ~EngineT() override {
     if (side_) cudaStreamDestroy(side_);
@@ -243,7 +255,10 @@ class EngineT final : public Engine {
 
   void ensure_side_stream() {
     if (side_) return;
-    cuda_check(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking), "side stream");
+    // highest priority: the bead CTA is dispatched ahead of the LB kernel's queued CTAs
+    int least = 0, greatest = 0;
+    cuda_check(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
+    cuda_check(cudaStreamCreateWithPriority(&side_, cudaStreamNonBlocking, greatest), "side stream");
     cuda_check(cudaEventCreateWithFlags(&ev_ready_, cudaEventDisableTiming), "event");
     cuda_check(cudaEventCreateWithFlags(&ev_bead_, cudaEventDisableTiming), "event");
   }
@@ -291,6 +306,7 @@ class EngineT final : public Engine {
     }
     P.k0 = (uint32_t)(c.seed & 0xffffffffu);
     P.k1 = (uint32_t)(0u | ((uint32_t)c.replica << 8));
+    P.rk = make_round_keys(P.k0, P.k1);
     double body[3] = {0, 0, 0};
     if (c.counter_force && c.N > 0) {
       const double vol = pow(c.L * c.a, 3);

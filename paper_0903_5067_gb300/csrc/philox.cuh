@@ -41,6 +41,35 @@ __host__ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t
   return c;
 }
 
+// The ten round keys of a Philox key, computed once on the host and passed in a kernel's
+// parameter block, so that each round costs two 32x32->64-bit multiplies and two
+// three-input xors.
+struct RoundKeys {
+  uint32_t k0[10], k1[10];
+};
+
+inline RoundKeys make_round_keys(uint32_t k0, uint32_t k1) {
+  RoundKeys rk;
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0;
+    rk.k1[r] = k1;
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return rk;
+}
+
+__device__ __forceinline__ U4 philox4x32_10_rk(U4 c, const RoundKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c.x;
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * c.z;
+    c = U4{(uint32_t)(p1 >> 32) ^ c.y ^ rk.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk.k1[r],
+           (uint32_t)p0};
+  }
+  return c;
+}
+
 // u = ((x >> 9) + 1/2) * 2^-23 in (0, 1): 23 random bits, exact in float and double.
 __device__ __forceinline__ float uniform_f32(uint32_t x) {
   // 1 + (x>>9) 2^-23 in [1, 2), minus (1 - 2^-24): exact (Sterbenz), result representable
@@ -70,6 +99,38 @@ __device__ __forceinline__ void box_muller(double u0, double u1, double& g0, dou
   g1 = r * s;
 }
 
+// -ln(u), u in (0, 1), single precision.  The hardware log2 has an absolute error bound
+// of 2^-22 on [0.5, 2], which would dominate the result near u = 1 (where the Box-Muller
+// radius is small); there, with t = 1 - u (exact), -ln(1 - t) is summed as its Taylor series
+// t + t^2/2 + ... + t^6/6 (truncation below 1e-8 relative for t < 1/16).
+__device__ __forceinline__ float neg_log_unit(float u) {
+  const float t = 1.0f - u;
+  const float series =
+      t * (1.0f + t * (0.5f + t * (0.333333343f + t * (0.25f + t * (0.2f + t * 0.166666672f)))));
+  const float fast = -0.693147182f * __log2f(u);
+  return t < 0.0625f ? series : fast;
+}
+
+// Box-Muller in single precision on the hardware transcendental units:
+// r = sqrt(-2 ln u0) as x * rsqrt(x), angle reduced to (-pi, pi) (see box_muller above).
+__device__ __forceinline__ void box_muller_fast(float u0, float u1, float& g0, float& g1) {
+  const float x = 2.0f * neg_log_unit(u0);
+  const float r = x * rsqrtf(x);
+  float s, c;
+  __sincosf(6.28318530717958647692f * (u1 - 0.5f), &s, &c);
+  g0 = -r * c;
+  g1 = -r * s;
+}
+
+template <class R>
+__device__ __forceinline__ void box_muller_lb(R u0, R u1, R& g0, R& g1) {
+  box_muller(u0, u1, g0, g1);
+}
+template <>
+__device__ __forceinline__ void box_muller_lb<float>(float u0, float u1, float& g0, float& g1) {
+  box_muller_fast(u0, u1, g0, g1);
+}
+
 template <class R>
 __device__ __forceinline__ R uniform01(uint32_t x);
 template <>
@@ -84,6 +145,16 @@ __device__ __forceinline__ void gauss4(uint32_t step, uint32_t index, uint32_t c
   const U4 r = philox4x32_10(U4{step, index, call, 0u}, k0, k1);
   box_muller(uniform01<R>(r.x), uniform01<R>(r.y), g[0], g[1]);
   box_muller(uniform01<R>(r.z), uniform01<R>(r.w), g[2], g[3]);
+}
+
+// Four standard normals from one Philox call (precomputed round keys), the fluid's
+// transform: fast single-precision Box-Muller for float, the full-precision one for double.
+template <class R>
+__device__ __forceinline__ void gauss4_rk(uint32_t step, uint32_t index, uint32_t call, const RoundKeys& rk,
+                                          R g[4]) {
+  const U4 r = philox4x32_10_rk(U4{step, index, call, 0u}, rk);
+  box_muller_lb<R>(uniform01<R>(r.x), uniform01<R>(r.y), g[0], g[1]);
+  box_muller_lb<R>(uniform01<R>(r.z), uniform01<R>(r.w), g[2], g[3]);
 }
 
 }  // namespace gblb

@@ -55,3 +55,22 @@ def perturbation(L: int, q: int = 19, amplitude: float = 1e-2, seed: int = 0) ->
     multiplies a rest state by (1 + this) to start away from equilibrium."""
     rng = np.random.default_rng(np.random.PCG64(seed + 104729))
     return amplitude * (2.0 * rng.random((q, L, L, L)) - 1.0)
+
+
+def c4_ensemble(R: int = 64, base_seed: int = 100):
+    """The batched-replica workload: replica r has box L_r = (16, 24, 32, 48, 64)[r mod 5] and
+    chain N_r = (8, 16, 32, 64)[(r // 5) mod 4], stepped down while L_r < 2 R_g,est(N_r)
+    (R_g,est^2 = 0.97^2 N^(2*0.588) / 6.5: Flory exponent and the R_e^2/R_g^2 ratio ~6.5 of the
+    paper's Table 1), seed base_seed + r, self-avoiding initial walk.
+    Returns (L list, N list, seeds, list of (N_r, 3) position arrays)."""
+    Ls, Ns, seeds, X = [], [], [], []
+    for r in range(R):
+        L = (16, 24, 32, 48, 64)[r % 5]
+        N = (8, 16, 32, 64)[(r // 5) % 4]
+        while N > 8 and L < 2.0 * np.sqrt(0.97 ** 2 * N ** (2 * 0.588) / 6.5):
+            N //= 2
+        Ls.append(L)
+        Ns.append(N)
+        seeds.append(base_seed + r)
+        X.append(chain_walk(N, L=L, bond=0.97, seed=base_seed + r, self_avoiding=True))
+    return Ls, Ns, seeds, X

@@ -52,6 +52,22 @@ _SIGS = {
     "lb_philox4x32_10": (C.c_int, [_vp, C.c_int64, C.c_uint32, C.c_uint32, _vp, _vp]),
     "lb_cell_index_f32": (C.c_int, [_vp, C.c_int64, C.c_float, C.c_int, _vp, _vp]),
     "lb_fluid_sums_noalloc": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double, _dp, _vp]),
+    "lb_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_uint64), C.c_double, C.c_double, C.c_double, C.c_double,
+                                  C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                  C.c_double, C.c_double, _dp, C.c_int]),
+    "lb_batch_set_stream": (C.c_int, [_vp, _vp]),
+    "lb_batch_workspace_size": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
+    "lb_batch_bind_workspace": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "lb_batch_set_shape": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "lb_batch_autotune": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "lb_batch_step": (C.c_int, [_vp, C.c_int64]),
+    "lb_batch_sync": (C.c_int, [_vp]),
+    "lb_batch_get_populations": (C.c_int, [_vp, C.c_int, _dp, C.c_size_t]),
+    "lb_batch_get_beads": (C.c_int, [_vp, C.c_int, _dp, _dp, C.c_size_t]),
+    "lb_batch_get_observables": (C.c_int, [_vp, C.c_int, _dp, C.c_size_t]),
+    "lb_batch_nodes": (C.c_int64, [_vp]),
+    "lb_batch_destroy": (None, [_vp]),
 }
 LB_NOALLOC_MAX_L = 256
 for _name, (_res, _args) in _SIGS.items():
@@ -197,6 +213,124 @@ def lb_fluid_sums_noalloc(pop_dev_ptr: int, L: int, a: float, h: float, stream: 
     _check(_lib.lb_fluid_sums_noalloc(_vp(pop_dev_ptr), int(L), a, h, _dbuf(out), _vp(stream) if stream else None),
            "lb_fluid_sums_noalloc")
     return out
+
+
+def lb_batch_create(L, N, seeds, rho, eta, eta_b, kT, h, a, m, zeta, k_fene, R0, eps, sigma, x0, precision):
+    R = len(L)
+    Ls = (C.c_int * R)(*[int(v) for v in L])
+    Ns = (C.c_int * R)(*[int(v) for v in N])
+    Ss = (C.c_uint64 * R)(*[int(v) for v in seeds])
+    xa = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).reshape(-1)
+    b = _vp()
+    _check(_lib.lb_batch_create(C.byref(b), R, Ls, Ns, Ss, rho, eta, eta_b, kT, h, a, m, zeta, k_fene, R0, eps,
+                                sigma, _dbuf(xa), int(precision)), "lb_batch_create")
+    return b
+
+
+def lb_batch_set_stream(b, stream_handle: int):
+    _check(_lib.lb_batch_set_stream(b, _vp(stream_handle) if stream_handle else None), "lb_batch_set_stream")
+
+
+def lb_batch_workspace_size(b) -> int:
+    n = C.c_size_t()
+    _check(_lib.lb_batch_workspace_size(b, C.byref(n)), "lb_batch_workspace_size")
+    return n.value
+
+
+def lb_batch_bind_workspace(b, device_ptr: int, nbytes: int):
+    _check(_lib.lb_batch_bind_workspace(b, _vp(device_ptr), nbytes), "lb_batch_bind_workspace")
+
+
+def lb_batch_set_shape(b, threads: int, blocks_per_sm: int):
+    _check(_lib.lb_batch_set_shape(b, int(threads), int(blocks_per_sm)), "lb_batch_set_shape")
+
+
+def lb_batch_autotune(b):
+    t, k = C.c_int(), C.c_int()
+    _check(_lib.lb_batch_autotune(b, C.byref(t), C.byref(k)), "lb_batch_autotune")
+    return t.value, k.value
+
+
+def lb_batch_step(b, n: int):
+    _check(_lib.lb_batch_step(b, int(n)), "lb_batch_step")
+
+
+def lb_batch_sync(b):
+    _check(_lib.lb_batch_sync(b), "lb_batch_sync")
+
+
+def lb_batch_get_populations(b, r: int, out: np.ndarray):
+    _check(_lib.lb_batch_get_populations(b, int(r), _dbuf(out), out.size), "lb_batch_get_populations")
+
+
+def lb_batch_get_beads(b, r: int, x, v, cap: int):
+    _check(_lib.lb_batch_get_beads(b, int(r), _dbuf(x), _dbuf(v), cap), "lb_batch_get_beads")
+
+
+def lb_batch_get_observables(b, r: int) -> np.ndarray:
+    out = np.zeros(LB_NOBS)
+    _check(_lib.lb_batch_get_observables(b, int(r), _dbuf(out), out.size), "lb_batch_get_observables")
+    return out
+
+
+def lb_batch_nodes(b) -> int:
+    return int(_lib.lb_batch_nodes(b))
+
+
+def lb_batch_destroy(b):
+    _lib.lb_batch_destroy(b)
+
+
+class Batch:
+    """R replicas (box sizes L[r], chains N[r] with positions X0[r]) on the current device,
+    workspace in a torch tensor, work on torch's current stream."""
+
+    def __init__(self, L, N, seeds, X0, rho=1.0, eta=3.0, eta_b=3.0, kT=1.0, h=0.01, a=1.0, m=1.0, zeta=20.8,
+                 k_fene=30.0, R0=1.5, eps=1.0, sigma=1.0, precision=LB_FP32):
+        import torch
+
+        self.L = [int(v) for v in L]
+        self.N = [int(v) for v in N]
+        xs = [np.asarray(x, dtype=np.float64).reshape(-1) for x, n in zip(X0, self.N) if n > 0]
+        x0 = np.concatenate(xs) if xs else None
+        self.b = lb_batch_create(self.L, self.N, seeds, rho, eta, eta_b, kT, h, a, m, zeta, k_fene, R0, eps,
+                                 sigma, x0, precision)
+        lb_batch_set_stream(self.b, torch.cuda.current_stream().cuda_stream)
+        nbytes = lb_batch_workspace_size(self.b)
+        self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        lb_batch_bind_workspace(self.b, self._ws.data_ptr(), nbytes)
+
+    def step(self, n=1):
+        lb_batch_step(self.b, n)
+
+    def sync(self):
+        lb_batch_sync(self.b)
+
+    def populations(self, r):
+        out = np.empty((19, self.L[r], self.L[r], self.L[r]))
+        lb_batch_get_populations(self.b, r, out)
+        return out
+
+    def beads(self, r):
+        x = np.empty((self.N[r], 3))
+        v = np.empty((self.N[r], 3))
+        lb_batch_get_beads(self.b, r, x, v, 3 * self.N[r])
+        return x, v
+
+    def observables(self, r):
+        return lb_batch_get_observables(self.b, r)
+
+    def close(self):
+        if self.b:
+            lb_batch_destroy(self.b)
+            self.b = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # --- convenience wrapper ---------------------------------------------------------------
