@@ -52,57 +52,50 @@ __device__ __forceinline__ unsigned div_small(unsigned n, unsigned L, float invL
   return (unsigned)q;
 }
 
+// Per-replica fields of the batched LB kernel; the shared fluid parameters and up to
+// kBatchGroup replicas travel in the kernel's parameter block (constant bank), so the
+// collision's coefficients stay instruction operands as in the single-box kernel.
+constexpr int kBatchGroup = 64;
+
+template <class S>
+struct BatchRep {
+  S* pop[2];
+  unsigned long long nnodes, tile0, plane;
+  unsigned long long* nonpos;
+  unsigned L;
+  float invL;
+};
+
+template <class S, class R>
+struct BatchLB {
+  FluidK<R> P;
+  int nrep;
+  unsigned long long total_tiles;
+  BatchRep<S> rep[kBatchGroup];
+  RoundKeys rk[kBatchGroup];
+};
+
 template <class S, class R, bool DEV, bool NOISE>
-__global__ void __launch_bounds__(512) k_batch_lb(const ReplicaK<S, R>* __restrict__ reps, int nrep,
-                                                   unsigned long long total_tiles, int parity,
+__global__ void __launch_bounds__(512) k_batch_lb(const __grid_constant__ BatchLB<S, R> B, int parity,
                                                    const uint32_t* __restrict__ d_step, uint32_t j) {
-  __shared__ FluidK<R> sP;
-  __shared__ S* s_src;
-  __shared__ S* s_dst;
-  __shared__ unsigned long long s_n, s_t0, s_t1;
-  __shared__ float s_invL;
-  __shared__ int s_rep;
   const uint32_t step = *d_step + j;
   const unsigned T = blockDim.x;
   // contiguous chunk of tiles per block: consecutive tiles mostly share a replica
-  const unsigned long long per = (total_tiles + gridDim.x - 1) / gridDim.x;
+  const unsigned long long per = (B.total_tiles + gridDim.x - 1) / gridDim.x;
   const unsigned long long t_begin = blockIdx.x * per;
-  const unsigned long long t_end = t_begin + per < total_tiles ? t_begin + per : total_tiles;
-  if (threadIdx.x == 0) s_rep = -1;
-  __syncthreads();  // s_rep, s_t1 are read by every thread: the reload branch stays uniform
+  const unsigned long long t_end = t_begin + per < B.total_tiles ? t_begin + per : B.total_tiles;
+  int r = 0;
   for (unsigned long long tile = t_begin; tile < t_end; ++tile) {
-    if (s_rep < 0 || tile >= s_t1) {  // uniform: every thread sees the same s_rep, s_t1
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int lo = 0, hi = nrep - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (reps[mid].tile0 <= tile)
-            lo = mid;
-          else
-            hi = mid - 1;
-        }
-        s_rep = lo;
-        s_src = reps[lo].pop[parity];
-        s_dst = reps[lo].pop[parity ^ 1];
-        s_n = reps[lo].nnodes;
-        s_t0 = reps[lo].tile0;
-        s_t1 = lo + 1 < nrep ? reps[lo + 1].tile0 : total_tiles;
-        s_invL = reps[lo].invL;
-      }
-      __syncthreads();
-      const unsigned* src = reinterpret_cast<const unsigned*>(&reps[s_rep].P);
-      unsigned* dst = reinterpret_cast<unsigned*>(&sP);
-      for (unsigned w = threadIdx.x; w < sizeof(FluidK<R>) / 4; w += T) dst[w] = src[w];
-    }
-    __syncthreads();
-    const unsigned long long node = (tile - s_t0) * T + threadIdx.x;
-    if (node < s_n) {
-      const unsigned L = sP.L;
+    while (r + 1 < B.nrep && B.rep[r + 1].tile0 <= tile) ++r;  // uniform
+    const BatchRep<S>& rp = B.rep[r];
+    const unsigned long long node = (tile - rp.tile0) * T + threadIdx.x;
+    if (node < rp.nnodes) {
+      const unsigned L = rp.L;
       unsigned x, y;
-      const unsigned t = div_small((unsigned)node, L, s_invL, x);
-      const unsigned z = div_small(t, L, s_invL, y);
-      lb_node_update<S, R, DEV, NOISE>(s_src, s_dst, sP, step, x, y, z);
+      const unsigned t = div_small((unsigned)node, L, rp.invL, x);
+      const unsigned z = div_small(t, L, rp.invL, y);
+      lb_node_update<S, R, DEV, NOISE>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r], rp.nonpos,
+                                       step, x, y, z);
     }
   }
 }
@@ -306,6 +299,30 @@ class BatchT final : public Batch {
       t += (q.nnodes + threads_ - 1) / threads_;
     }
     total_tiles_ = t;
+    groups_.clear();
+    for (size_t g0 = 0; g0 < eng_.size(); g0 += kBatchGroup) {
+      BatchLB<S, R> G;
+      memset(&G, 0, sizeof(G));
+      G.P = tab[g0].P;
+      unsigned long long tt = 0;
+      const size_t g1 = g0 + kBatchGroup < eng_.size() ? g0 + kBatchGroup : eng_.size();
+      G.nrep = (int)(g1 - g0);
+      for (size_t r = g0; r < g1; ++r) {
+        BatchRep<S>& q = G.rep[r - g0];
+        q.pop[0] = tab[r].pop[0];
+        q.pop[1] = tab[r].pop[1];
+        q.nnodes = tab[r].nnodes;
+        q.tile0 = tt;
+        q.plane = tab[r].P.plane;
+        q.nonpos = tab[r].P.nonpos;
+        q.L = tab[r].P.L;
+        q.invL = tab[r].invL;
+        G.rk[r - g0] = tab[r].P.rk;
+        tt += (q.nnodes + threads_ - 1) / threads_;
+      }
+      G.total_tiles = tt;
+      groups_.push_back(G);
+    }
     cuda_check(cudaMemcpyAsync(d_reps_, tab.data(), tab.size() * sizeof(ReplicaK<S, R>), cudaMemcpyHostToDevice, s),
                "upload replica table");
     cuda_check(cudaStreamSynchronize(s), "sync table");
@@ -321,21 +338,18 @@ class BatchT final : public Batch {
     k_batch_bead<S, R, DEV><<<R_, 512, smem_, side_>>>(d_reps_, par, d_step_, j);
     cuda_check(cudaGetLastError(), "batch bead");
     cuda_check(cudaEventRecord(ev_bead_, side_), "record bead");
-    unsigned grid;
-    if (bps_ == 0) {
-      grid = (unsigned)total_tiles_;
-    } else {
-      int dev = 0, sms = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      grid = (unsigned)(sms * bps_);
-      if (grid > total_tiles_) grid = (unsigned)total_tiles_;
+    int dev = 0, sms = 0;
+    cuda_check(cudaGetDevice(&dev), "device");
+    cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    for (const BatchLB<S, R>& G : groups_) {
+      unsigned grid = (unsigned)G.total_tiles;
+      if (bps_ > 0 && (unsigned long long)sms * bps_ < G.total_tiles) grid = (unsigned)(sms * bps_);
+      if (noise_)
+        k_batch_lb<S, R, DEV, true><<<grid, threads_, 0, s>>>(G, par, d_step_, j);
+      else
+        k_batch_lb<S, R, DEV, false><<<grid, threads_, 0, s>>>(G, par, d_step_, j);
+      cuda_check(cudaGetLastError(), "batch LB");
     }
-    if (noise_)
-      k_batch_lb<S, R, DEV, true><<<grid, threads_, 0, s>>>(d_reps_, R_, total_tiles_, par, d_step_, j);
-    else
-      k_batch_lb<S, R, DEV, false><<<grid, threads_, 0, s>>>(d_reps_, R_, total_tiles_, par, d_step_, j);
-    cuda_check(cudaGetLastError(), "batch LB");
     cuda_check(cudaStreamWaitEvent(s, ev_bead_, 0), "wait bead");
     k_batch_apply<S, R><<<dim3((cap_max_ + 255) / 256, Q, R_), 256, 0, s>>>(d_reps_, par);
     cuda_check(cudaGetLastError(), "batch apply");
@@ -358,6 +372,7 @@ class BatchT final : public Batch {
   }
 
   std::vector<std::unique_ptr<EngineT<S, R, DEV>>> eng_;
+  std::vector<BatchLB<S, R>> groups_;
   std::vector<std::vector<double>> x0_;
   std::vector<size_t> offs_;
   size_t table_off_ = 0, step_off_ = 0, bytes_ = 0, smem_ = 0;

@@ -51,6 +51,9 @@ struct FluidK {
   R rho0;
   R gs, gb;        // relaxation eigenvalues: shear modes 5..9, bulk mode 4 (kinetic modes: 0)
   R cnoise[Q];     // sqrt(mu b_k (1 - gamma_k^2)), mode k's noise per sqrt(rho); 0 if silent
+  // the same relaxation and noise in terms of the scaled moments a_k = m*_k / b_k used by the
+  // back-transform: a_k = am_k m_k + ae_k m_eq,k + ag_k sqrt(rho) g_k  (k = 4..18)
+  R am[Q], ae[Q], ag[Q];
   uint32_t k0, k1; // Philox key of the fluid stream
   RoundKeys rk;    // its ten round keys
   int ncalls;      // Philox calls per node: 0 (noise off), 2 (stress modes only), 4 (all)
@@ -257,11 +260,14 @@ __host__ __device__ __forceinline__ void pops_from_scaled(const R a[Q], R n[Q]) 
 // ---------------------------------------------------------------------------------------
 // One node of the LB step: pull the 19 populations from the neighbours in src (periodic),
 // collide, write the 19 post-collision populations of node (x, y, z) to dst.
+// (L, plane, rk, nonpos: the box's size, plane stride, noise keys and counter, which the
+// batched kernel takes per replica; P: the remaining, shared parameters)
 template <class S, class R, bool DEV, bool NOISE>
 __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
+                                               const unsigned L, const unsigned long long plane,
+                                               const RoundKeys& rk, unsigned long long* nonpos,
                                                const uint32_t step, const unsigned x, const unsigned y,
                                                const unsigned z) {
-  const unsigned L = P.L;
   const unsigned xm = x ? x - 1 : L - 1, xp = (x + 1 < L) ? x + 1 : 0;
   const unsigned ym = y ? y - 1 : L - 1, yp = (y + 1 < L) ? y + 1 : 0;
   const unsigned zm = z ? z - 1 : L - 1, zp = (z + 1 < L) ? z + 1 : 0;
@@ -270,7 +276,6 @@ __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __r
   const unsigned ry[3] = {yp * L, y * L, ym * L};
   const unsigned rz[3] = {zp * LL, z * LL, zm * LL};
   const unsigned sxs[3] = {xp, x, xm};
-  const unsigned long long plane = P.plane;
 
   R n[Q];
 #pragma unroll
@@ -287,84 +292,72 @@ __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __r
   const R jx = m[1], jy = m[2], jz = m[3];
   const R ir = R(1) / rho;
   const R xx = jx * jx * ir, yy = jy * jy * ir, zz = jz * jz * ir;
-  // post-collision moments: relaxation of the stress modes towards equilibrium (Eq. 4),
-  // kinetic modes to zero, then the fluctuating part
-  R ms[Q];
-  ms[0] = m[0];
-  ms[1] = jx;
-  ms[2] = jy;
-  ms[3] = jz;
+  // post-collision moments, directly as scaled moments a_k = m*_k / b_k: relaxation of the
+  // stress modes towards equilibrium (Eq. 4), kinetic modes to zero, plus the fluctuating
+  // part sqrt(rho) phi_k g_k / b_k
+  R a[Q];
+  a[0] = m[0];
+  a[1] = jx * R(InvB<1>::v);
+  a[2] = jy * R(InvB<2>::v);
+  a[3] = jz * R(InvB<3>::v);
   {
     const R e4 = xx + yy + zz, e5 = R(2) * xx - yy - zz, e6 = yy - zz;
     const R e7 = jx * jy * ir, e8 = jy * jz * ir, e9 = jx * jz * ir;
-    ms[4] = e4 + P.gb * (m[4] - e4);
-    ms[5] = e5 + P.gs * (m[5] - e5);
-    ms[6] = e6 + P.gs * (m[6] - e6);
-    ms[7] = e7 + P.gs * (m[7] - e7);
-    ms[8] = e8 + P.gs * (m[8] - e8);
-    ms[9] = e9 + P.gs * (m[9] - e9);
+    a[4] = P.am[4] * m[4] + P.ae[4] * e4;
+    a[5] = P.am[5] * m[5] + P.ae[5] * e5;
+    a[6] = P.am[6] * m[6] + P.ae[6] * e6;
+    a[7] = P.am[7] * m[7] + P.ae[7] * e7;
+    a[8] = P.am[8] * m[8] + P.ae[8] * e8;
+    a[9] = P.am[9] * m[9] + P.ae[9] * e9;
   }
 #pragma unroll
-  for (int k = 10; k < Q; ++k) ms[k] = R(0);
+  for (int k = 10; k < Q; ++k) a[k] = R(0);
 
   if (NOISE) {
     R sr = R(0);
     if (rho > R(0)) {
       sr = sqrt(rho);
     } else {
-      atomicAdd(P.nonpos, 1ull);
+      atomicAdd(nonpos, 1ull);
     }
-    R g[4];
-    gauss4_rk<R>(step, node, 0u, P.rk, g);
-    ms[4] += (P.cnoise[4] * sr) * g[0];
-    ms[5] += (P.cnoise[5] * sr) * g[1];
-    ms[6] += (P.cnoise[6] * sr) * g[2];
-    ms[7] += (P.cnoise[7] * sr) * g[3];
-    gauss4_rk<R>(step, node, 1u, P.rk, g);
-    ms[8] += (P.cnoise[8] * sr) * g[0];
-    ms[9] += (P.cnoise[9] * sr) * g[1];
+    R g[4];  // sqrt(rho) g
+    gauss4_rk<R>(step, node, 0u, rk, sr, g);
+    a[4] += P.ag[4] * g[0];
+    a[5] += P.ag[5] * g[1];
+    a[6] += P.ag[6] * g[2];
+    a[7] += P.ag[7] * g[3];
+    gauss4_rk<R>(step, node, 1u, rk, sr, g);
+    a[8] += P.ag[8] * g[0];
+    a[9] += P.ag[9] * g[1];
     if (P.ncalls > 2) {
-      ms[10] = (P.cnoise[10] * sr) * g[2];
-      ms[11] = (P.cnoise[11] * sr) * g[3];
-      gauss4_rk<R>(step, node, 2u, P.rk, g);
-      ms[12] = (P.cnoise[12] * sr) * g[0];
-      ms[13] = (P.cnoise[13] * sr) * g[1];
-      ms[14] = (P.cnoise[14] * sr) * g[2];
-      ms[15] = (P.cnoise[15] * sr) * g[3];
-      gauss4_rk<R>(step, node, 3u, P.rk, g);
-      ms[16] = (P.cnoise[16] * sr) * g[0];
-      ms[17] = (P.cnoise[17] * sr) * g[1];
-      ms[18] = (P.cnoise[18] * sr) * g[2];
+      a[10] = P.ag[10] * g[2];
+      a[11] = P.ag[11] * g[3];
+      gauss4_rk<R>(step, node, 2u, rk, sr, g);
+      a[12] = P.ag[12] * g[0];
+      a[13] = P.ag[13] * g[1];
+      a[14] = P.ag[14] * g[2];
+      a[15] = P.ag[15] * g[3];
+      gauss4_rk<R>(step, node, 3u, rk, sr, g);
+      a[16] = P.ag[16] * g[0];
+      a[17] = P.ag[17] * g[1];
+      a[18] = P.ag[18] * g[2];
     }
   }
 
   if (P.body_on) {
     R dm[10];
     force_moments(rho, jx, jy, jz, P.body_dJ[0], P.body_dJ[1], P.body_dJ[2], P.gs, P.gb, dm);
-#pragma unroll
-    for (int k = 1; k < 10; ++k) ms[k] += dm[k];
+    a[1] += dm[1] * R(InvB<1>::v);
+    a[2] += dm[2] * R(InvB<2>::v);
+    a[3] += dm[3] * R(InvB<3>::v);
+    a[4] += dm[4] * R(InvB<4>::v);
+    a[5] += dm[5] * R(InvB<5>::v);
+    a[6] += dm[6] * R(InvB<6>::v);
+    a[7] += dm[7] * R(InvB<7>::v);
+    a[8] += dm[8] * R(InvB<8>::v);
+    a[9] += dm[9] * R(InvB<9>::v);
   }
 
-  R a[Q];
-  a[0] = ms[0];
-  a[1] = ms[1] * R(InvB<1>::v);
-  a[2] = ms[2] * R(InvB<2>::v);
-  a[3] = ms[3] * R(InvB<3>::v);
-  a[4] = ms[4] * R(InvB<4>::v);
-  a[5] = ms[5] * R(InvB<5>::v);
-  a[6] = ms[6] * R(InvB<6>::v);
-  a[7] = ms[7] * R(InvB<7>::v);
-  a[8] = ms[8] * R(InvB<8>::v);
-  a[9] = ms[9] * R(InvB<9>::v);
-  a[10] = ms[10] * R(InvB<10>::v);
-  a[11] = ms[11] * R(InvB<11>::v);
-  a[12] = ms[12] * R(InvB<12>::v);
-  a[13] = ms[13] * R(InvB<13>::v);
-  a[14] = ms[14] * R(InvB<14>::v);
-  a[15] = ms[15] * R(InvB<15>::v);
-  a[16] = ms[16] * R(InvB<16>::v);
-  a[17] = ms[17] * R(InvB<17>::v);
-  a[18] = ms[18] * R(InvB<18>::v);
   R out[Q];
   pops_from_scaled<R>(a, out);
 #pragma unroll
@@ -380,7 +373,7 @@ __global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* _
   const unsigned y = blockIdx.y * blockDim.y + threadIdx.y;
   const unsigned z = blockIdx.z;
   if (x >= P.L || y >= P.L) return;
-  lb_node_update<S, R, DEV, NOISE>(src, dst, P, step, x, y, z);
+  lb_node_update<S, R, DEV, NOISE>(src, dst, P, P.L, P.plane, P.rk, P.nonpos, step, x, y, z);
 }
 
 // ---------------------------------------------------------------------------------------

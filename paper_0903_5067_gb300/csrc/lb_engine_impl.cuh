@@ -302,7 +302,11 @@ class EngineT final : public Engine {
       if (k >= 5 && k <= 9) g = gs;
       const double bk = norm36(k) / 36.0;
       const bool on = noise && k >= 4 && (k <= 9 || !c.stress_only);
-      P.cnoise[k] = on ? (R)sqrt(mu * bk * (1.0 - g * g)) : (R)0;
+      const double cn = on ? sqrt(mu * bk * (1.0 - g * g)) : 0.0;
+      P.cnoise[k] = (R)cn;
+      P.am[k] = (R)(g / bk);
+      P.ae[k] = (R)((1.0 - g) / bk);
+      P.ag[k] = (R)(cn / bk);
     }
     P.k0 = (uint32_t)(c.seed & 0xffffffffu);
     P.k1 = (uint32_t)(0u | ((uint32_t)c.replica << 8));

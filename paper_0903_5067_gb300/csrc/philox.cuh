@@ -102,33 +102,35 @@ __device__ __forceinline__ void box_muller(double u0, double u1, double& g0, dou
 // -ln(u), u in (0, 1), single precision.  The hardware log2 has an absolute error bound
 // of 2^-22 on [0.5, 2], which would dominate the result near u = 1 (where the Box-Muller
 // radius is small); there, with t = 1 - u (exact), -ln(1 - t) is summed as its Taylor series
-// t + t^2/2 + ... + t^6/6 (truncation below 1e-8 relative for t < 1/16).
+// t + t^2/2 + t^3/3 (truncation below 3e-10 relative for t < 1e-3).
 __device__ __forceinline__ float neg_log_unit(float u) {
   const float t = 1.0f - u;
-  const float series =
-      t * (1.0f + t * (0.5f + t * (0.333333343f + t * (0.25f + t * (0.2f + t * 0.166666672f)))));
+  const float series = t * (1.0f + t * (0.5f + t * 0.333333343f));
   const float fast = -0.693147182f * __log2f(u);
-  return t < 0.0625f ? series : fast;
+  return t < 1.0e-3f ? series : fast;
 }
 
-// Box-Muller in single precision on the hardware transcendental units:
-// r = sqrt(-2 ln u0) as x * rsqrt(x), angle reduced to (-pi, pi) (see box_muller above).
-__device__ __forceinline__ void box_muller_fast(float u0, float u1, float& g0, float& g1) {
+// Box-Muller in single precision on the hardware transcendental units, both normals
+// multiplied by `scale`: r = sqrt(-2 ln u0) as x * rsqrt(x), angle reduced to (-pi, pi)
+// through cos(2 pi u) = -cos(2 pi (u - 1/2)).
+__device__ __forceinline__ void box_muller_fast(float u0, float u1, float scale, float& g0, float& g1) {
   const float x = 2.0f * neg_log_unit(u0);
-  const float r = x * rsqrtf(x);
+  const float r = -scale * (x * rsqrtf(x));
   float s, c;
   __sincosf(6.28318530717958647692f * (u1 - 0.5f), &s, &c);
-  g0 = -r * c;
-  g1 = -r * s;
+  g0 = r * c;
+  g1 = r * s;
 }
 
 template <class R>
-__device__ __forceinline__ void box_muller_lb(R u0, R u1, R& g0, R& g1) {
+__device__ __forceinline__ void box_muller_lb(R u0, R u1, R scale, R& g0, R& g1) {
   box_muller(u0, u1, g0, g1);
+  g0 *= scale;
+  g1 *= scale;
 }
 template <>
-__device__ __forceinline__ void box_muller_lb<float>(float u0, float u1, float& g0, float& g1) {
-  box_muller_fast(u0, u1, g0, g1);
+__device__ __forceinline__ void box_muller_lb<float>(float u0, float u1, float scale, float& g0, float& g1) {
+  box_muller_fast(u0, u1, scale, g0, g1);
 }
 
 template <class R>
@@ -147,14 +149,14 @@ __device__ __forceinline__ void gauss4(uint32_t step, uint32_t index, uint32_t c
   box_muller(uniform01<R>(r.z), uniform01<R>(r.w), g[2], g[3]);
 }
 
-// Four standard normals from one Philox call (precomputed round keys), the fluid's
-// transform: fast single-precision Box-Muller for float, the full-precision one for double.
+// Four standard normals times `scale` from one Philox call (precomputed round keys), the
+// fluid's transform: fast single-precision Box-Muller for float, full precision for double.
 template <class R>
 __device__ __forceinline__ void gauss4_rk(uint32_t step, uint32_t index, uint32_t call, const RoundKeys& rk,
-                                          R g[4]) {
+                                          R scale, R g[4]) {
   const U4 r = philox4x32_10_rk(U4{step, index, call, 0u}, rk);
-  box_muller_lb<R>(uniform01<R>(r.x), uniform01<R>(r.y), g[0], g[1]);
-  box_muller_lb<R>(uniform01<R>(r.z), uniform01<R>(r.w), g[2], g[3]);
+  box_muller_lb<R>(uniform01<R>(r.x), uniform01<R>(r.y), scale, g[0], g[1]);
+  box_muller_lb<R>(uniform01<R>(r.z), uniform01<R>(r.w), scale, g[2], g[3]);
 }
 
 }  // namespace gblb
