@@ -128,6 +128,18 @@ int lb_set_obs_stride(lb_ctx* ctx, int stride);
 /* Take the current bead positions as the reference t0 of g1 and g3; clear accumulators. */
 int lb_reset_reference(lb_ctx* ctx);
 
+/* Gradient of a chain observable through T coupled steps, by the adjoint of the step with
+ * the noise held fixed (same Philox streams forward and backward).  Observable:
+ * O = sum_b |x_b(T) - x_b(0)|^2 (unwrapped positions).  Gradients with respect to the
+ * initial bead positions x_b(0) (grad_x0, 3N, bead-major) and to zeta_bare (grad_zeta).
+ * The forward run keeps full-state checkpoints every K steps and recomputes each segment
+ * during the reverse sweep (memory ~ (T/K + K) states).  Must be called on a context that
+ * has not stepped yet (the initial force is F_cons(x_0)); requires a chain and no fluid body
+ * force; leaves the context at step T.  Allocates its checkpoint and adjoint memory with
+ * cudaMalloc for the duration of the call. */
+int lb_adjoint_displacement(lb_ctx* ctx, int64_t T, int K, double* objective, double* grad_x0,
+                            size_t cap, double* grad_zeta);
+
 /* Checkpoint / resume: parameters, options, step counter, populations (storage precision),
  * bead state.  Noise is counter-based, so a resumed run continues bit-identically. */
 int lb_save(lb_ctx* ctx, const char* path);

@@ -443,6 +443,20 @@ int lb_load(lb_ctx* ctx, const char* path) {
   });
 }
 
+int lb_adjoint_displacement(lb_ctx* ctx, int64_t T, int K, double* objective, double* grad_x0, size_t cap,
+                            double* grad_zeta) {
+  if (!ctx || !objective || !grad_x0 || !grad_zeta || T < 1 || K < 1) return LB_ERR_ARG;
+  if (ctx->cfg.N == 0) return fail(LB_ERR_STATE, "adjoint needs a chain");
+  if (cap < 3 * (size_t)ctx->cfg.N) return fail(LB_ERR_ARG, "gradient buffer too small");
+  if (ctx->step != 0) return fail(LB_ERR_STATE, "adjoint must start from the initial state");
+  return guarded([&] {
+    materialise(ctx);
+    ctx->eng->adjoint_displacement(T, K, (uint32_t)ctx->step, objective, grad_x0, grad_zeta, ctx->stream);
+    ctx->step += T;
+    return status_from_device(ctx->eng->read_status(ctx->stream));
+  });
+}
+
 int64_t lb_get_step(lb_ctx* ctx) { return ctx ? ctx->step : -1; }
 
 int lb_set_timing(lb_ctx* ctx, int enable) {

@@ -56,6 +56,11 @@ class Engine {
   virtual void observables(double* out, int64_t step, int accumulate, cudaStream_t s) = 0;
   virtual void reset_reference(cudaStream_t s) = 0;
   virtual unsigned read_status(cudaStream_t s) = 0;
+  // adjoint: objective O = sum_b |x_b(T) - x_b(0)|^2 over T steps from the current state,
+  // its gradient with respect to the current bead positions (3N) and zeta, noise fixed,
+  // forward checkpoints every K steps; leaves the state at step k0 + T
+  virtual void adjoint_displacement(int64_t T, int K, uint32_t k0, double* O, double* gx, double* gz,
+                                    cudaStream_t s) = 0;
   // raw state for checkpoints
   virtual size_t state_bytes() const = 0;
   virtual void save_state(void* host, cudaStream_t s) = 0;

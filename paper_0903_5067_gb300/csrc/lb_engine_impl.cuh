@@ -6,6 +6,7 @@
 
 #include <vector>
 
+#include "lb_adjoint.cuh"
 #include "lb_device.cuh"
 #include "lb_engine.h"
 
@@ -107,6 +108,169 @@ class EngineT final : public Engine {
       cuda_check(cudaGetLastError(), "apply kernel");
     }
     cur_ ^= 1;
+  }
+
+  void adjoint_displacement(int64_t T, int K, uint32_t k0, double* O, double* gx, double* gz,
+                            cudaStream_t s) override {
+    if (N_ == 0) throw LbError(S_STATE, "adjoint needs a chain");
+    const FluidK<R> P = fluid();
+    if (P.body_on) throw LbError(S_STATE, "adjoint does not support the fluid body force");
+    if (T < 1 || K < 1) throw LbError(S_ARG, "T and K must be >= 1");
+    const size_t popb = (size_t)Q * plane_ * sizeof(S);
+    const size_t n3 = 3 * (size_t)N_;
+    const size_t beadb = n3 * (5 * sizeof(R) + sizeof(int));
+    const int nck = (int)((T + K - 1) / K);
+    const size_t lamb = (size_t)Q * plane_ * sizeof(R);
+    // scratch layout
+    size_t off = 0;
+    auto take = [&](size_t b) {
+      off = align_up(off, 256);
+      const size_t o = off;
+      off += b;
+      return o;
+    };
+    const size_t o_ck = take((size_t)nck * (popb + beadb));
+    const size_t o_seg = take((size_t)K * (popb + beadb));
+    const size_t o_fin = take(popb + beadb);
+    const size_t o_lam0 = take(lamb), o_lam1 = take(lamb);
+    const size_t o_bar = take(3 * n3 * sizeof(R));
+    const size_t o_adj = take(10 * n3 * sizeof(R) + (size_t)cap_ * (3 + 1 + 4) * sizeof(R) + cap_ * sizeof(int) +
+                              (size_t)cap_ * 7 * sizeof(R) + N_ * sizeof(R) + 4096);
+    // count (256 B), nodes (cap ints, padded to 256 B), values (4 x cap)
+    const size_t o_sp = take(256 + align_up(cap_ * sizeof(int), 256) + 4 * (size_t)cap_ * sizeof(R));
+    const size_t o_z = take(sizeof(double));
+    unsigned char* base = nullptr;
+    cuda_check(cudaMalloc(&base, off), "adjoint scratch");
+    struct Free {
+      unsigned char* p;
+      ~Free() { cudaFree(p); }
+    } guard{base};
+    auto save_state = [&](unsigned char* dst) {
+      cuda_check(cudaMemcpyAsync(dst, pop_[cur_], popb, cudaMemcpyDeviceToDevice, s), "save pops");
+      unsigned char* q = dst + popb;
+      for (auto pr : {std::make_pair((void*)x_, n3 * sizeof(R)), std::make_pair((void*)xl_, n3 * sizeof(R)),
+                      std::make_pair((void*)v_, n3 * sizeof(R)), std::make_pair((void*)F_, n3 * sizeof(R)),
+                      std::make_pair((void*)Fc_, n3 * sizeof(R)), std::make_pair((void*)img_, n3 * sizeof(int))}) {
+        cuda_check(cudaMemcpyAsync(q, pr.first, pr.second, cudaMemcpyDeviceToDevice, s), "save beads");
+        q += pr.second;
+      }
+    };
+    auto load_state = [&](const unsigned char* src, bool pops) {
+      if (pops) cuda_check(cudaMemcpyAsync(pop_[cur_], src, popb, cudaMemcpyDeviceToDevice, s), "load pops");
+      const unsigned char* q = src + popb;
+      for (auto pr : {std::make_pair((void*)x_, n3 * sizeof(R)), std::make_pair((void*)xl_, n3 * sizeof(R)),
+                      std::make_pair((void*)v_, n3 * sizeof(R)), std::make_pair((void*)F_, n3 * sizeof(R)),
+                      std::make_pair((void*)Fc_, n3 * sizeof(R)), std::make_pair((void*)img_, n3 * sizeof(int))}) {
+        cuda_check(cudaMemcpyAsync(pr.first, q, pr.second, cudaMemcpyDeviceToDevice, s), "load beads");
+        q += pr.second;
+      }
+    };
+    auto ck = [&](int i) { return base + o_ck + (size_t)i * (popb + beadb); };
+    auto seg = [&](int i) { return base + o_seg + (size_t)i * (popb + beadb); };
+    // 1. forward pass with checkpoints
+    std::vector<double> x0h(n3), xTh(n3);
+    get_beads(x0h.data(), nullptr, s);
+    for (int64_t t = 0; t < T; ++t) {
+      if (t % K == 0) save_state(ck((int)(t / K)));
+      step((uint32_t)(k0 + t), s, nullptr, nullptr);
+    }
+    save_state(base + o_fin);
+    get_beads(xTh.data(), nullptr, s);
+    double obj = 0.0;
+    std::vector<R> xb0(n3);
+    for (size_t t = 0; t < n3; ++t) {
+      const double d = xTh[t] - x0h[t];
+      obj += d * d;
+      xb0[t] = (R)(2.0 * d);
+    }
+    // 2. adjoint state at T
+    R* lam[2] = {reinterpret_cast<R*>(base + o_lam0), reinterpret_cast<R*>(base + o_lam1)};
+    cuda_check(cudaMemsetAsync(lam[0], 0, lamb, s), "lambda");
+    cuda_check(cudaMemsetAsync(lam[1], 0, lamb, s), "lambda");
+    AdjK<R> A;
+    memset(&A, 0, sizeof(A));
+    R* bars = reinterpret_cast<R*>(base + o_bar);
+    A.xbar = bars;
+    A.vbar = bars + n3;
+    A.fbar = bars + 2 * n3;
+    cuda_check(cudaMemsetAsync(bars, 0, 3 * n3 * sizeof(R), s), "bars");
+    cuda_check(cudaMemcpyAsync(A.xbar, xb0.data(), n3 * sizeof(R), cudaMemcpyHostToDevice, s), "xbar");
+    {
+      R* q = reinterpret_cast<R*>(base + o_adj);
+      A.xp = q; q += n3;
+      A.xpl = q; q += n3;
+      A.vh = q; q += n3;
+      A.ub = q; q += n3;
+      A.g = q; q += n3;
+      A.fc = q; q += n3;
+      A.fct = q; q += n3;
+      A.vhb = q; q += n3;
+      A.xpb = q; q += n3;
+      A.fcb = q; q += n3;
+      A.e_gw = q; q += 3 * (size_t)cap_;
+      A.e_wb = q; q += cap_;
+      A.e_rb = q; q += 4 * (size_t)cap_;
+      A.u_fb = q; q += 3 * (size_t)cap_;
+      A.u_rb = q; q += 4 * (size_t)cap_;
+      A.zb_b = q; q += N_;
+      A.e_slot = reinterpret_cast<int*>(q);
+      unsigned char* sp = base + o_sp;
+      A.s_count = reinterpret_cast<int*>(sp);
+      A.s_node = reinterpret_cast<int*>(sp + 256);
+      A.s_val = reinterpret_cast<R*>(sp + 256 + align_up(cap_ * sizeof(int), 256));
+      A.zbar = reinterpret_cast<double*>(base + o_z);
+    }
+    cuda_check(cudaMemsetAsync(A.zbar, 0, sizeof(double), s), "zbar");
+    const ChainK<R> C = chain();
+    const size_t ne = 8 * (size_t)N_;
+    size_t M = 1;
+    while (M < ne) M <<= 1;
+    const size_t smem = align_up(6 * n3 / 3 * sizeof(R) + 32, 16) + M * 8 + ne * 4 + 64;
+    if (smem > 48 * 1024)
+      cuda_check(cudaFuncSetAttribute(k_adj_bead<S, R, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                 "adjoint smem");
+    dim3 blk, grd;
+    lb_launch_shape(blk, grd);
+    int cur_lam = 0;
+    // 3. reverse sweep over the segments
+    for (int sgi = nck - 1; sgi >= 0; --sgi) {
+      const int64_t t0 = (int64_t)sgi * K, t1 = t0 + K < T ? t0 + K : T;
+      load_state(ck(sgi), true);
+      for (int64_t t = t0; t < t1; ++t) {
+        save_state(seg((int)(t - t0)));
+        step((uint32_t)(k0 + t), s, nullptr, nullptr);
+      }
+      for (int64_t t = t1 - 1; t >= t0; --t) {
+        const unsigned char* st = seg((int)(t - t0));
+        load_state(st, false);
+        const S* pops = reinterpret_cast<const S*>(st);
+        k_adj_bead<S, R, DEV><<<1, 512, smem, s>>>(pops, lam[cur_lam], P, C, A, (uint32_t)(k0 + t));
+        cuda_check(cudaGetLastError(), "adjoint bead");
+        if (P.ncalls > 0)
+          k_adj_lb<S, R, DEV, true><<<grd, blk, 0, s>>>(pops, lam[cur_lam], lam[cur_lam ^ 1], P, (uint32_t)(k0 + t));
+        else
+          k_adj_lb<S, R, DEV, false><<<grd, blk, 0, s>>>(pops, lam[cur_lam], lam[cur_lam ^ 1], P, (uint32_t)(k0 + t));
+        cuda_check(cudaGetLastError(), "adjoint LB");
+        k_adj_sparse_add<R><<<dim3((cap_ + 255) / 256, Q), 256, 0, s>>>(lam[cur_lam ^ 1], P, A.s_node, A.s_val,
+                                                                        A.s_count, cap_);
+        cuda_check(cudaGetLastError(), "adjoint sparse add");
+        cur_lam ^= 1;
+      }
+    }
+    // 4. the initial force F_0 = F_cons(x_0): xbar += H(x_0) fbar
+    load_state(ck(0), false);
+    k_chain_force_vjp<R><<<1, 512, 6 * n3 / 3 * sizeof(R), s>>>(C, A.fbar, A.xbar);
+    cuda_check(cudaGetLastError(), "initial force adjoint");
+    std::vector<R> xbh(n3);
+    double zb = 0.0;
+    cuda_check(cudaMemcpyAsync(xbh.data(), A.xbar, n3 * sizeof(R), cudaMemcpyDeviceToHost, s), "dl xbar");
+    cuda_check(cudaMemcpyAsync(&zb, A.zbar, sizeof(double), cudaMemcpyDeviceToHost, s), "dl zbar");
+    // 5. leave the context at the end of the forward run
+    load_state(base + o_fin, true);
+    cuda_check(cudaStreamSynchronize(s), "adjoint sync");
+    *O = obj;
+    for (size_t t = 0; t < n3; ++t) gx[t] = (double)xbh[t] - 2.0 * (xTh[t] - x0h[t]);
+    *gz = zb;
   }
 
   // --- access for the batched driver (one engine per replica, stepped in lockstep) ---

@@ -45,6 +45,7 @@ _SIGS = {
     "lb_save": (C.c_int, [_vp, C.c_char_p]),
     "lb_load": (C.c_int, [_vp, C.c_char_p]),
     "lb_get_step": (C.c_int64, [_vp]),
+    "lb_adjoint_displacement": (C.c_int, [_vp, C.c_int64, C.c_int, _dp, _dp, C.c_size_t, _dp]),
     "lb_set_timing": (C.c_int, [_vp, C.c_int]),
     "lb_get_timing": (C.c_int, [_vp, _dp, C.POINTER(C.c_int64)]),
     "lb_destroy": (None, [_vp]),
@@ -175,6 +176,16 @@ def lb_save(ctx, path: str):
 
 def lb_load(ctx, path: str):
     _check(_lib.lb_load(ctx, path.encode()), "lb_load")
+
+
+def lb_adjoint_displacement(ctx, T: int, K: int, N: int):
+    """(O, dO/dx0 (N,3), dO/dzeta) for O = sum_b |x_b(T) - x_b(0)|^2, noise held fixed."""
+    obj = C.c_double()
+    gz = C.c_double()
+    gx = np.zeros((N, 3))
+    _check(_lib.lb_adjoint_displacement(ctx, int(T), int(K), C.byref(obj), _dbuf(gx), gx.size, C.byref(gz)),
+           "lb_adjoint_displacement")
+    return obj.value, gx, gz.value
 
 
 def lb_get_step(ctx) -> int:
