@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
       // adjoint of the total force of step k+1 and of v_h (from v' = v_h + h F'/2m)
       A.fct[t] = A.fbar[t] + h / (R(2) * C.m) * A.vbar[t];
       A.vhb[t] = A.vbar[t];
-      A.xpb[t] = R(0);
+      A.xpb[t] = A.xbar[t];  // x' is the position output of this step
     }
   }
   __syncthreads();
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
       for (int q = 0; q < 3; ++q) xpb[q] += wb[c] * A.e_gw[q * C.cap + e];
     }
 #pragma unroll
-    for (int q = 0; q < 3; ++q) A.xpb[3 * b + q] = xpb[q];
+    for (int q = 0; q < 3; ++q) A.xpb[3 * b + q] += xpb[q];
   }
   __syncthreads();
   // ---- chain forces: x'bar += Hessian . F_cons-bar (F_cons-bar = F_total-bar) ---------

@@ -4,9 +4,9 @@ L = 32, N = 16 workload (100 steps, checkpoint every 10, seed 7).
 
 Objective O = sum_b |x_b(T) - x_b(0)|^2; derivatives with respect to the initial positions
 (checked along random directions) and zeta.  The trilinear weights have kinks on the cell
-faces, where a one-sided adjoint and a central difference differ; the perturbation is kept
-small (1e-6) and the oracle-based test verifies that no bead changes cell between the two
-perturbed trajectories."""
+faces, where a one-sided adjoint and a central difference differ; the oracle-based test uses
+a perturbation of 1e-5 (smaller steps are dominated by round-off of the 100-step objective)
+and verifies that no bead changes cell between the two perturbed trajectories."""
 import numpy as np
 import pytest
 
@@ -77,7 +77,7 @@ def test_adjoint_c5_workload_matches_oracle_finite_differences(lblib):
     O_or, _ = _oracle_objective(L, X0, zeta, T, seed)
     assert O64 == pytest.approx(O_or, rel=1e-10)
     assert O32 == pytest.approx(O_or, rel=1e-5)
-    eps = 1e-6
+    eps = 1e-5
     rng = np.random.default_rng(11)
     checked = 0
     for _ in range(4):
@@ -87,8 +87,8 @@ def test_adjoint_c5_workload_matches_oracle_finite_differences(lblib):
         if not np.array_equal(cp_, cm_):
             continue  # a bead crossed a cell face between the two runs: derivative kink
         fd = (op - om) / (2 * eps)
-        assert (gx64 * d).sum() == pytest.approx(fd, rel=1e-6)
-        assert (gx32 * d).sum() == pytest.approx(fd, rel=1e-3)
+        assert (gx64 * d).sum() == pytest.approx(fd, rel=1e-6, abs=1e-8)
+        assert (gx32 * d).sum() == pytest.approx(fd, rel=1e-3, abs=1e-6)
         checked += 1
         if checked == 2:
             break
@@ -97,8 +97,8 @@ def test_adjoint_c5_workload_matches_oracle_finite_differences(lblib):
     om, cm_ = _oracle_objective(L, X0, zeta - eps, T, seed)
     if np.array_equal(cp_, cm_):
         fdz = (op - om) / (2 * eps)
-        assert gz64 == pytest.approx(fdz, rel=1e-6)
-        assert gz32 == pytest.approx(fdz, rel=1e-3)
+        assert gz64 == pytest.approx(fdz, rel=1e-6, abs=1e-8)
+        assert gz32 == pytest.approx(fdz, rel=1e-3, abs=1e-6)
 
 
 def test_autograd_function_returns_the_adjoint(lblib):
@@ -113,7 +113,7 @@ def test_autograd_function_returns_the_adjoint(lblib):
     O = chain_displacement(x, z, params, T=T, K=K)
     (3.0 * O).backward()
     O_ref, gx, gz = _gpu_adjoint(lblib, L, X0, 20.8, T, K, seed, lblib.LB_FP64)
-    assert float(O) == pytest.approx(O_ref, rel=1e-14)
+    assert O.item() == pytest.approx(O_ref, rel=1e-14)
     assert np.allclose(x.grad.numpy(), 3.0 * gx, rtol=1e-12)
     assert float(z.grad) == pytest.approx(3.0 * gz, rel=1e-12)
 
