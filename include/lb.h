@@ -82,6 +82,12 @@ int lb_add_chain(lb_ctx* ctx, int N, double m, double zeta, double k_fene, doubl
 int lb_set_options(lb_ctx* ctx, int noise_fluid, int noise_beads, int stress_only,
                    const double ext_bead_force[3], int counter_force_fluid);
 
+/* Multiple time stepping (Sec. II E: MD step 0.01, LB step 0.02): n MD steps of length h/n
+ * per LB step of length h (lb_create's h), the beads seeing the frozen post-stream fluid and
+ * the fluid receiving their reaction averaged over the LB step.  n = 1 (default): LB step =
+ * MD step.  1 <= n <= 16 and 8 N n <= 16384; only before the first device call. */
+int lb_set_md_substeps(lb_ctx* ctx, int n);
+
 /* Device stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream); NULL =
  * legacy default stream.  Must name a stream of the current device. */
 int lb_set_stream(lb_ctx* ctx, void* stream);
@@ -171,13 +177,14 @@ int lb_cell_index_f32(const float* x_dev, int64_t n, float a, int L, int32_t* ou
  * Sec. III B-C).  Replica r has L[r] nodes per side (4..256), a chain of N[r] beads (0..1024)
  * whose 3N[r] positions are concatenated in x0 (replica order; NULL only if every N[r] = 0),
  * and its own noise stream: Philox key (seeds[r] low 32 bits, tag | r << 8).  Fluid and chain
- * parameters as in lb_create / lb_add_chain, shared by all replicas.  precision: LB_FP32 or
- * LB_FP64.  Workspace, stream and errors as for a context. */
+ * parameters as in lb_create / lb_add_chain, shared by all replicas; md_substeps as in
+ * lb_set_md_substeps.  precision: LB_FP32 or LB_FP64.  Workspace, stream and errors as for a
+ * context. */
 typedef struct lb_batch lb_batch;
 int lb_batch_create(lb_batch** out, int R, const int* L, const int* N, const uint64_t* seeds,
                     double rho, double eta, double eta_b, double kT, double h, double a, double m,
                     double zeta, double k_fene, double R0, double eps, double sigma,
-                    const double* x0, int precision);
+                    const double* x0, int precision, int md_substeps);
 int lb_batch_set_stream(lb_batch* b, void* stream);
 int lb_batch_workspace_size(lb_batch* b, size_t* bytes);
 int lb_batch_bind_workspace(lb_batch* b, void* device_ptr, size_t bytes);
@@ -194,6 +201,9 @@ int lb_batch_get_populations(lb_batch* b, int r, double* out, size_t cap);
 int lb_batch_get_beads(lb_batch* b, int r, double* x, double* v, size_t cap);
 int lb_batch_get_observables(lb_batch* b, int r, double* out, size_t cap);
 int64_t lb_batch_nodes(lb_batch* b); /* total nodes of all replicas */
+/* Add the current R_g^2, R_e^2 of every replica to its FP64 accumulators; read the means
+ * with lb_batch_get_observables (entries 17..19). */
+int lb_batch_accumulate(lb_batch* b);
 void lb_batch_destroy(lb_batch* b);
 
 /* --- allocation-free variant ---------------------------------------------------------

@@ -108,6 +108,7 @@ class ChainParams:
     sigma: float = 1.0
     noise_beads: bool = True
     ext_force: tuple = (0.0, 0.0, 0.0)  # constant external force on every bead
+    substeps: int = 1  # MD steps per LB step (Sec. II E: dt_MD = 0.01, dtau_LB = 0.02 -> 2)
 
 
 def relaxation(fp: FluidParams) -> np.ndarray:
@@ -443,12 +444,13 @@ def bead_kick_drift(X, V, F, cp: ChainParams, h: float):
     return X + h * Vh, Vh
 
 
-def coupling_force(Vh, ub, cp: ChainParams, fp: FluidParams, step_k: int, replica: int = 0):
+def coupling_force(Vh, ub, cp: ChainParams, fp: FluidParams, step_k: int, replica: int = 0, dt=None):
     """Friction against the interpolated flow plus the Langevin force that balances it:
-    F_c = -zeta_bare (v_half - u_b) + sqrt(2 kT zeta_bare / h) g_b."""
+    F_c = -zeta_bare (v_half - u_b) + sqrt(2 kT zeta_bare / dt) g_b (dt: the MD step)."""
+    dt = fp.h if dt is None else dt
     Fc = -cp.zeta * (Vh - ub)
     if cp.noise_beads and fp.kT > 0.0:
-        amp = math.sqrt(2.0 * fp.kT * cp.zeta / fp.h)
+        amp = math.sqrt(2.0 * fp.kT * cp.zeta / dt)
         Fc = Fc + amp * bead_gaussians(fp.seed, replica, step_k, Vh.shape[0])
     return Fc
 
@@ -460,13 +462,18 @@ def bead_kick(Vh, F, cp: ChainParams, h: float):
 
 # ---------------------------------------------------------------------------------------
 # Coupled step (reading: velocity Verlet with the friction evaluated at the half-step
-# velocity; LB step = MD step).  State k -> k+1:
-#   1. v_half = v + h F/(2m);  x' = x + h v_half
-#   2. F_cons(x')  (FENE + WCA + optional constant external force)
-#   3. u_b = trilinear interpolation of the post-stream flow velocity at x'
-#   4. F_c = -zeta (v_half - u_b) + sqrt(2 kT zeta / h) g_b;  f(r) = -sum_b w_b(r) F_c / a^3
-#   5. stream + collide every node with the force density f
-#   6. F = F_cons + F_c;  v' = v_half + h F / (2m)
+# velocity).  One LB step of length h carries n = substeps MD steps of length dt = h / n
+# (the paper uses dt = 0.01, dtau = 0.02, Sec. II E).  State k -> k+1:
+#   n_ps = stream(n*)                                   (the fluid the beads see, frozen)
+#   for s = 0 .. n-1 (noise counter q = k n + s):
+#     1. v_half = v + dt F/(2m);  x' = x + dt v_half
+#     2. F_cons(x')  (FENE + WCA + optional constant external force)
+#     3. u_b = trilinear interpolation of the post-stream flow velocity at x'
+#     4. F_c = -zeta (v_half - u_b) + sqrt(2 kT zeta / dt) g_b;
+#        f(r) += -(dt/h) sum_b w_b(r) F_c / a^3     (reaction averaged over the LB step)
+#     5. F = F_cons + F_c;  v' = v_half + dt F / (2m)
+#   collide every node with the force density f
+# For n = 1 this is the plain step with LB step = MD step.
 # ---------------------------------------------------------------------------------------
 @dataclasses.dataclass
 class State:
@@ -502,13 +509,17 @@ def step(st: State, fp: FluidParams, cp: ChainParams | None, replica: int = 0,
     X, V, F, Fc = st.X, st.V, st.F, st.Fc
     if cp is not None and cp.N > 0:
         box = fp.L * fp.a
-        X, Vh = bead_kick_drift(X, V, F, cp, fp.h)
-        Fcons = chain_forces(X, cp, box) + np.asarray(cp.ext_force, dtype=float)[None]
-        ub = interpolate_u(n_ps, fp, X)
-        Fc = coupling_force(Vh, ub, cp, fp, k, replica)
-        f = spread(Fc, X, fp)
-        F = Fcons + Fc
-        V = bead_kick(Vh, F, cp, fp.h)
+        nsub = max(1, int(cp.substeps))
+        dt = fp.h / nsub
+        f = np.zeros((3, fp.L, fp.L, fp.L))
+        for sub in range(nsub):
+            X, Vh = bead_kick_drift(X, V, F, cp, dt)
+            Fcons = chain_forces(X, cp, box) + np.asarray(cp.ext_force, dtype=float)[None]
+            ub = interpolate_u(n_ps, fp, X)
+            Fc = coupling_force(Vh, ub, cp, fp, k * nsub + sub, replica, dt=dt)
+            f += (dt / fp.h) * spread(Fc, X, fp)
+            F = Fcons + Fc
+            V = bead_kick(Vh, F, cp, dt)
     n_new = collide(n_ps, fp, k, force_density=f, replica=replica, stats=stats)
     return State(n_new, X, V, F, Fc, k + 1)
 
@@ -570,11 +581,12 @@ def fluid_momentum(st: State, fp: FluidParams) -> np.ndarray:
 
 
 def total_momentum(st: State, fp: FluidParams, cp: ChainParams | None) -> np.ndarray:
-    """Fluid + beads + (h/2) sum_b F_c: exactly conserved by the coupled step when no
-    external force acts."""
+    """Fluid + beads + (dt/2) sum_b F_c (dt: the MD step): exactly conserved by the coupled
+    step when no external force acts."""
     P = fluid_momentum(st, fp)
     if cp is not None and cp.N > 0:
-        P = P + cp.m * st.V.sum(axis=0) + 0.5 * fp.h * st.Fc.sum(axis=0)
+        dt = fp.h / max(1, int(cp.substeps))
+        P = P + cp.m * st.V.sum(axis=0) + 0.5 * dt * st.Fc.sum(axis=0)
     return P
 
 

@@ -210,6 +210,7 @@ int lb_add_chain(lb_ctx* ctx, int N, double m, double zeta, double k_fene, doubl
   if (!ctx) return LB_ERR_ARG;
   if (ctx->live || ctx->cfg.N > 0) return fail(LB_ERR_STATE, "chain must be added once, before the first step");
   if (N < 1 || N > 1024) return fail(LB_ERR_ARG, "N out of range [1, 1024]");
+  if (8ll * N * ctx->cfg.substeps > 16384) return fail(LB_ERR_ARG, "8 N substeps exceeds 16384");
   if (!(m > 0) || !(zeta >= 0) || !(k_fene >= 0) || !(R0 > 0) || !(eps >= 0) || !(sigma > 0))
     return fail(LB_ERR_ARG, "invalid chain parameters");
   return guarded([&] {
@@ -270,6 +271,15 @@ int lb_set_options(lb_ctx* ctx, int noise_fluid, int noise_beads, int stress_onl
   for (int q = 0; q < 3; ++q) c.ext[q] = ext_bead_force ? ext_bead_force[q] : 0.0;
   c.counter_force = counter_force_fluid ? 1 : 0;
   if (ctx->eng) ctx->eng->set_config(c);
+  return LB_OK;
+}
+
+int lb_set_md_substeps(lb_ctx* ctx, int n) {
+  if (!ctx || n < 1 || n > 16) return LB_ERR_ARG;
+  if (ctx->live) return fail(LB_ERR_STATE, "substeps must be set before the first device call");
+  if (8ll * ctx->cfg.N * n > 16384) return fail(LB_ERR_ARG, "8 N substeps exceeds 16384");
+  ctx->cfg.substeps = n;
+  ctx->eng.reset();
   return LB_OK;
 }
 

@@ -435,8 +435,9 @@ extern "C" {
 
 int lb_batch_create(lb_batch** out, int R, const int* L, const int* N, const uint64_t* seeds, double rho, double eta,
                     double eta_b, double kT, double h, double a, double m, double zeta, double k_fene, double R0,
-                    double eps, double sigma, const double* x0, int precision) {
+                    double eps, double sigma, const double* x0, int precision, int md_substeps) {
   if (!out || R < 1 || R > 4096 || !L || !seeds) return LB_ERR_ARG;
+  if (md_substeps < 1 || md_substeps > 16) return LB_ERR_ARG;
   *out = nullptr;
   if (precision != LB_FP32 && precision != LB_FP64) return LB_ERR_ARG;
   if (!(rho > 0) || !(eta > 0) || !(eta_b > 0) || !(h > 0) || !(a > 0) || !(kT >= 0)) return LB_ERR_ARG;
@@ -449,7 +450,7 @@ int lb_batch_create(lb_batch** out, int R, const int* L, const int* N, const uin
       Config& c = cfgs[r];
       if (L[r] < 4 || L[r] > 256) return (int)LB_ERR_ARG;
       const int Nr = N ? N[r] : 0;
-      if (Nr < 0 || Nr > 1024 || (Nr > 0 && !x0)) return (int)LB_ERR_ARG;
+      if (Nr < 0 || Nr > 1024 || (Nr > 0 && !x0) || 8ll * Nr * md_substeps > 16384) return (int)LB_ERR_ARG;
       c.L = L[r];
       c.rho = rho;
       c.eta = eta;
@@ -467,6 +468,7 @@ int lb_batch_create(lb_batch** out, int R, const int* L, const int* N, const uin
       c.R0 = R0;
       c.eps = eps;
       c.sigma = sigma;
+      c.substeps = md_substeps;
       if (Nr > 0) {
         xs[r].assign(x0 + off, x0 + off + 3 * (size_t)Nr);
         off += 3 * (size_t)Nr;
@@ -581,6 +583,16 @@ int lb_batch_get_observables(lb_batch* bt, int r, double* out, size_t cap) {
   return bguard([&] {
     bmaterialise(bt);
     bt->b->replica(r).observables(out, bt->step, 0, bt->stream);
+    return (int)LB_OK;
+  });
+}
+
+int lb_batch_accumulate(lb_batch* bt) {
+  if (!bt) return LB_ERR_ARG;
+  return bguard([&] {
+    bmaterialise(bt);
+    for (size_t r = 0; r < bt->cfgs.size(); ++r)
+      if (bt->cfgs[r].N > 0) bt->b->replica((int)r).observables(nullptr, bt->step, 1, bt->stream);
     return (int)LB_OK;
   });
 }

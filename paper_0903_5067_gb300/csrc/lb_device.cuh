@@ -70,9 +70,12 @@ struct ChainK {
   R amp;            // sqrt(2 kT zeta / h), 0 without bead noise
   uint32_t k0, k1;  // Philox key of the bead stream
   R ext[3];         // constant external force on each bead
-  R u_scale;        // a / h: lattice -> physical velocity
+  R u_scale;        // a / h (h: the LB step): lattice -> physical velocity
   R inv_a3;         // 1 / a^3
-  R dJ_scale;       // h^2 / a: force density -> lattice momentum per step
+  R dJ_scale;       // h^2 / a: force density -> lattice momentum per LB step
+  int nsub;         // MD steps per LB step (h above is the MD step h_LB / nsub)
+  R spread;         // 1 / nsub: each MD step's reaction, averaged over the LB step
+  R* fc_hist;       // nsub x 3N coupling forces of the MD substeps
   // bead state (global, 3N each, bead-major)
   R* x;    // wrapped positions in [0, box): high part
   R* xl;   // low part: position = x + xl + img * box (compensated, ~2x the precision of R)
@@ -501,6 +504,9 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
   R* sx = reinterpret_cast<R*>(smem);
   R* sl = sx + 3 * N;
 
+  // MD substeps against the frozen post-stream fluid (one for LB step = MD step)
+  for (int sub = 0; sub < C.nsub; ++sub) {
+  const int eoff = sub * 8 * N;
   // 1. first half kick and drift: v_half = v + h F/2m, x' = x + h v_half, in compensated
   //    (hi, lo) arithmetic, then wrapped into [0, box) with the image counter
   for (int t = tid; t < 3 * N; t += nt) {
@@ -539,8 +545,8 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
   chain_forces_block<R>(sx, sl, C, C.fcons);
 
   // 3. corners of every bead: cell, trilinear weight, post-stream rho and J at the node
-  for (int e = tid; e < 8 * N; e += nt) {
-    const int b = e >> 3, c = e & 7;
+  for (int e0 = tid; e0 < 8 * N; e0 += nt) {
+    const int b = e0 >> 3, c = e0 & 7, e = eoff + e0;
     const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
     R fr[3];
     int cl[3];
@@ -568,7 +574,7 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
   for (int b = tid; b < N; b += nt) {
     R ub[3] = {R(0), R(0), R(0)};
     for (int c = 0; c < 8; ++c) {
-      const int e = 8 * b + c;
+      const int e = eoff + 8 * b + c;
       const R w = C.e_w[e];
       const R ir = R(1) / C.e_mom[e];
       ub[0] += w * C.e_mom[1 * C.cap + e] * ir;
@@ -576,7 +582,7 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
       ub[2] += w * C.e_mom[3 * C.cap + e] * ir;
     }
     R g[4] = {R(0), R(0), R(0), R(0)};
-    if (C.amp != R(0)) gauss4<R>(step, (uint32_t)b, 0u, C.k0, C.k1, g);
+    if (C.amp != R(0)) gauss4<R>(step * (uint32_t)C.nsub + (uint32_t)sub, (uint32_t)b, 0u, C.k0, C.k1, g);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const int t = 3 * b + q;
@@ -584,15 +590,17 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
       const R fc = -C.zeta * (vh - ub[q] * C.u_scale) + C.amp * g[q];
       const R Ft = C.fcons[t] + fc;
       C.Fc[t] = fc;
+      C.fc_hist[sub * 3 * N + t] = fc;
       C.F[t] = Ft;
       C.v[t] = vh + h * Ft / (R(2) * C.m);
     }
   }
   __syncthreads();
+  }  // substeps
 
   // 5. deterministic spreading: sort (node, entry) keys, sum each node's contributions in
   //    entry order, then turn the node force into population corrections
-  const int ne = 8 * N;
+  const int ne = 8 * N * C.nsub;
   int M = 1;
   while (M < ne) M <<= 1;
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem);
@@ -639,11 +647,12 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
     R f[3] = {R(0), R(0), R(0)};
     for (int r = i; r < ne && (int)(keys[r] >> 32) == node; ++r) {
       const int e = (int)(keys[r] & 0xffffffffu);
-      const R w = C.e_w[e];
-      const int b = e >> 3;
-      f[0] -= w * C.Fc[3 * b + 0] * C.inv_a3;
-      f[1] -= w * C.Fc[3 * b + 1] * C.inv_a3;
-      f[2] -= w * C.Fc[3 * b + 2] * C.inv_a3;
+      const R w = C.e_w[e] * C.spread;
+      const int sub = e / (8 * N), b = (e - sub * 8 * N) >> 3;
+      const R* fch = C.fc_hist + sub * 3 * N;
+      f[0] -= w * fch[3 * b + 0] * C.inv_a3;
+      f[1] -= w * fch[3 * b + 1] * C.inv_a3;
+      f[2] -= w * fch[3 * b + 2] * C.inv_a3;
     }
     const R rho = C.e_mom[e0], jx = C.e_mom[C.cap + e0], jy = C.e_mom[2 * C.cap + e0],
             jz = C.e_mom[3 * C.cap + e0];

@@ -21,6 +21,7 @@ struct Config {
   double m = 1, zeta = 0, kfene = 0, R0 = 1, eps = 0, sigma = 1;
   // options
   int noise_fluid = 1, noise_beads = 1, stress_only = 0, counter_force = 0;
+  int substeps = 1;  // MD steps per LB step
   double ext[3] = {0, 0, 0};
 };
 

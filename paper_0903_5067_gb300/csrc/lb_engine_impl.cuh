@@ -22,7 +22,8 @@ class EngineT final : public Engine {
     nnodes_ = (unsigned long long)L_ * L_ * L_;
     plane_ = align_up(nnodes_, 64);
     N_ = c.N;
-    cap_ = 8 * (N_ > 0 ? N_ : 1);
+    nsub_ = c.substeps > 0 ? c.substeps : 1;
+    cap_ = 8 * (N_ > 0 ? N_ : 1) * nsub_;
     nparts_ = (int)((nnodes_ + 255) / 256);
     layout(nullptr);
   }
@@ -113,6 +114,7 @@ class EngineT final : public Engine {
   void adjoint_displacement(int64_t T, int K, uint32_t k0, double* O, double* gx, double* gz,
                             cudaStream_t s) override {
     if (N_ == 0) throw LbError(S_STATE, "adjoint needs a chain");
+    if (nsub_ != 1) throw LbError(S_STATE, "adjoint needs one MD step per LB step");
     const FluidK<R> P = fluid();
     if (P.body_on) throw LbError(S_STATE, "adjoint does not support the fluid body force");
     if (T < 1 || K < 1) throw LbError(S_ARG, "T and K must be >= 1");
@@ -436,7 +438,7 @@ class EngineT final : public Engine {
   }
 
   size_t bead_smem() const {
-    const size_t ne = 8 * (size_t)N_;
+    const size_t ne = 8 * (size_t)N_ * nsub_;
     size_t M = 1;
     while (M < ne) M <<= 1;
     const size_t sortb = M * 8 + ne * 4;
@@ -498,18 +500,21 @@ class EngineT final : public Engine {
     C.eps = (R)c.eps;
     C.sig2 = (R)(c.sigma * c.sigma);
     C.rc2 = (R)(pow(2.0, 1.0 / 3.0) * c.sigma * c.sigma);
-    C.h = (R)c.h;
+    C.h = (R)(c.h / nsub_);  // the MD step
     C.a = (R)c.a;
     C.box = (R)(c.L * c.a);
     C.half_box = (R)(0.5 * c.L * c.a);
     const bool noise = c.noise_beads && c.kT > 0.0;
-    C.amp = noise ? (R)sqrt(2.0 * c.kT * c.zeta / c.h) : (R)0;
+    C.amp = noise ? (R)sqrt(2.0 * c.kT * c.zeta / (c.h / nsub_)) : (R)0;
     C.k0 = (uint32_t)(c.seed & 0xffffffffu);
     C.k1 = (uint32_t)(1u | ((uint32_t)c.replica << 8));
     for (int q = 0; q < 3; ++q) C.ext[q] = (R)c.ext[q];
     C.u_scale = (R)(c.a / c.h);
     C.inv_a3 = (R)(1.0 / (c.a * c.a * c.a));
     C.dJ_scale = (R)(c.h * c.h / c.a);
+    C.nsub = nsub_;
+    C.spread = (R)(1.0 / nsub_);
+    C.fc_hist = fch_;
     C.x = x_;
     C.xl = xl_;
     C.img = img_;
@@ -546,7 +551,7 @@ class EngineT final : public Engine {
     O.Fc = Fc_;
     O.box = c.L * c.a;
     O.m = c.m;
-    O.h = c.h;
+    O.h = c.h / nsub_;
     O.xref = xref_;
     O.acc = acc_;
     O.nonpos = nonpos_;
@@ -577,6 +582,7 @@ class EngineT final : public Engine {
     Fc_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
     vh_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
     fcons_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
+    fch_ = reinterpret_cast<R*>(take(n3 * nsub_ * sizeof(R)));
     xref_ = reinterpret_cast<double*>(take(n3 * sizeof(double)));
     e_node_ = reinterpret_cast<int*>(take(cap_ * sizeof(int)));
     e_w_ = reinterpret_cast<R*>(take(cap_ * sizeof(R)));
@@ -593,13 +599,14 @@ class EngineT final : public Engine {
   }
 
   Config cfg_;
-  int L_ = 0, N_ = 0, cap_ = 8, nparts_ = 0;
+  int L_ = 0, N_ = 0, cap_ = 8, nparts_ = 0, nsub_ = 1;
   unsigned long long nnodes_ = 0, plane_ = 0;
   size_t bytes_ = 0;
   int cur_ = 0;
   cudaStream_t side_ = nullptr;
   cudaEvent_t ev_ready_ = nullptr, ev_bead_ = nullptr;
   S* pop_[2] = {nullptr, nullptr};
+  R *fch_ = nullptr;
   R *x_ = nullptr, *xl_ = nullptr, *v_ = nullptr, *F_ = nullptr, *Fc_ = nullptr, *vh_ = nullptr, *fcons_ = nullptr;
   int* img_ = nullptr;
   double* xref_ = nullptr;

@@ -21,8 +21,9 @@ def chain_walk(N: int, L: int, a: float = 1.0, bond: float = 0.97, seed: int = 0
     """Initial bead positions (N, 3), float64, unwrapped, first bead near the box centre.
 
     Random walk of fixed step ``bond``.  With ``self_avoiding`` a trial bead closer than
-    ``sigma`` to any earlier bead other than its predecessor is rejected (up to max_tries
-    per bead); raises ValueError if the walk gets stuck.
+    ``sigma`` to any earlier bead other than its predecessor, or to a periodic image of one
+    (the box has side L a), is rejected (up to max_tries per bead); raises ValueError if the
+    walk gets stuck.
     """
     rng = np.random.default_rng(np.random.PCG64(seed))
     X = np.zeros((max(N, 0), 3))
@@ -35,7 +36,9 @@ def chain_walk(N: int, L: int, a: float = 1.0, bond: float = 0.97, seed: int = 0
             trial = X[i - 1] + bond * _unit_vectors(rng, 1)[0]
             if not self_avoiding or i < 2:
                 break
-            d = np.linalg.norm(X[: i - 1] - trial, axis=1)
+            dv = X[: i - 1] - trial
+            dv -= L * a * np.round(dv / (L * a))
+            d = np.linalg.norm(dv, axis=1)
             if np.all(d >= sigma):
                 break
         else:

@@ -32,6 +32,8 @@ _SIGS = {
                                C.c_double, _dp, _dp, C.c_double, C.c_int]),
     "lb_set_options": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _dp, C.c_int]),
     "lb_set_stream": (C.c_int, [_vp, _vp]),
+    "lb_set_md_substeps": (C.c_int, [_vp, C.c_int]),
+    "lb_batch_accumulate": (C.c_int, [_vp]),
     "lb_workspace_size": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
     "lb_bind_workspace": (C.c_int, [_vp, _vp, C.c_size_t]),
     "lb_step": (C.c_int, [_vp, C.c_int64]),
@@ -56,7 +58,7 @@ _SIGS = {
     "lb_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_uint64), C.c_double, C.c_double, C.c_double, C.c_double,
                                   C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
-                                  C.c_double, C.c_double, _dp, C.c_int]),
+                                  C.c_double, C.c_double, _dp, C.c_int, C.c_int]),
     "lb_batch_set_stream": (C.c_int, [_vp, _vp]),
     "lb_batch_workspace_size": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
     "lb_batch_bind_workspace": (C.c_int, [_vp, _vp, C.c_size_t]),
@@ -118,6 +120,14 @@ def lb_set_options(ctx, noise_fluid=1, noise_beads=1, stress_only=0, ext_bead_fo
     ext = None if ext_bead_force is None else np.ascontiguousarray(ext_bead_force, dtype=np.float64)
     _check(_lib.lb_set_options(ctx, int(noise_fluid), int(noise_beads), int(stress_only), _dbuf(ext),
                                int(counter_force_fluid)), "lb_set_options")
+
+
+def lb_set_md_substeps(ctx, n: int):
+    _check(_lib.lb_set_md_substeps(ctx, int(n)), "lb_set_md_substeps")
+
+
+def lb_batch_accumulate(b):
+    _check(_lib.lb_batch_accumulate(b), "lb_batch_accumulate")
 
 
 def lb_set_stream(ctx, stream_handle: int):
@@ -226,7 +236,8 @@ def lb_fluid_sums_noalloc(pop_dev_ptr: int, L: int, a: float, h: float, stream: 
     return out
 
 
-def lb_batch_create(L, N, seeds, rho, eta, eta_b, kT, h, a, m, zeta, k_fene, R0, eps, sigma, x0, precision):
+def lb_batch_create(L, N, seeds, rho, eta, eta_b, kT, h, a, m, zeta, k_fene, R0, eps, sigma, x0, precision,
+                    md_substeps=1):
     R = len(L)
     Ls = (C.c_int * R)(*[int(v) for v in L])
     Ns = (C.c_int * R)(*[int(v) for v in N])
@@ -234,7 +245,7 @@ def lb_batch_create(L, N, seeds, rho, eta, eta_b, kT, h, a, m, zeta, k_fene, R0,
     xa = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).reshape(-1)
     b = _vp()
     _check(_lib.lb_batch_create(C.byref(b), R, Ls, Ns, Ss, rho, eta, eta_b, kT, h, a, m, zeta, k_fene, R0, eps,
-                                sigma, _dbuf(xa), int(precision)), "lb_batch_create")
+                                sigma, _dbuf(xa), int(precision), int(md_substeps)), "lb_batch_create")
     return b
 
 
@@ -297,7 +308,7 @@ class Batch:
     workspace in a torch tensor, work on torch's current stream."""
 
     def __init__(self, L, N, seeds, X0, rho=1.0, eta=3.0, eta_b=3.0, kT=1.0, h=0.01, a=1.0, m=1.0, zeta=20.8,
-                 k_fene=30.0, R0=1.5, eps=1.0, sigma=1.0, precision=LB_FP32):
+                 k_fene=30.0, R0=1.5, eps=1.0, sigma=1.0, precision=LB_FP32, md_substeps=1):
         import torch
 
         self.L = [int(v) for v in L]
@@ -305,7 +316,7 @@ class Batch:
         xs = [np.asarray(x, dtype=np.float64).reshape(-1) for x, n in zip(X0, self.N) if n > 0]
         x0 = np.concatenate(xs) if xs else None
         self.b = lb_batch_create(self.L, self.N, seeds, rho, eta, eta_b, kT, h, a, m, zeta, k_fene, R0, eps,
-                                 sigma, x0, precision)
+                                 sigma, x0, precision, md_substeps)
         lb_batch_set_stream(self.b, torch.cuda.current_stream().cuda_stream)
         nbytes = lb_batch_workspace_size(self.b)
         self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
@@ -330,6 +341,9 @@ class Batch:
 
     def observables(self, r):
         return lb_batch_get_observables(self.b, r)
+
+    def accumulate(self):
+        lb_batch_accumulate(self.b)
 
     def close(self):
         if self.b:
@@ -365,6 +379,9 @@ class Simulation:
 
     def set_options(self, **kw):
         lb_set_options(self.ctx, **kw)
+
+    def set_md_substeps(self, n: int):
+        lb_set_md_substeps(self.ctx, n)
 
     def _bind(self):
         if self._bound:

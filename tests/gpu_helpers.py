@@ -36,6 +36,7 @@ class Case:
     eps: float = 1.0
     sigma: float = 1.0
     chain_seed: int = 0
+    substeps: int = 1
 
     def fluid(self):
         body = (0.0, 0.0, 0.0)
@@ -50,7 +51,8 @@ class Case:
         if self.N == 0:
             return None
         return o.ChainParams(N=self.N, m=self.m, zeta=self.zeta, k_fene=self.k_fene, R0=self.R0, eps=self.eps,
-                             sigma=self.sigma, noise_beads=self.noise_beads, ext_force=self.ext)
+                             sigma=self.sigma, noise_beads=self.noise_beads, ext_force=self.ext,
+                             substeps=self.substeps)
 
     def x0(self):
         return inputs.chain_walk(self.N, L=self.L, a=self.a, bond=0.97, seed=self.chain_seed or self.seed,
@@ -77,6 +79,8 @@ def gpu_sim(lb, case: Case, precision: int):
     if case.N > 0:
         sim.add_chain(case.N, m=case.m, zeta=case.zeta, k_fene=case.k_fene, R0=case.R0, eps=case.eps,
                       sigma=case.sigma, x0=case.x0())
+        if case.substeps > 1:
+            sim.set_md_substeps(case.substeps)
     sim.set_options(noise_fluid=int(case.noise_fluid), noise_beads=int(case.noise_beads),
                     stress_only=int(case.stress_only), ext_bead_force=list(case.ext),
                     counter_force_fluid=int(case.counter))

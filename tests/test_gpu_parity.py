@@ -227,3 +227,16 @@ def test_cell_index_is_bit_exact(lblib):
         torch.cuda.synchronize()
         want = o.cell_index(x, np.float32(a), L)
         assert np.array_equal(out.cpu().numpy(), want), a
+
+
+def test_md_substeps_with_paper_parameters(lblib):
+    """The paper's production setting (Sec. II E): kT = 1.2, rho = 0.864, nu = 2.8, k = 7,
+    R0 = 2, zeta = 20.8, MD step 0.01 with an LB step of 0.02 (two MD substeps)."""
+    case = Case(L=10, N=8, steps=25, seed=31, rho=0.864, eta=0.864 * 2.8, eta_b=0.864 * 2.8, kT=1.2, h=0.02,
+                k_fene=7.0, R0=2.0, substeps=2)
+    st = oracle_run(case)
+    for prec, tol in ((lblib.LB_FP64, 1e-12), (lblib.LB_FP32, 1e-5)):
+        n, x, v, _ = gpu_run(lblib, case, prec)
+        assert pop_rel_err(n, st.n) <= tol
+        ex, ev = bead_errs(x, v, st, case)
+        assert ex <= tol and ev <= (10 * tol if prec == lblib.LB_FP64 else tol)

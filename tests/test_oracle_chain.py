@@ -204,3 +204,25 @@ def test_bead_in_fluctuating_fluid_is_at_the_fluid_temperature():
         if k > 200:
             vs.append(st.V[0].copy())
     assert np.var(vs) == pytest.approx(fp.kT / cp.m, rel=0.08)
+
+
+def test_md_substeps_conserve_mass_and_momentum():
+    """Two MD steps per LB step (Sec. II E: dt = 0.01, dtau = 0.02): the fluid receives the
+    reaction averaged over the LB step, so the invariant a^3 sum j + sum m v + (dt/2) sum F_c
+    (dt the MD step) still holds to round-off."""
+    fp = o.FluidParams(L=8, rho=0.864, eta=0.864 * 2.8, eta_b=0.864 * 2.8, kT=1.2, h=0.02, a=1.0, seed=4)
+    cp = o.ChainParams(N=6, m=1.0, zeta=20.8, k_fene=7.0, R0=2.0, eps=1.0, sigma=1.0, substeps=2)
+    st = o.init_state(fp, cp, inputs.chain_walk(6, L=8, bond=0.97, seed=4, self_avoiding=True))
+    M0, P0 = o.total_mass(st, fp), o.total_momentum(st, fp, cp)
+    st = o.run(st, fp, cp, 60)
+    scale = fp.L ** 3 * fp.a ** 3 * fp.rho * fp.a / fp.h
+    assert o.total_mass(st, fp) == pytest.approx(M0, rel=1e-13)
+    assert np.allclose(o.total_momentum(st, fp, cp), P0, rtol=0, atol=1e-13 * scale)
+
+
+def test_single_substep_is_the_plain_step():
+    fp, cp, st = _c1_like(L=6, N=4, seed=2)
+    cp1 = o.ChainParams(**{**cp.__dict__, "substeps": 1})
+    a = o.run(st, fp, cp, 5)
+    b = o.run(st, fp, cp1, 5)
+    assert np.array_equal(a.n, b.n) and np.array_equal(a.X, b.X)
