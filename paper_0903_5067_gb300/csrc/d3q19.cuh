@@ -30,6 +30,20 @@ __host__ __device__ constexpr int cz(int i) {
 }
 __host__ __device__ constexpr int c2(int i) { return cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i); }
 
+// the components of all 19 velocities packed two bits each (c + 1), for loops over i that
+// are not unrolled: component = ((packed >> 2i) & 3) - 1
+__host__ __device__ constexpr unsigned long long pack_component(int comp) {
+  unsigned long long p = 0;
+  for (int i = 0; i < Q; ++i) {
+    const int c = comp == 0 ? cx(i) : (comp == 1 ? cy(i) : cz(i));
+    p |= (unsigned long long)(c + 1) << (2 * i);
+  }
+  return p;
+}
+__host__ __device__ constexpr int unpack_component(unsigned long long packed, int i) {
+  return (int)((packed >> (2 * i)) & 3ull) - 1;
+}
+
 // weight numerator over 36: 12, 2, 1
 __host__ __device__ constexpr int w36(int i) { return c2(i) == 0 ? 12 : (c2(i) == 1 ? 2 : 1); }
 

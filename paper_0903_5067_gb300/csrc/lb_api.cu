@@ -324,11 +324,12 @@ int lb_step(lb_ctx* ctx, int64_t n) {
         cuda_check(cudaEventCreate(&e1), "event");
         ctx->evs.emplace_back(e0, e1);
       }
-      ctx->eng->step((uint32_t)ctx->step, ctx->stream, e0, e1);
+      ctx->eng->step_deferred((uint32_t)ctx->step, ctx->stream, e0, e1);
       ctx->step += 1;
       if (ctx->obs_stride > 0 && ctx->cfg.N > 0 && ctx->step % ctx->obs_stride == 0)
         ctx->eng->observables(nullptr, ctx->step, 1, ctx->stream);
     }
+    ctx->eng->flush(ctx->stream);
     return (int)LB_OK;
   });
 }

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(512) k_batch_bead(const ReplicaK<S, R>* __rest
     for (unsigned w = threadIdx.x; w < sizeof(ChainK<R>) / 4; w += blockDim.x) d[w] = c[w];
   }
   __syncthreads();
-  bead_step_block<S, R, DEV>(rp.pop[parity], sP, sC, *d_step + j, smem);
+  bead_step_block<S, R, DEV>(rp.pop[parity], sP, sC, pend_complete(sC), *d_step + j, smem);
 }
 
 template <class S, class R>
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) k_batch_apply(const ReplicaK<S, R>* __res
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= *rp.C.p_count) return;
   const int i = blockIdx.y;
-  S* p = rp.pop[parity ^ 1] + (unsigned long long)i * rp.P.plane + (unsigned)rp.C.p_node[u];
+  S* p = rp.pop[parity ^ 1] + (unsigned long long)i * rp.P.plane + (unsigned)rp.C.p_pos[u].x;
   st<S, R>(p, ld<S, R>(p) + rp.C.p_dn[i * rp.C.cap + u]);
 }
 

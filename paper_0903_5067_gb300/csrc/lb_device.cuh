@@ -41,6 +41,17 @@ __device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat16* p, float
 template <>
 __device__ __forceinline__ void st<__half, float>(__half* p, float v) { *p = __float2half_rn(v); }
 
+// 1/x and sqrt(x) for the LB kernel: hardware reciprocal / reciprocal square root in single
+// precision (2 ulp), correctly rounded operations in double
+template <class R>
+__device__ __forceinline__ R lb_rcp(R x) { return R(1) / x; }
+template <>
+__device__ __forceinline__ float lb_rcp<float>(float x) { return __fdividef(1.0f, x); }
+template <class R>
+__device__ __forceinline__ R lb_sqrt_pos(R x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float lb_sqrt_pos<float>(float x) { return x * rsqrtf(x); }
+
 // ---------------------------------------------------------------------------------------
 // kernel parameter blocks (passed by value)
 // ---------------------------------------------------------------------------------------
@@ -54,6 +65,9 @@ struct FluidK {
   // the same relaxation and noise in terms of the scaled moments a_k = m*_k / b_k used by the
   // back-transform: a_k = am_k m_k + ae_k m_eq,k + ag_k sqrt(rho) g_k  (k = 4..18)
   R am[Q], ae[Q], ag[Q];
+  // the same times w_2 = 1/36, the weight of the next-nearest velocities, which the forward
+  // kernel's back-transform then needs no more multiplications for
+  R wam[Q], wae[Q], wag[Q];
   uint32_t k0, k1; // Philox key of the fluid stream
   RoundKeys rk;    // its ten round keys
   int ncalls;      // Philox calls per node: 0 (noise off), 2 (stress modes only), 4 (all)
@@ -89,12 +103,45 @@ struct ChainK {
   int* e_node;  // 8N corner nodes
   R* e_w;      // 8N trilinear weights
   R* e_mom;    // 4 x 8N: post-stream rho, Jx, Jy, Jz at the corner node
-  int* p_node; // pending force corrections: node, and 19 population deltas [i][cap]
+  int4* p_pos; // pending force corrections: {node, x, y, z}, and 19 deltas [i][cap]
   R* p_dn;
   int* p_count;
   int cap;     // 8N
   unsigned* status;
 };
+
+// Force corrections in flight between consecutive steps of a multi-step run: the bead kernel
+// of step k writes them (with the LB tiles whose pulls read a corrected node stamped k); the
+// LB kernel of step k+1 adds them to the populations it pulls from stamped tiles, and the bead
+// kernel of step k+1 to the populations it gathers.  One flush applies the last step's.
+template <class R>
+struct PendK {
+  int have_prev;  // 0: the stored populations are complete (first step of a run)
+  int prev_stamp;
+  const int4* prev_pos;
+  const R* prev_dn;
+  const int* prev_count;
+  const int* prev_flags;
+  int4* cur_pos;
+  R* cur_dn;
+  int* cur_count;
+  int* cur_flags;  // nullptr: do not stamp tiles
+  int cur_stamp;
+  int cap;
+  unsigned bx, by, tiles_x, tiles_y;  // LB kernel tile geometry
+};
+
+// pending block of a complete step: no previous corrections, the new ones into the chain's
+// own list, no stamps
+template <class R>
+__host__ __device__ inline PendK<R> pend_complete(const ChainK<R>& C) {
+  PendK<R> Pd{};
+  Pd.cur_pos = C.p_pos;
+  Pd.cur_dn = C.p_dn;
+  Pd.cur_count = C.p_count;
+  Pd.cap = C.cap;
+  return Pd;
+}
 
 // ---------------------------------------------------------------------------------------
 // moment algebra
@@ -258,6 +305,49 @@ __host__ __device__ __forceinline__ void pops_from_scaled(const R a[Q], R n[Q]) 
   n[18] = w2 * (S8 - D8);
 }
 
+// the same map from w_2-scaled moments a'_k = a_k / 36: n_0 = 12 (...), nearest-neighbour
+// populations 2 (S' +- D'), next-nearest S' +- D'
+template <class R>
+__host__ __device__ __forceinline__ void pops_from_w2scaled(const R a[Q], R n[Q]) {
+  n[0] = R(12) * (a[0] - a[4] + a[16]);
+  const R t = a[0] - a[5] - R(2) * a[16] + a[17];
+  const R Sx = a[0] + R(2) * (a[5] - a[16] - a[17]);
+  const R Sy = t + (a[6] - a[18]);
+  const R Sz = t - (a[6] - a[18]);
+  const R Dx = a[1] - R(2) * a[10], Dy = a[2] - R(2) * a[11], Dz = a[3] - R(2) * a[12];
+  n[1] = R(2) * (Sx + Dx);
+  n[2] = R(2) * (Sx - Dx);
+  n[3] = R(2) * (Sy + Dy);
+  n[4] = R(2) * (Sy - Dy);
+  n[5] = R(2) * (Sz + Dz);
+  n[6] = R(2) * (Sz - Dz);
+  const R base = a[0] + a[4] + a[16];
+  const R P = a[5] + a[17], Qv = a[6] + a[18];
+  const R X = base + P + Qv, Y = base + P - Qv, Z = base - R(2) * P;
+  const R A = a[1] + a[10], B = a[2] + a[11], Cc = a[3] + a[12];
+  const R D3 = (A + B) + (a[13] - a[14]);
+  const R D4 = (A - B) + (a[13] + a[14]);
+  const R D5 = (A + Cc) - (a[13] - a[15]);
+  const R D6 = (A - Cc) - (a[13] + a[15]);
+  const R D7 = (B + Cc) + (a[14] - a[15]);
+  const R D8 = (B - Cc) + (a[14] + a[15]);
+  const R S3 = X + a[7], S4 = X - a[7];
+  const R S5 = Y + a[9], S6 = Y - a[9];
+  const R S7 = Z + a[8], S8 = Z - a[8];
+  n[7] = S3 + D3;
+  n[8] = S3 - D3;
+  n[9] = S4 + D4;
+  n[10] = S4 - D4;
+  n[11] = S5 + D5;
+  n[12] = S5 - D5;
+  n[13] = S6 + D6;
+  n[14] = S6 - D6;
+  n[15] = S7 + D7;
+  n[16] = S7 - D7;
+  n[17] = S8 + D8;
+  n[18] = S8 - D8;
+}
+
 // ---------------------------------------------------------------------------------------
 // LB kernel: pull-stream + collide for every node (Sec. II B, Eq. 3)
 // ---------------------------------------------------------------------------------------
@@ -270,7 +360,8 @@ __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __r
                                                const unsigned L, const unsigned long long plane,
                                                const RoundKeys& rk, unsigned long long* nonpos,
                                                const uint32_t step, const unsigned x, const unsigned y,
-                                               const unsigned z) {
+                                               const unsigned z, const R* __restrict__ dcol = nullptr,
+                                               unsigned dstride = 0) {
   const unsigned xm = x ? x - 1 : L - 1, xp = (x + 1 < L) ? x + 1 : 0;
   const unsigned ym = y ? y - 1 : L - 1, yp = (y + 1 < L) ? y + 1 : 0;
   const unsigned zm = z ? z - 1 : L - 1, zp = (z + 1 < L) ? z + 1 : 0;
@@ -286,6 +377,10 @@ __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __r
     const unsigned idx = sxs[cx(i) + 1] + ry[cy(i) + 1] + rz[cz(i) + 1];
     n[i] = ld<S, R>(src + (unsigned long long)i * plane + idx);
   }
+  if (dcol) {  // previous step's force corrections at the pulled nodes (stamped tiles only)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) n[i] += dcol[i * dstride];
+  }
   const unsigned node = x + y * L + z * LL;
 
   // moments 0..9 (the kinetic modes relax to zero and are not needed)
@@ -293,25 +388,25 @@ __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __r
   moments_0_9<R>(n, m);
   const R rho = DEV ? P.rho0 + m[0] : m[0];
   const R jx = m[1], jy = m[2], jz = m[3];
-  const R ir = R(1) / rho;
+  const R ir = lb_rcp<R>(rho);
   const R xx = jx * jx * ir, yy = jy * jy * ir, zz = jz * jz * ir;
-  // post-collision moments, directly as scaled moments a_k = m*_k / b_k: relaxation of the
-  // stress modes towards equilibrium (Eq. 4), kinetic modes to zero, plus the fluctuating
-  // part sqrt(rho) phi_k g_k / b_k
+  // post-collision moments, directly as w_2-scaled moments a'_k = m*_k / (36 b_k): relaxation
+  // of the stress modes towards equilibrium (Eq. 4), kinetic modes to zero, plus the
+  // fluctuating part sqrt(rho) phi_k g_k / (36 b_k)
   R a[Q];
-  a[0] = m[0];
-  a[1] = jx * R(InvB<1>::v);
-  a[2] = jy * R(InvB<2>::v);
-  a[3] = jz * R(InvB<3>::v);
+  a[0] = m[0] * R(1.0 / 36.0);
+  a[1] = jx * R(InvB<1>::v / 36.0);
+  a[2] = jy * R(InvB<2>::v / 36.0);
+  a[3] = jz * R(InvB<3>::v / 36.0);
   {
     const R e4 = xx + yy + zz, e5 = R(2) * xx - yy - zz, e6 = yy - zz;
     const R e7 = jx * jy * ir, e8 = jy * jz * ir, e9 = jx * jz * ir;
-    a[4] = P.am[4] * m[4] + P.ae[4] * e4;
-    a[5] = P.am[5] * m[5] + P.ae[5] * e5;
-    a[6] = P.am[6] * m[6] + P.ae[6] * e6;
-    a[7] = P.am[7] * m[7] + P.ae[7] * e7;
-    a[8] = P.am[8] * m[8] + P.ae[8] * e8;
-    a[9] = P.am[9] * m[9] + P.ae[9] * e9;
+    a[4] = P.wam[4] * m[4] + P.wae[4] * e4;
+    a[5] = P.wam[5] * m[5] + P.wae[5] * e5;
+    a[6] = P.wam[6] * m[6] + P.wae[6] * e6;
+    a[7] = P.wam[7] * m[7] + P.wae[7] * e7;
+    a[8] = P.wam[8] * m[8] + P.wae[8] * e8;
+    a[9] = P.wam[9] * m[9] + P.wae[9] * e9;
   }
 #pragma unroll
   for (int k = 10; k < Q; ++k) a[k] = R(0);
@@ -319,64 +414,110 @@ __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __r
   if (NOISE) {
     R sr = R(0);
     if (rho > R(0)) {
-      sr = sqrt(rho);
+      sr = lb_sqrt_pos<R>(rho);
     } else {
       atomicAdd(nonpos, 1ull);
     }
     R g[4];  // sqrt(rho) g
     gauss4_rk<R>(step, node, 0u, rk, sr, g);
-    a[4] += P.ag[4] * g[0];
-    a[5] += P.ag[5] * g[1];
-    a[6] += P.ag[6] * g[2];
-    a[7] += P.ag[7] * g[3];
+    a[4] += P.wag[4] * g[0];
+    a[5] += P.wag[5] * g[1];
+    a[6] += P.wag[6] * g[2];
+    a[7] += P.wag[7] * g[3];
     gauss4_rk<R>(step, node, 1u, rk, sr, g);
-    a[8] += P.ag[8] * g[0];
-    a[9] += P.ag[9] * g[1];
+    a[8] += P.wag[8] * g[0];
+    a[9] += P.wag[9] * g[1];
     if (P.ncalls > 2) {
-      a[10] = P.ag[10] * g[2];
-      a[11] = P.ag[11] * g[3];
+      a[10] = P.wag[10] * g[2];
+      a[11] = P.wag[11] * g[3];
       gauss4_rk<R>(step, node, 2u, rk, sr, g);
-      a[12] = P.ag[12] * g[0];
-      a[13] = P.ag[13] * g[1];
-      a[14] = P.ag[14] * g[2];
-      a[15] = P.ag[15] * g[3];
+      a[12] = P.wag[12] * g[0];
+      a[13] = P.wag[13] * g[1];
+      a[14] = P.wag[14] * g[2];
+      a[15] = P.wag[15] * g[3];
       gauss4_rk<R>(step, node, 3u, rk, sr, g);
-      a[16] = P.ag[16] * g[0];
-      a[17] = P.ag[17] * g[1];
-      a[18] = P.ag[18] * g[2];
+      a[16] = P.wag[16] * g[0];
+      a[17] = P.wag[17] * g[1];
+      a[18] = P.wag[18] * g[2];
     }
   }
 
   if (P.body_on) {
     R dm[10];
     force_moments(rho, jx, jy, jz, P.body_dJ[0], P.body_dJ[1], P.body_dJ[2], P.gs, P.gb, dm);
-    a[1] += dm[1] * R(InvB<1>::v);
-    a[2] += dm[2] * R(InvB<2>::v);
-    a[3] += dm[3] * R(InvB<3>::v);
-    a[4] += dm[4] * R(InvB<4>::v);
-    a[5] += dm[5] * R(InvB<5>::v);
-    a[6] += dm[6] * R(InvB<6>::v);
-    a[7] += dm[7] * R(InvB<7>::v);
-    a[8] += dm[8] * R(InvB<8>::v);
-    a[9] += dm[9] * R(InvB<9>::v);
+    a[1] += dm[1] * R(InvB<1>::v / 36.0);
+    a[2] += dm[2] * R(InvB<2>::v / 36.0);
+    a[3] += dm[3] * R(InvB<3>::v / 36.0);
+    a[4] += dm[4] * R(InvB<4>::v / 36.0);
+    a[5] += dm[5] * R(InvB<5>::v / 36.0);
+    a[6] += dm[6] * R(InvB<6>::v / 36.0);
+    a[7] += dm[7] * R(InvB<7>::v / 36.0);
+    a[8] += dm[8] * R(InvB<8>::v / 36.0);
+    a[9] += dm[9] * R(InvB<9>::v / 36.0);
   }
 
   R out[Q];
-  pops_from_scaled<R>(a, out);
+  pops_from_w2scaled<R>(a, out);
 #pragma unroll
   for (int i = 0; i < Q; ++i) st<S, R>(dst + (unsigned long long)i * plane + node, out[i]);
 }
 
-// LB kernel: pull-stream + collide for every node (Sec. II B, Eq. 3); 3D grid of
-// (x-row segments) x (y rows) x z planes.
+// One LB tile: pull-stream + collide for the (blockDim.x x blockDim.y) nodes at
+// (tx, ty, z) (Sec. II B, Eq. 3).  In a tile stamped by the previous deferred step, that
+// step's force corrections are first scattered into a shared table D[i][thread] (each (i,
+// node) pair has at most one source node) and added to the pulled populations.  Shared
+// memory: 19 x blockDim.x x blockDim.y x sizeof(R) when Pd.have_prev.
+template <class S, class R, bool DEV, bool NOISE>
+__device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
+                                        const PendK<R>& Pd, const uint32_t step, unsigned tx, unsigned ty,
+                                        unsigned z, unsigned tile, unsigned char* lsm) {
+  const unsigned L = P.L;
+  const unsigned bx = blockDim.x, by = blockDim.y;
+  const unsigned x = tx * bx + threadIdx.x;
+  const unsigned y = ty * by + threadIdx.y;
+  const unsigned T = bx * by;
+  const unsigned tid = threadIdx.x + bx * threadIdx.y;
+  R* D = nullptr;
+  if (Pd.have_prev && Pd.prev_flags[tile] == Pd.prev_stamp) {  // uniform over the block
+    D = reinterpret_cast<R*>(lsm);
+    for (unsigned j = tid; j < Q * T; j += T) D[j] = R(0);
+    __syncthreads();
+    const int cnt = *Pd.prev_count;
+    const int iL = (int)L;
+    const int x0 = (int)(tx * bx), y0 = (int)(ty * by), z0 = (int)z;
+    constexpr unsigned long long PX = pack_component(0), PY = pack_component(1), PZ = pack_component(2);
+    for (int u = (int)tid; u < cnt; u += (int)T) {
+      const int4 p = Pd.prev_pos[u];
+      // corrected node within one link of the tile (periodic)?
+      if ((p.w - z0 + 1 + iL) % iL > 2) continue;
+      if ((p.z - y0 + 1 + iL) % iL > (int)by + 1) continue;
+      if ((p.y - x0 + 1 + iL) % iL > (int)bx + 1) continue;
+      // a rolled loop keeps this rare path from raising the register count of the kernel
+#pragma unroll 1
+      for (int i = 0; i < Q; ++i) {
+        int rx = p.y + unpack_component(PX, i), ry = p.z + unpack_component(PY, i), rz = p.w + unpack_component(PZ, i);
+        rx = rx < 0 ? rx + iL : (rx >= iL ? rx - iL : rx);
+        ry = ry < 0 ? ry + iL : (ry >= iL ? ry - iL : ry);
+        rz = rz < 0 ? rz + iL : (rz >= iL ? rz - iL : rz);
+        const int lx = rx - x0, ly = ry - y0;
+        if (rz == z0 && lx >= 0 && lx < (int)bx && ly >= 0 && ly < (int)by)
+          D[i * T + ly * bx + lx] = Pd.prev_dn[i * Pd.cap + u];
+      }
+    }
+    __syncthreads();
+  }
+  if (x >= L || y >= L) return;
+  lb_node_update<S, R, DEV, NOISE>(src, dst, P, P.L, P.plane, P.rk, P.nonpos, step, x, y, z,
+                                   D ? D + tid : nullptr, T);
+}
+
+// LB kernel: 3D grid of (x-row segments) x (y rows) x z planes
 template <class S, class R, bool DEV, bool NOISE>
 __global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* __restrict__ dst,
-                                                  const FluidK<R> P, const uint32_t step) {
-  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned y = blockIdx.y * blockDim.y + threadIdx.y;
-  const unsigned z = blockIdx.z;
-  if (x >= P.L || y >= P.L) return;
-  lb_node_update<S, R, DEV, NOISE>(src, dst, P, P.L, P.plane, P.rk, P.nonpos, step, x, y, z);
+                                                  const FluidK<R> P, const PendK<R> Pd, const uint32_t step) {
+  extern __shared__ __align__(16) unsigned char lsm[];
+  const unsigned tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  lb_tile<S, R, DEV, NOISE>(src, dst, P, Pd, step, blockIdx.x, blockIdx.y, blockIdx.z, tile, lsm);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -432,7 +573,7 @@ __device__ __forceinline__ R pair_coef(R r2, bool bonded, const ChainK<R>& C, un
 template <class R>
 __device__ __forceinline__ void chain_forces_block(const R* __restrict__ sh, const R* __restrict__ sl,
                                                    const ChainK<R>& C, R* __restrict__ out) {
-  const int N = C.N, nt = blockDim.x, tid = threadIdx.x;
+  const int N = C.N, nt = blockDim.x * blockDim.y, tid = threadIdx.x + blockDim.x * threadIdx.y;
   int lanes = 1;
   while (lanes < 32 && lanes * 2 * N <= nt) lanes *= 2;
   const int per = nt / lanes;
@@ -443,12 +584,13 @@ __device__ __forceinline__ void chain_forces_block(const R* __restrict__ sh, con
     if (b < N) {
       for (int j = lane; j < N; j += lanes) {
         if (j == b) continue;
+        const bool bonded = (j == b - 1) || (j == b + 1);
         R d[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q)
           d[q] = pair_delta<R>(sh[3 * b + q], sl[3 * b + q], sh[3 * j + q], sl[3 * j + q], C.box, C.half_box);
         const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        const R coef = pair_coef<R>(r2, (j == b - 1) || (j == b + 1), C, C.status);
+        const R coef = pair_coef<R>(r2, bonded, C, C.status);
         f[0] += coef * d[0];
         f[1] += coef * d[1];
         f[2] += coef * d[2];
@@ -463,6 +605,129 @@ __device__ __forceinline__ void chain_forces_block(const R* __restrict__ sh, con
       for (int q = 0; q < 3; ++q) out[3 * b + q] = f[q] + C.ext[q];
     }
   }
+}
+
+// Bitonic sort (ascending) of M keys in shared memory, M a power of two >= 32, by a block of
+// nt threads (a multiple of 32).  Compare-exchange distances j >= 32 go through shared memory
+// with a barrier each; the distances j < 32 of every stage run in registers, each warp
+// holding a contiguous chunk of 32 keys and exchanging through shuffles.
+__device__ __forceinline__ void bitonic_sort_block(unsigned long long* keys, int M, int tid, int nt) {
+  for (int k = 2; k <= M; k <<= 1) {
+    for (int j = k >> 1; j >= 32; j >>= 1) {
+      for (int i = tid; i < M; i += nt) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long ka = keys[i], kb = keys[ixj];
+          const bool up = (i & k) == 0;
+          if ((ka > kb) == up) {
+            keys[i] = kb;
+            keys[ixj] = ka;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < M; i += nt) {  // whole warps: M and nt are multiples of 32
+      unsigned long long v = keys[i];
+      const bool up = (i & k) == 0;
+      for (int j = (k >> 1) < 16 ? (k >> 1) : 16; j > 0; j >>= 1) {
+        const unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)v, j);
+        const unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(v >> 32), j);
+        const unsigned long long o = ((unsigned long long)hi << 32) | lo;
+        // the lower element of the pair keeps the minimum in an ascending run
+        const bool take_min = ((i & j) == 0) == up;
+        v = take_min ? (o < v ? o : v) : (o > v ? o : v);
+      }
+      keys[i] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// open-addressing hash (node -> slot) of the previous step's corrected nodes, in shared
+// memory; probes are bounded by the table size
+__device__ __forceinline__ unsigned hash_node(int node, unsigned mask) {
+  // integer finaliser (xor-shift-multiply, the "lowbias32" constants of C. Wellons' hash
+  // prospector): lattice neighbours differ in few, structured
+  // bits, which a plain multiplicative hash would map to clustered low bits
+  unsigned h = (unsigned)node;
+  h ^= h >> 16;
+  h *= 0x7feb352du;
+  h ^= h >> 15;
+  h *= 0x846ca68bu;
+  h ^= h >> 16;
+  return h & mask;
+}
+// The first four probes are unrolled and branch-free (a data-dependent loop per lookup is
+// very slow in a warp); a lookup still unresolved after them continues in a bounded loop.
+__device__ __forceinline__ int hash_find(const int* __restrict__ hk, const int* __restrict__ hv, unsigned mask,
+                                         int node) {
+  const unsigned h = hash_node(node, mask);
+  int slot = -1;
+  bool stop = false;
+#pragma unroll
+  for (unsigned it = 0; it < 4; ++it) {
+    const unsigned hh = (h + it) & mask;
+    const int k = hk[hh];
+    slot = (!stop && k == node) ? (int)hh : slot;
+    stop = stop || k == node || k < 0;
+  }
+  if (!stop) {
+    for (unsigned it = 4; it <= mask; ++it) {
+      const unsigned hh = (h + it) & mask;
+      const int k = hk[hh];
+      if (k == node) {
+        slot = (int)hh;
+        break;
+      }
+      if (k < 0) break;
+    }
+  }
+  return slot >= 0 ? hv[slot] : -1;
+}
+
+// post-stream populations at node (qx,qy,qz): rho and lattice momentum; with a hash of the
+// previous step's corrections (hmask != 0), the corrections of the pulled nodes are included
+template <class S, class R, bool DEV>
+__device__ __forceinline__ void gather_node_c(const S* __restrict__ pop, const FluidK<R>& P, int qx, int qy,
+                                              int qz, R mom[4], const int* hk, const int* hv, unsigned hmask,
+                                              const R* __restrict__ pdn, int cap) {
+  const int L = (int)P.L;
+  unsigned idx[Q];
+  R v[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {  // all 19 loads in flight before any lookup
+    int sx = qx - cx(i), sy = qy - cy(i), sz = qz - cz(i);
+    sx = sx < 0 ? sx + L : (sx >= L ? sx - L : sx);
+    sy = sy < 0 ? sy + L : (sy >= L ? sy - L : sy);
+    sz = sz < 0 ? sz + L : (sz >= L ? sz - L : sz);
+    idx[i] = (unsigned)sx + (unsigned)L * ((unsigned)sy + (unsigned)L * (unsigned)sz);
+    v[i] = ld<S, R>(pop + (unsigned long long)i * P.plane + idx[i]);
+  }
+  if (hmask) {
+    // lookups first, then every correction load unconditionally (slot 0 stands in for a
+    // missing node and is multiplied by zero), so the loads overlap
+    int u[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) u[i] = hash_find(hk, hv, hmask, (int)idx[i]);
+    R d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = pdn[i * cap + (u[i] >= 0 ? u[i] : 0)];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] += u[i] >= 0 ? d[i] : R(0);
+  }
+  R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    rho += v[i];
+    if (cx(i)) jx += R(cx(i)) * v[i];
+    if (cy(i)) jy += R(cy(i)) * v[i];
+    if (cz(i)) jz += R(cz(i)) * v[i];
+  }
+  mom[0] = DEV ? P.rho0 + rho : rho;
+  mom[1] = jx;
+  mom[2] = jy;
+  mom[3] = jz;
 }
 
 // post-stream populations at node (qx,qy,qz): rho and lattice momentum
@@ -496,13 +761,39 @@ __device__ __forceinline__ void gather_node(const S* __restrict__ pop, const Flu
 // per-node population corrections.  `smem` holds max(6N R, sort keys) bytes.
 template <class S, class R, bool DEV>
 __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const FluidK<R>& P, const ChainK<R>& C,
-                                                const uint32_t step, unsigned char* smem) {
+                                                const PendK<R>& Pd, const uint32_t step, unsigned char* smem) {
   const int N = C.N;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
   const int L = (int)P.L;
   const R h = C.h;
   R* sx = reinterpret_cast<R*>(smem);
   R* sl = sx + 3 * N;
+  // hash of the previous step's corrections (table after the positions, 16-byte aligned)
+  unsigned hmask = 0;
+  int* hk = reinterpret_cast<int*>(smem + ((6 * N * sizeof(R) + 15) & ~(size_t)15));
+  int* hv = nullptr;
+  if (Pd.have_prev) {
+    const int cnt = *Pd.prev_count;
+    unsigned H = 1;
+    while (H < 2u * (unsigned)(cnt > 0 ? cnt : 1)) H <<= 1;
+    hmask = H - 1;
+    hv = hk + H;
+    for (unsigned j = tid; j < H; j += nt) hk[j] = -1;
+    __syncthreads();
+    for (int u = tid; u < cnt; u += nt) {
+      const int node = Pd.prev_pos[u].x;
+      unsigned hh = hash_node(node, hmask);
+      for (unsigned it = 0; it <= hmask; ++it) {
+        const int old = atomicCAS(&hk[hh], -1, node);
+        if (old == -1 || old == node) {
+          hv[hh] = u;
+          break;
+        }
+        hh = (hh + 1) & hmask;
+      }
+    }
+    __syncthreads();
+  }
 
   // MD substeps against the frozen post-stream fluid (one for LB step = MD step)
   for (int sub = 0; sub < C.nsub; ++sub) {
@@ -562,7 +853,7 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
     const int qx = (cl[0] + dx) % L, qy = (cl[1] + dy) % L, qz = (cl[2] + dz) % L;
     const R w = (dx ? fr[0] : R(1) - fr[0]) * (dy ? fr[1] : R(1) - fr[1]) * (dz ? fr[2] : R(1) - fr[2]);
     R mom[4];
-    gather_node<S, R, DEV>(pop, P, qx, qy, qz, mom);
+    gather_node_c<S, R, DEV>(pop, P, qx, qy, qz, mom, hk, hv, hmask, Pd.prev_dn, Pd.cap);
     C.e_node[e] = qx + L * (qy + L * qz);
     C.e_w[e] = w;
 #pragma unroll
@@ -601,28 +892,13 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
   // 5. deterministic spreading: sort (node, entry) keys, sum each node's contributions in
   //    entry order, then turn the node force into population corrections
   const int ne = 8 * N * C.nsub;
-  int M = 1;
+  int M = 32;  // at least one warp-wide chunk; padding keys sort to the end
   while (M < ne) M <<= 1;
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem);
   for (int i = tid; i < M; i += nt)
     keys[i] = (i < ne) ? (((unsigned long long)(unsigned)C.e_node[i] << 32) | (unsigned)i) : ~0ull;
   __syncthreads();
-  for (int k = 2; k <= M; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < M; i += nt) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const unsigned long long ka = keys[i], kb = keys[ixj];
-          const bool up = (i & k) == 0;
-          if ((ka > kb) == up) {
-            keys[i] = kb;
-            keys[ixj] = ka;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
+  bitonic_sort_block(keys, M, tid, nt);
   // leaders: first entry of each node run; slot = number of leaders before it
   // (serial scan by one warp over chunks: ne <= 8192)
   int* slot = reinterpret_cast<int*>(keys + M);
@@ -636,7 +912,7 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
       if (i < ne) slot[i] = lead ? base + __popc(mask & ((1u << tid) - 1u)) : -1;
       base += __popc(mask);
     }
-    if (tid == 0) *C.p_count = base;
+    if (tid == 0) *Pd.cur_count = base;
   }
   __syncthreads();
   for (int i = tid; i < ne; i += nt) {
@@ -672,30 +948,46 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
     }
     R dn[Q];
     dmoments_to_dpops(dm, dn);
-    C.p_node[u] = node;
+    const int pz = node / (L * L), py = (node / L) % L, px = node % L;
+    Pd.cur_pos[u] = make_int4(node, px, py, pz);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) C.p_dn[q * C.cap + u] = dn[q];
+    for (int q = 0; q < Q; ++q) Pd.cur_dn[q * Pd.cap + u] = dn[q];
+    if (Pd.cur_flags) {  // stamp the LB tiles whose nodes pull from this node
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int rx = (px + cx(q) + L) % L, ry = (py + cy(q) + L) % L, rz = (pz + cz(q) + L) % L;
+        const unsigned t = (unsigned)rx / Pd.bx + Pd.tiles_x * ((unsigned)ry / Pd.by + Pd.tiles_y * (unsigned)rz);
+        Pd.cur_flags[t] = Pd.cur_stamp;
+      }
+    }
   }
 }
 
+// Lets the next kernel in the stream, when launched with programmatic stream serialization
+// (the LB kernel of the same step), start while this grid still runs.
+__device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// The bead step as its own one-CTA grid.  The LB kernel of the same step reads neither its
+// outputs nor anything it writes, so it is released at once and runs alongside.
 template <class S, class R, bool DEV>
 __global__ void __launch_bounds__(512) k_bead_step(const S* __restrict__ pop, const FluidK<R> P,
-                                                    const ChainK<R> C, const uint32_t step) {
+                                                    const ChainK<R> C, const PendK<R> Pd, const uint32_t step) {
   extern __shared__ __align__(16) unsigned char smem[];
-  bead_step_block<S, R, DEV>(pop, P, C, step, smem);
+  allow_dependent_launch();
+  bead_step_block<S, R, DEV>(pop, P, C, Pd, step, smem);
 }
 
 // B[i][node] += dn_i at every pending node (each node appears once in the list); one thread
 // per (node, population): blockIdx.y is the population
 template <class S, class R>
 __global__ void __launch_bounds__(256) k_apply_pending(S* __restrict__ pop, const FluidK<R> P,
-                                                        const int* __restrict__ p_node,
+                                                        const int4* __restrict__ p_pos,
                                                         const R* __restrict__ p_dn,
                                                         const int* __restrict__ p_count, int cap) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= *p_count) return;
   const int i = blockIdx.y;
-  S* p = pop + (unsigned long long)i * P.plane + (unsigned)p_node[u];
+  S* p = pop + (unsigned long long)i * P.plane + (unsigned)p_pos[u].x;
   st<S, R>(p, ld<S, R>(p) + p_dn[i * cap + u]);
 }
 

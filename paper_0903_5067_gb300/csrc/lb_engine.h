@@ -50,7 +50,12 @@ class Engine {
   // fluid at rest, chain from x0/v0 (3N doubles each, v0 may be null), forces F0
   virtual void initialise(const double* x0, const double* v0, cudaStream_t s) = 0;
   virtual void set_config(const Config& c) = 0;  // options changed (same sizes)
+  // one step, complete on return (ev0/ev1, when given, bracket the LB kernel)
   virtual void step(uint32_t k, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) = 0;
+  // one step whose bead force correction stays pending until the next deferred step reads
+  // it or flush() applies it; every other method flushes first
+  virtual void step_deferred(uint32_t k, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) = 0;
+  virtual void flush(cudaStream_t s) = 0;
   virtual void get_populations(double* out, cudaStream_t s) = 0;
   virtual void set_populations(const double* in, cudaStream_t s) = 0;
   virtual void get_beads(double* x, double* v, cudaStream_t s) = 0;

@@ -39,6 +39,14 @@ class EngineT final : public Engine {
       cuda_check(cudaFuncSetAttribute(k_bead_step<S, R, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)bead_smem()),
                  "bead kernel shared memory");
+    if (lb_smem() > 48 * 1024) {
+      cuda_check(cudaFuncSetAttribute(k_lb_step<S, R, DEV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)lb_smem()),
+                 "LB kernel shared memory");
+      cuda_check(cudaFuncSetAttribute(k_lb_step<S, R, DEV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)lb_smem()),
+                 "LB kernel shared memory");
+    }
     const unsigned long long nb = (nnodes_ + 255) / 256;
     k_init_rest<S, R, DEV><<<(unsigned)nb, 256, 0, s>>>(pop_[0], nnodes_, plane_, (R)cfg_.rho);
     cuda_check(cudaGetLastError(), "init populations");
@@ -75,44 +83,59 @@ class EngineT final : public Engine {
       k_chain_init_forces<R><<<1, 512, 6 * N_ * sizeof(R), s>>>(C);
       cuda_check(cudaGetLastError(), "init forces");
     }
-    cuda_check(cudaMemsetAsync(p_count_, 0, sizeof(int), s), "memset pending");
+    for (int j = 0; j < 2; ++j) cuda_check(cudaMemsetAsync(p_count_[j], 0, sizeof(int), s), "memset pending");
+    reset_stamps(s);
   }
 
-  // One coupled step.  The bead kernel (one CTA) and the LB kernel both read only buffer A,
-  // so the bead kernel runs on a side stream concurrently with the LB kernel; the force
-  // correction joins them and adds the bead reaction to buffer B.
+  // One coupled step, complete on return: the bead kernel (one CTA), then the LB kernel,
+  // released as soon as the bead CTA is resident (both read only buffer A), then the force
+  // correction adds the bead reaction to buffer B.  One stream.
   void step(uint32_t k, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) override {
+    flush(s);
     const FluidK<R> P = fluid();
     const S* A = pop_[cur_];
     S* Bo = pop_[cur_ ^ 1];
-    if (N_ > 0) {
-      ensure_side_stream();
-      const ChainK<R> C = chain();
-      cuda_check(cudaEventRecord(ev_ready_, s), "record ready");
-      cuda_check(cudaStreamWaitEvent(side_, ev_ready_, 0), "wait ready");
-      k_bead_step<S, R, DEV><<<1, 512, bead_smem(), side_>>>(A, P, C, k);
-      cuda_check(cudaGetLastError(), "bead kernel");
-      cuda_check(cudaEventRecord(ev_bead_, side_), "record bead");
-    }
-    dim3 blk, grd;
-    lb_launch_shape(blk, grd);
-    if (ev0) cudaEventRecord(ev0, s);
-    if (P.ncalls > 0)
-      k_lb_step<S, R, DEV, true><<<grd, blk, 0, s>>>(A, Bo, P, k);
-    else
-      k_lb_step<S, R, DEV, false><<<grd, blk, 0, s>>>(A, Bo, P, k);
-    if (ev1) cudaEventRecord(ev1, s);
-    cuda_check(cudaGetLastError(), "LB kernel");
-    if (N_ > 0) {
-      cuda_check(cudaStreamWaitEvent(s, ev_bead_, 0), "wait bead");
-      k_apply_pending<S, R><<<dim3((cap_ + 255) / 256, Q), 256, 0, s>>>(Bo, P, p_node_, p_dn_, p_count_, cap_);
-      cuda_check(cudaGetLastError(), "apply kernel");
-    }
+    const PendK<R> Pd = pend(false);
+    if (N_ > 0) launch_bead(A, P, Pd, k, s);
+    launch_lb(A, Bo, P, Pd, k, s, ev0, ev1);
+    if (N_ > 0) apply(Bo, P, pslot_, s);
     cur_ ^= 1;
+  }
+
+  // One coupled step whose force correction stays pending: the next deferred step adds it
+  // where it reads the populations (the LB tiles stamped by this step, the bead kernel in
+  // its gather), and flush() applies it.  Stream order gives every dependency: the bead
+  // kernel of step k starts after the LB and bead kernels of step k-1 have completed, and
+  // the LB kernel of step k, released early, touches nothing the bead kernel of step k
+  // reads or writes.
+  void step_deferred(uint32_t k, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) override {
+    if (N_ == 0) {
+      step(k, s, ev0, ev1);
+      return;
+    }
+    if (!open_ && stamp_ > (1 << 30)) reset_stamps(s);
+    const FluidK<R> P = fluid();
+    const S* A = pop_[cur_];
+    S* Bo = pop_[cur_ ^ 1];
+    if (open_) pslot_ ^= 1;
+    const PendK<R> Pd = pend(true);
+    launch_bead(A, P, Pd, k, s);
+    launch_lb(A, Bo, P, Pd, k, s, ev0, ev1);
+    ++stamp_;
+    open_ = true;
+    cur_ ^= 1;
+  }
+
+  // apply the pending force correction of the last deferred step
+  void flush(cudaStream_t s) override {
+    if (!open_) return;
+    apply(pop_[cur_], fluid(), pslot_, s);
+    open_ = false;
   }
 
   void adjoint_displacement(int64_t T, int K, uint32_t k0, double* O, double* gx, double* gz,
                             cudaStream_t s) override {
+    flush(s);
     if (N_ == 0) throw LbError(S_STATE, "adjoint needs a chain");
     if (nsub_ != 1) throw LbError(S_STATE, "adjoint needs one MD step per LB step");
     const FluidK<R> P = fluid();
@@ -287,13 +310,8 @@ class EngineT final : public Engine {
   int chain_length() const { return N_; }
   const Config& config() const { return cfg_; }
 
-  ~EngineT() override {
-    if (side_) cudaStreamDestroy(side_);
-    if (ev_ready_) cudaEventDestroy(ev_ready_);
-    if (ev_bead_) cudaEventDestroy(ev_bead_);
-  }
-
   void get_populations(double* out, cudaStream_t s) override {
+    flush(s);
     double* stage = reinterpret_cast<double*>(pop_[cur_ ^ 1]);
     const unsigned nb = (unsigned)((nnodes_ + 255) / 256);
     for (int i = 0; i < Q; ++i) {
@@ -308,6 +326,7 @@ class EngineT final : public Engine {
   }
 
   void set_populations(const double* in, cudaStream_t s) override {
+    flush(s);
     double* stage = reinterpret_cast<double*>(pop_[cur_ ^ 1]);
     const unsigned nb = (unsigned)((nnodes_ + 255) / 256);
     for (int i = 0; i < Q; ++i) {
@@ -318,11 +337,11 @@ class EngineT final : public Engine {
       k_plane_from_f64<S, R, DEV><<<nb, 256, 0, s>>>(pop_[cur_] + (size_t)i * plane_, stage, nnodes_, wr);
       cuda_check(cudaGetLastError(), "plane from f64");
     }
-    cuda_check(cudaMemsetAsync(p_count_, 0, sizeof(int), s), "memset pending");
     cuda_check(cudaStreamSynchronize(s), "sync upload");
   }
 
   void get_beads(double* x, double* v, cudaStream_t s) override {
+    flush(s);
     if (N_ == 0) return;
     std::vector<R> xw(3 * N_), xlo(3 * N_), vv(3 * N_);
     std::vector<int> im(3 * N_);
@@ -339,6 +358,7 @@ class EngineT final : public Engine {
   }
 
   void observables(double* out, int64_t step, int accumulate, cudaStream_t s) override {
+    flush(s);
     ObsK<R> O = obs(step, accumulate);
     if (!accumulate) {
       k_fluid_partials<S, R, DEV><<<nparts_, 256, 0, s>>>(pop_[cur_], nnodes_, plane_, parts_);
@@ -363,6 +383,7 @@ class EngineT final : public Engine {
   }
 
   unsigned read_status(cudaStream_t s) override {
+    flush(s);
     unsigned st = 0;
     cuda_check(cudaMemcpyAsync(&st, status_, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "status");
     cuda_check(cudaStreamSynchronize(s), "sync status");
@@ -375,6 +396,7 @@ class EngineT final : public Engine {
            4 * sizeof(double) + sizeof(unsigned long long);
   }
   void save_state(void* host, cudaStream_t s) override {
+    flush(s);
     unsigned char* p = static_cast<unsigned char*>(host);
     for (int i = 0; i < Q; ++i) {
       cuda_check(cudaMemcpyAsync(p, pop_[cur_] + (size_t)i * plane_, nnodes_ * sizeof(S), cudaMemcpyDeviceToHost, s),
@@ -385,6 +407,7 @@ class EngineT final : public Engine {
     cuda_check(cudaStreamSynchronize(s), "sync save");
   }
   void load_state(const void* host, cudaStream_t s) override {
+    flush(s);
     unsigned char* p = const_cast<unsigned char*>(static_cast<const unsigned char*>(host));
     for (int i = 0; i < Q; ++i) {
       cuda_check(cudaMemcpyAsync(pop_[cur_] + (size_t)i * plane_, p, nnodes_ * sizeof(S), cudaMemcpyHostToDevice, s),
@@ -392,7 +415,6 @@ class EngineT final : public Engine {
       p += nnodes_ * sizeof(S);
     }
     p = copy_beads(p, false, s);
-    cuda_check(cudaMemsetAsync(p_count_, 0, sizeof(int), s), "memset pending");
     cuda_check(cudaStreamSynchronize(s), "sync load");
   }
 
@@ -419,15 +441,84 @@ class EngineT final : public Engine {
     return p;
   }
 
-  void ensure_side_stream() {
-    if (side_) return;
-    // highest priority: the bead CTA is dispatched ahead of the LB kernel's queued CTAs
-    int least = 0, greatest = 0;
-    cuda_check(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
-    cuda_check(cudaStreamCreateWithPriority(&side_, cudaStreamNonBlocking, greatest), "side stream");
-    cuda_check(cudaEventCreateWithFlags(&ev_ready_, cudaEventDisableTiming), "event");
-    cuda_check(cudaEventCreateWithFlags(&ev_bead_, cudaEventDisableTiming), "event");
+  void launch_bead(const S* A, const FluidK<R>& P, const PendK<R>& Pd, uint32_t k, cudaStream_t s) {
+    k_bead_step<S, R, DEV><<<1, 512, bead_smem(), s>>>(A, P, chain(), Pd, k);
+    cuda_check(cudaGetLastError(), "bead kernel");
   }
+
+  // LB kernel with programmatic stream serialization: it may start once the preceding bead
+  // kernel has signalled (at its start); without a preceding bead kernel it is an ordinary
+  // launch.  Timing events, when given, bracket it.
+  void launch_lb(const S* A, S* Bo, const FluidK<R>& P, const PendK<R>& Pd, uint32_t k, cudaStream_t s,
+                 cudaEvent_t ev0, cudaEvent_t ev1) {
+    dim3 blk, grd;
+    lb_launch_shape(blk, grd);
+    cudaLaunchConfig_t lc;
+    memset(&lc, 0, sizeof(lc));
+    lc.gridDim = grd;
+    lc.blockDim = blk;
+    lc.dynamicSmemBytes = Pd.have_prev ? lb_smem() : 0;
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    if (ev0) cudaEventRecord(ev0, s);
+    if (P.ncalls > 0)
+      cuda_check(cudaLaunchKernelEx(&lc, k_lb_step<S, R, DEV, true>, A, Bo, P, Pd, k), "LB kernel");
+    else
+      cuda_check(cudaLaunchKernelEx(&lc, k_lb_step<S, R, DEV, false>, A, Bo, P, Pd, k), "LB kernel");
+    if (ev1) cudaEventRecord(ev1, s);
+    cuda_check(cudaGetLastError(), "LB kernel");
+  }
+
+  void apply(S* buf, const FluidK<R>& P, int slot, cudaStream_t s) {
+    k_apply_pending<S, R><<<dim3((cap_ + 255) / 256, Q), 256, 0, s>>>(buf, P, p_pos_[slot], p_dn_[slot],
+                                                                     p_count_[slot], cap_);
+    cuda_check(cudaGetLastError(), "apply kernel");
+  }
+
+  // pending-correction block: deferred steps read slot pslot_^1 (when open) and write
+  // pslot_ with stamps; complete steps write slot pslot_ only, without stamps
+  PendK<R> pend(bool deferred) const {
+    PendK<R> Pd;
+    memset(&Pd, 0, sizeof(Pd));
+    const int c = pslot_, p = pslot_ ^ 1;
+    Pd.have_prev = (deferred && open_) ? 1 : 0;
+    Pd.prev_stamp = stamp_ - 1;
+    Pd.prev_pos = p_pos_[p];
+    Pd.prev_dn = p_dn_[p];
+    Pd.prev_count = p_count_[p];
+    Pd.prev_flags = flags_[p];
+    Pd.cur_pos = p_pos_[c];
+    Pd.cur_dn = p_dn_[c];
+    Pd.cur_count = p_count_[c];
+    Pd.cur_flags = deferred ? flags_[c] : nullptr;
+    Pd.cur_stamp = stamp_;
+    Pd.cap = cap_;
+    dim3 blk, grd;
+    lb_launch_shape(blk, grd);
+    Pd.bx = blk.x;
+    Pd.by = blk.y;
+    Pd.tiles_x = grd.x;
+    Pd.tiles_y = grd.y;
+    return Pd;
+  }
+
+  void reset_stamps(cudaStream_t s) {
+    for (int j = 0; j < 2; ++j)
+      cuda_check(cudaMemsetAsync(flags_[j], 0xff, ntiles() * sizeof(int), s), "memset stamps");
+    stamp_ = 0;
+  }
+
+  size_t ntiles() const {
+    dim3 blk, grd;
+    lb_launch_shape(blk, grd);
+    return (size_t)grd.x * grd.y * grd.z;
+  }
+
+  size_t lb_smem() const { return (size_t)Q * 256 * sizeof(R); }
 
   void lb_launch_shape(dim3& blk, dim3& grd) const {
     unsigned bx = ((unsigned)L_ + 31) / 32 * 32;
@@ -439,10 +530,13 @@ class EngineT final : public Engine {
 
   size_t bead_smem() const {
     const size_t ne = 8 * (size_t)N_ * nsub_;
-    size_t M = 1;
+    size_t M = 32;
     while (M < ne) M <<= 1;
     const size_t sortb = M * 8 + ne * 4;
-    const size_t posb = 6 * (size_t)N_ * sizeof(R);
+    // positions (hi, lo), then the hash of the previous step's corrections (2 x H ints)
+    size_t H = 1;
+    while (H < 2 * (size_t)cap_) H <<= 1;
+    const size_t posb = align_up(6 * (size_t)N_ * sizeof(R), 16) + 2 * H * sizeof(int);
     return sortb > posb ? sortb : posb;
   }
 
@@ -473,6 +567,9 @@ class EngineT final : public Engine {
       P.am[k] = (R)(g / bk);
       P.ae[k] = (R)((1.0 - g) / bk);
       P.ag[k] = (R)(cn / bk);
+      P.wam[k] = (R)(g / bk / 36.0);
+      P.wae[k] = (R)((1.0 - g) / bk / 36.0);
+      P.wag[k] = (R)(cn / bk / 36.0);
     }
     P.k0 = (uint32_t)(c.seed & 0xffffffffu);
     P.k1 = (uint32_t)(0u | ((uint32_t)c.replica << 8));
@@ -526,9 +623,9 @@ class EngineT final : public Engine {
     C.e_node = e_node_;
     C.e_w = e_w_;
     C.e_mom = e_mom_;
-    C.p_node = p_node_;
-    C.p_dn = p_dn_;
-    C.p_count = p_count_;
+    C.p_pos = p_pos_[0];
+    C.p_dn = p_dn_[0];
+    C.p_count = p_count_[0];
     C.cap = cap_;
     C.status = status_;
     return C;
@@ -587,9 +684,12 @@ class EngineT final : public Engine {
     e_node_ = reinterpret_cast<int*>(take(cap_ * sizeof(int)));
     e_w_ = reinterpret_cast<R*>(take(cap_ * sizeof(R)));
     e_mom_ = reinterpret_cast<R*>(take(4 * cap_ * sizeof(R)));
-    p_node_ = reinterpret_cast<int*>(take(cap_ * sizeof(int)));
-    p_dn_ = reinterpret_cast<R*>(take((size_t)Q * cap_ * sizeof(R)));
-    p_count_ = reinterpret_cast<int*>(take(sizeof(int)));
+    for (int j = 0; j < 2; ++j) {
+      p_pos_[j] = reinterpret_cast<int4*>(take(cap_ * sizeof(int4)));
+      p_dn_[j] = reinterpret_cast<R*>(take((size_t)Q * cap_ * sizeof(R)));
+      p_count_[j] = reinterpret_cast<int*>(take(sizeof(int)));
+      flags_[j] = reinterpret_cast<int*>(take(ntiles() * sizeof(int)));
+    }
     status_ = reinterpret_cast<unsigned*>(take(sizeof(unsigned)));
     nonpos_ = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long)));
     acc_ = reinterpret_cast<double*>(take(4 * sizeof(double)));
@@ -603,8 +703,6 @@ class EngineT final : public Engine {
   unsigned long long nnodes_ = 0, plane_ = 0;
   size_t bytes_ = 0;
   int cur_ = 0;
-  cudaStream_t side_ = nullptr;
-  cudaEvent_t ev_ready_ = nullptr, ev_bead_ = nullptr;
   S* pop_[2] = {nullptr, nullptr};
   R *fch_ = nullptr;
   R *x_ = nullptr, *xl_ = nullptr, *v_ = nullptr, *F_ = nullptr, *Fc_ = nullptr, *vh_ = nullptr, *fcons_ = nullptr;
@@ -612,9 +710,12 @@ class EngineT final : public Engine {
   double* xref_ = nullptr;
   int* e_node_ = nullptr;
   R *e_w_ = nullptr, *e_mom_ = nullptr;
-  int* p_node_ = nullptr;
-  R* p_dn_ = nullptr;
-  int* p_count_ = nullptr;
+  int4* p_pos_[2] = {nullptr, nullptr};
+  R* p_dn_[2] = {nullptr, nullptr};
+  int* p_count_[2] = {nullptr, nullptr};
+  int* flags_[2] = {nullptr, nullptr};  // per LB tile: stamp of the last deferred step that corrected it
+  int pslot_ = 0, stamp_ = 0;
+  bool open_ = false;  // a deferred step's correction is pending
   unsigned* status_ = nullptr;
   unsigned long long* nonpos_ = nullptr;
   double *acc_ = nullptr, *obs_ = nullptr, *parts_ = nullptr;
