@@ -446,9 +446,11 @@ class EngineT final : public Engine {
     cuda_check(cudaGetLastError(), "bead kernel");
   }
 
-  // LB kernel with programmatic stream serialization: it may start once the preceding bead
-  // kernel has signalled (at its start); without a preceding bead kernel it is an ordinary
-  // launch.  Timing events, when given, bracket it.
+  // LB kernel.  After the bead kernel of the same step it is launched with programmatic
+  // stream serialization and may start once the bead kernel has signalled (at its start); the
+  // LB kernel reads nothing the bead kernel writes.  Otherwise (no chain) it is an ordinary
+  // launch, which waits for the previous step's LB kernel to complete.  Timing events, when
+  // given, bracket it.
   void launch_lb(const S* A, S* Bo, const FluidK<R>& P, const PendK<R>& Pd, uint32_t k, cudaStream_t s,
                  cudaEvent_t ev0, cudaEvent_t ev1) {
     dim3 blk, grd;
@@ -463,7 +465,7 @@ class EngineT final : public Engine {
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = at;
-    lc.numAttrs = 1;
+    lc.numAttrs = N_ > 0 ? 1 : 0;
     if (ev0) cudaEventRecord(ev0, s);
     if (P.ncalls > 0)
       cuda_check(cudaLaunchKernelEx(&lc, k_lb_step<S, R, DEV, true>, A, Bo, P, Pd, k), "LB kernel");
