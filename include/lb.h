@@ -134,6 +134,17 @@ int lb_set_obs_stride(lb_ctx* ctx, int stride);
 /* Take the current bead positions as the reference t0 of g1 and g3; clear accumulators. */
 int lb_reset_reference(lb_ctx* ctx);
 
+/* Trajectory recording for the observables of Sec. III A/B (g1, g2, g3, Rouse modes,
+ * S(k), S(k,t); see the lb_analysis_* functions below).  traj_dev: caller-owned device
+ * memory for `capacity` frames of 3N doubles (unwrapped positions, [frame][bead][xyz]),
+ * used as a ring: frame f is stored at slot f mod capacity.  Frame 0 is the current state,
+ * written at this call; then one frame after every `stride` steps of lb_step.  A NULL
+ * buffer, capacity <= 0 or stride <= 0 stops recording.  LB_ERR_STATE without a chain.
+ * The library writes the buffer on its stream; read it after lb_sync. */
+int lb_record_trajectory(lb_ctx* ctx, double* traj_dev, int capacity, int stride);
+/* Frames recorded since the last lb_record_trajectory (the ring keeps the last capacity). */
+int lb_trajectory_frames(lb_ctx* ctx, int64_t* frames);
+
 /* Gradient of a chain observable through T coupled steps, by the adjoint of the step with
  * the noise held fixed (same Philox streams forward and backward).  Observable:
  * O = sum_b |x_b(T) - x_b(0)|^2 (unwrapped positions).  Gradients with respect to the
@@ -205,6 +216,33 @@ int64_t lb_batch_nodes(lb_batch* b); /* total nodes of all replicas */
  * with lb_batch_get_observables (entries 17..19). */
 int lb_batch_accumulate(lb_batch* b);
 void lb_batch_destroy(lb_batch* b);
+
+/* --- chain observables on a device trajectory (Sec. III A and III B) ----------------------
+ * traj: T frames of N beads, [t][n][xyz] FP64 unwrapped positions on the current device
+ * (e.g. the ring of lb_record_trajectory, unrolled to oldest-first).  Outputs are
+ * caller-owned device arrays, written on `stream` (a cudaStream_t, NULL = legacy default);
+ * nothing is allocated and nothing synchronises.  Averages over time origins use every
+ * origin t0 with t0 + lag < T.  Every output element is a fixed-order sum, so results are
+ * reproducible bit for bit.  Invalid sizes or pointers return LB_ERR_ARG.
+ *
+ * lb_analysis_msd: out[3][max_lag+1] = g1, g2, g3 at lags 0..max_lag: the mean-square
+ *   displacement of monomers i0 and i1 (averaged over both; the paper uses the two innermost
+ *   monomers), the same in the centre-of-mass frame, and of the centre of mass (Sec. III B).
+ * lb_analysis_rouse_modes: X[T][P][3], X_p(t) = (1/N) sum_{n=1..N} r_n(t) cos(p pi (n-1/2)/N)
+ *   for p = 1..P, P <= N-1 (Sec. III B, Rouse modes).
+ * lb_analysis_rouse_correlation: c[P][max_lag+1] = < X_p(t0+lag) . X_p(t0) >; c[p][0] is
+ *   <X_p^2>, the normalisation of the paper's correlation function.  max_lag <= 65535.
+ * lb_analysis_static_sk: S[nk] = (1/N) sum_{i,j} < sin(k r_ij) / (k r_ij) > over the T
+ *   frames, for the nk wave numbers k[] (device array) (Sec. III A, S(k)).
+ * lb_analysis_dynamic_sk: S[nk][max_lag+1] = (1/N) sum_{i,j} < sin(k d)/(k d) >,
+ *   d = |r_i(t0+lag) - r_j(t0)|, over origins t0 = 0, s, 2s, ... (s = origin_stride)
+ *   (Sec. III B, S(k,t); the isotropic average of exp(i k.[r_i(t) - r_j(0)])). */
+int lb_analysis_msd(const double* traj, int T, int N, int max_lag, int i0, int i1, double* out, void* stream);
+int lb_analysis_rouse_modes(const double* traj, int T, int N, int P, double* X, void* stream);
+int lb_analysis_rouse_correlation(const double* X, int T, int P, int max_lag, double* c, void* stream);
+int lb_analysis_static_sk(const double* traj, int T, int N, const double* k, int nk, double* S, void* stream);
+int lb_analysis_dynamic_sk(const double* traj, int T, int N, const double* k, int nk, int max_lag,
+                           int origin_stride, double* S, void* stream);
 
 /* --- allocation-free variant ---------------------------------------------------------
  * Fluid mass and momentum of a population field, like lb_get_observables' entries [1] and

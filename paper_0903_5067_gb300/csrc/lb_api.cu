@@ -43,6 +43,10 @@ struct lb_ctx {
   Config cfg;
   std::vector<double> x0, v0;
   int obs_stride = 0;
+  // trajectory recording: caller-owned device ring of traj_cap frames of 3N doubles
+  double* traj = nullptr;
+  int traj_cap = 0, traj_stride = 0;
+  int64_t traj_frames = 0, traj_origin = 0;
   cudaStream_t stream = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -57,6 +61,9 @@ struct lb_ctx {
 };
 
 namespace {
+
+int fail(int code, const char* msg);
+void record_frame(lb_ctx* ctx);
 
 int fail(int code, const char* msg) {
   if (getenv("GBLB_VERBOSE")) fprintf(stderr, "libgblb: %s\n", msg);
@@ -135,6 +142,12 @@ bool generate_chain(const Config& c, double bond, int saw, std::vector<double>& 
     if (!placed) return false;
   }
   return true;
+}
+
+void record_frame(lb_ctx* ctx) {
+  double* dst = ctx->traj + (size_t)(ctx->traj_frames % ctx->traj_cap) * 3 * (size_t)ctx->cfg.N;
+  ctx->eng->record_frame(dst, ctx->stream);
+  ctx->traj_frames += 1;
 }
 
 void materialise(lb_ctx* ctx) {
@@ -328,6 +341,7 @@ int lb_step(lb_ctx* ctx, int64_t n) {
       ctx->step += 1;
       if (ctx->obs_stride > 0 && ctx->cfg.N > 0 && ctx->step % ctx->obs_stride == 0)
         ctx->eng->observables(nullptr, ctx->step, 1, ctx->stream);
+      if (ctx->traj && (ctx->step - ctx->traj_origin) % ctx->traj_stride == 0) record_frame(ctx);
     }
     ctx->eng->flush(ctx->stream);
     return (int)LB_OK;
@@ -392,6 +406,32 @@ int lb_get_observables(lb_ctx* ctx, double* out, size_t cap) {
     ctx->eng->observables(out, ctx->step, 0, ctx->stream);
     return status_from_device(ctx->eng->read_status(ctx->stream));
   });
+}
+
+int lb_record_trajectory(lb_ctx* ctx, double* traj_dev, int capacity, int stride) {
+  if (!ctx) return LB_ERR_ARG;
+  if (!traj_dev || capacity <= 0 || stride <= 0) {
+    ctx->traj = nullptr;
+    ctx->traj_cap = ctx->traj_stride = 0;
+    return LB_OK;
+  }
+  if (ctx->cfg.N <= 0) return fail(LB_ERR_STATE, "trajectory recording needs a chain");
+  return guarded([&] {
+    materialise(ctx);
+    ctx->traj = traj_dev;
+    ctx->traj_cap = capacity;
+    ctx->traj_stride = stride;
+    ctx->traj_frames = 0;
+    ctx->traj_origin = ctx->step;
+    record_frame(ctx);
+    return (int)LB_OK;
+  });
+}
+
+int lb_trajectory_frames(lb_ctx* ctx, int64_t* frames) {
+  if (!ctx || !frames) return LB_ERR_ARG;
+  *frames = ctx->traj ? ctx->traj_frames : 0;
+  return LB_OK;
 }
 
 int lb_set_obs_stride(lb_ctx* ctx, int stride) {

@@ -991,6 +991,15 @@ __global__ void __launch_bounds__(256) k_apply_pending(S* __restrict__ pop, cons
   st<S, R>(p, ld<S, R>(p) + p_dn[i * cap + u]);
 }
 
+// one trajectory frame: unwrapped positions x + xl + img * box in FP64, in the order (and
+// without contraction) of the host read-back
+template <class R>
+__global__ void k_record_frame(const R* __restrict__ x, const R* __restrict__ xl, const int* __restrict__ img,
+                               int n3, double box, double* __restrict__ dst) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += gridDim.x * blockDim.x)
+    dst[t] = __dadd_rn(__dadd_rn((double)x[t], (double)xl[t]), __dmul_rn((double)img[t], box));
+}
+
 // ---------------------------------------------------------------------------------------
 // initial state, conversions, reductions
 // ---------------------------------------------------------------------------------------

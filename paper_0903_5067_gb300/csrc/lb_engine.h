@@ -61,6 +61,8 @@ class Engine {
   virtual void get_beads(double* x, double* v, cudaStream_t s) = 0;
   virtual void observables(double* out, int64_t step, int accumulate, cudaStream_t s) = 0;
   virtual void reset_reference(cudaStream_t s) = 0;
+  // write the current unwrapped bead positions (3N doubles) to device memory
+  virtual void record_frame(double* dst, cudaStream_t s) = 0;
   virtual unsigned read_status(cudaStream_t s) = 0;
   // adjoint: objective O = sum_b |x_b(T) - x_b(0)|^2 over T steps from the current state,
   // its gradient with respect to the current bead positions (3N) and zeta, noise fixed,

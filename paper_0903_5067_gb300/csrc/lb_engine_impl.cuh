@@ -382,6 +382,15 @@ class EngineT final : public Engine {
     cuda_check(cudaStreamSynchronize(s), "sync ref");
   }
 
+  // bead arrays are final once the bead kernel of the last step has run (pending fluid
+  // corrections do not touch them), so no flush
+  void record_frame(double* dst, cudaStream_t s) override {
+    if (N_ == 0) return;
+    const int n3 = 3 * N_;
+    k_record_frame<R><<<(n3 + 255) / 256, 256, 0, s>>>(x_, xl_, img_, n3, cfg_.L * cfg_.a, dst);
+    cuda_check(cudaGetLastError(), "record frame");
+  }
+
   unsigned read_status(cudaStream_t s) override {
     flush(s);
     unsigned st = 0;

@@ -43,6 +43,13 @@ _SIGS = {
     "lb_get_beads": (C.c_int, [_vp, _dp, _dp, C.c_size_t]),
     "lb_get_observables": (C.c_int, [_vp, _dp, C.c_size_t]),
     "lb_set_obs_stride": (C.c_int, [_vp, C.c_int]),
+    "lb_record_trajectory": (C.c_int, [_vp, _vp, C.c_int, C.c_int]),
+    "lb_trajectory_frames": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
+    "lb_analysis_msd": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp]),
+    "lb_analysis_rouse_modes": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
+    "lb_analysis_rouse_correlation": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
+    "lb_analysis_static_sk": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_int, _vp, _vp]),
+    "lb_analysis_dynamic_sk": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
     "lb_reset_reference": (C.c_int, [_vp]),
     "lb_save": (C.c_int, [_vp, C.c_char_p]),
     "lb_load": (C.c_int, [_vp, C.c_char_p]),
@@ -174,6 +181,37 @@ def lb_get_observables(ctx) -> np.ndarray:
 
 def lb_set_obs_stride(ctx, stride: int):
     _check(_lib.lb_set_obs_stride(ctx, int(stride)), "lb_set_obs_stride")
+
+
+def lb_record_trajectory(ctx, traj_ptr: int, capacity: int, stride: int):
+    _check(_lib.lb_record_trajectory(ctx, traj_ptr, int(capacity), int(stride)), "lb_record_trajectory")
+
+
+def lb_trajectory_frames(ctx) -> int:
+    n = C.c_int64()
+    _check(_lib.lb_trajectory_frames(ctx, C.byref(n)), "lb_trajectory_frames")
+    return n.value
+
+
+def lb_analysis_msd(traj_ptr, T, N, max_lag, i0, i1, out_ptr, stream):
+    _check(_lib.lb_analysis_msd(traj_ptr, T, N, max_lag, i0, i1, out_ptr, stream), "lb_analysis_msd")
+
+
+def lb_analysis_rouse_modes(traj_ptr, T, N, P, X_ptr, stream):
+    _check(_lib.lb_analysis_rouse_modes(traj_ptr, T, N, P, X_ptr, stream), "lb_analysis_rouse_modes")
+
+
+def lb_analysis_rouse_correlation(X_ptr, T, P, max_lag, c_ptr, stream):
+    _check(_lib.lb_analysis_rouse_correlation(X_ptr, T, P, max_lag, c_ptr, stream), "lb_analysis_rouse_correlation")
+
+
+def lb_analysis_static_sk(traj_ptr, T, N, k_ptr, nk, S_ptr, stream):
+    _check(_lib.lb_analysis_static_sk(traj_ptr, T, N, k_ptr, nk, S_ptr, stream), "lb_analysis_static_sk")
+
+
+def lb_analysis_dynamic_sk(traj_ptr, T, N, k_ptr, nk, max_lag, origin_stride, S_ptr, stream):
+    _check(_lib.lb_analysis_dynamic_sk(traj_ptr, T, N, k_ptr, nk, max_lag, origin_stride, S_ptr, stream),
+           "lb_analysis_dynamic_sk")
 
 
 def lb_reset_reference(ctx):
@@ -423,6 +461,26 @@ class Simulation:
     def observables(self) -> np.ndarray:
         self._bind()
         return lb_get_observables(self.ctx)
+
+    def record_trajectory(self, stride: int, capacity: int):
+        """Record the unwrapped bead positions now and after every `stride` steps into a
+        device ring of `capacity` frames (a torch float64 tensor owned by this object)."""
+        import torch
+
+        self._bind()
+        self._traj = torch.empty((int(capacity), self.N, 3), dtype=torch.float64, device="cuda")
+        lb_record_trajectory(self.ctx, self._traj.data_ptr(), capacity, stride)
+
+    def trajectory(self):
+        """The recorded frames, oldest first, as a (T, N, 3) float64 CUDA tensor."""
+        import torch
+
+        self.sync()
+        n = lb_trajectory_frames(self.ctx)
+        cap = self._traj.shape[0]
+        if n <= cap:
+            return self._traj[:n]
+        return torch.roll(self._traj, -(n % cap), dims=0)
 
     def save(self, path: str):
         self._bind()

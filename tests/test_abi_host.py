@@ -89,3 +89,23 @@ def test_strerror_names_every_status(lblib):
     for code in range(8):
         assert lblib.lb_strerror(code) != "unknown status"
     assert lblib.lb_strerror(99) == "unknown status"
+
+
+def test_analysis_and_recording_validate_arguments(lblib):
+    """Argument checks run before any launch (no GPU needed)."""
+    for call in (lambda: lblib.lb_analysis_msd(None, 10, 4, 3, 1, 2, None, None),
+                 lambda: lblib.lb_analysis_msd(1, 10, 4, 3, 1, 4, 1, None),  # i1 out of range
+                 lambda: lblib.lb_analysis_rouse_modes(1, 10, 1, 1, 1, None),  # N < 2
+                 lambda: lblib.lb_analysis_rouse_modes(1, 10, 4, 4, 1, None),  # P > N-1
+                 lambda: lblib.lb_analysis_rouse_correlation(1, 10, 3, 70000, 1, None),
+                 lambda: lblib.lb_analysis_static_sk(1, 10, 4, None, 2, 1, None),
+                 lambda: lblib.lb_analysis_dynamic_sk(1, 10, 4, 1, 2, 3, 0, 1, None)):  # stride 0
+        with pytest.raises(lblib.LBError) as ei:
+            call()
+        assert ei.value.code == lblib.LB_ERR_ARG
+    ctx = lblib.lb_create(8, 1.0, 3.0, 3.0, 1.0, 0.01, 1.0, 1, lblib.LB_FP32)
+    with pytest.raises(lblib.LBError) as ei:  # no chain to record
+        lblib.lb_record_trajectory(ctx, 1, 4, 1)
+    assert ei.value.code == lblib.LB_ERR_STATE
+    assert lblib.lb_trajectory_frames(ctx) == 0
+    lblib.lb_destroy(ctx)
