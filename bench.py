@@ -314,6 +314,39 @@ def run_ours(args):
                  "hbm_frac": BYTES_PER_NODE["f32"] * nodes / (tb / kb) / 1e9 / measured_peaks()[0],
                  "workload": "64 replicas, L in {16,24,32,48,64}, N in {8,16,32,64}, FP32, graph-captured"}
 
+    # chain observables (Sec. III A/B) on a recorded trajectory: 1000 frames of the N=128
+    # chain in an L=32 box; each analysis kernel timed once after a warm-up call
+    observ = None
+    if not args.no_observables:
+        from paper_0903_5067_gb300 import analysis as an
+
+        so = lb.Simulation(L=32, seed=seed, precision=lb.LB_FP32, **PARAMS)
+        so.add_chain(N, x0=inputs.chain_walk(N, L=32, bond=0.97, seed=seed, self_avoiding=True), **CHAIN)
+        so.record_trajectory(stride=1, capacity=1000)
+        so.step(999)
+        traj = so.trajectory()
+        so.close()
+        T_o = traj.shape[0]
+        ks = [0.1 * (1.25 ** q) for q in range(16)]
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            a0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            return (time.perf_counter() - a0) * 1e3, r
+
+        t_msd, _ = timed(lambda: an.msd(traj, 500))
+        t_rouse, _ = timed(lambda: an.rouse_correlation(an.rouse_modes(traj), 500))
+        t_sk, _ = timed(lambda: an.static_sk(traj, ks))
+        t_skt, _ = timed(lambda: an.dynamic_sk(traj, ks[:4], 100, origin_stride=20))
+        observ = {"frames": T_o, "N": N, "msd_ms": t_msd, "rouse_ms": t_rouse, "static_sk_ms": t_sk,
+                  "dynamic_sk_ms": t_skt,
+                  "static_sk_pairs_per_s": len(ks) * T_o * N * (N - 1) / 2 / (t_sk / 1e3),
+                  "work": "g1/g2/g3 to lag 500; Rouse modes p=1..127 and correlation to lag 500; S(k) at 16 k; "
+                          "S(k,t) at 4 k, lags 0..100, origins every 20 frames; FP64, host-timed with sync"}
+
     value, tmax = aggregate_throughput(L ** 3 * args.steps / 1e6, t32, ws, dev)
     v64, _ = aggregate_throughput(L ** 3 * k64 / 1e6, t64, ws, dev)
 
@@ -368,6 +401,7 @@ def run_ours(args):
                        "fp32_over_fp64": value / v64},
         "bead_steps_per_s": N * args.steps * ws / tmax,
         "batch_c4": batch,
+        "observables_f3": observ,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "C ABI, pinned host buffers: set_populations, K x (step + get_beads), get_populations"},
         "gpu_launches": 2 * args.steps + 1,
@@ -388,6 +422,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-observables", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
