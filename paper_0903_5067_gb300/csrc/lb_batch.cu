@@ -5,9 +5,12 @@
 // L = 10..35 for the finite-size extrapolation, Sec. II E and Sec. III B; the CPU-cost study
 // sums three box sizes per chain length, Sec. III C).  Each replica owns an ordinary engine
 // (its memory, noise keys and chain); the batch drives them in lockstep:
-//   - k_batch_bead: one thread block per replica's chain (side stream, concurrent),
-//   - k_batch_lb: a tile table over all replicas' nodes, persistent thread blocks walking it,
-//   - k_batch_apply: the force corrections of every replica.
+//   - k_batch_bead: one thread block per replica's chain; it releases the LB kernel of the
+//     same step at its start (programmatic dependent launch, one stream),
+//   - k_batch_lb: a tile table over all replicas' nodes, persistent thread blocks walking it;
+//     tiles stamped by the previous step's bead kernel add its force corrections to what
+//     they pull, the bead kernel adds them to its gathers,
+//   - k_batch_apply: the last step's force corrections, once at the end of each call.
 // Step indices come from a device counter so that a captured CUDA graph of G steps (G even)
 // can be replayed; the tile size and the number of persistent blocks are chosen by a
 // measuring autotuner.
@@ -27,6 +30,7 @@ struct ReplicaK {
   S* pop[2];
   FluidK<R> P;
   ChainK<R> C;
+  PendK<R> pd[2];  // pending corrections of a step of parity j: writes slot j, reads slot j ^ 1
   unsigned long long nnodes;
   unsigned long long tile0;  // first global tile of this replica
   float invL;
@@ -57,11 +61,13 @@ __device__ __forceinline__ unsigned div_small(unsigned n, unsigned L, float invL
 // collision's coefficients stay instruction operands as in the single-box kernel.
 constexpr int kBatchGroup = 64;
 
-template <class S>
+template <class S, class R>
 struct BatchRep {
   S* pop[2];
   unsigned long long nnodes, tile0, plane;
+  unsigned seg0;  // first stamp segment of the replica
   unsigned long long* nonpos;
+  const R* p_dense[2];  // dense correction fields by slot
   unsigned L;
   float invL;
 };
@@ -71,41 +77,80 @@ struct BatchLB {
   FluidK<R> P;
   int nrep;
   unsigned long long total_tiles;
-  BatchRep<S> rep[kBatchGroup];
+  const int* flags[2];           // per 32-node segment: the step that last stamped it, by slot
+  unsigned long long* counter;   // this group's two tile counters (by step parity)
+  BatchRep<S, R> rep[kBatchGroup];
   RoundKeys rk[kBatchGroup];
 };
 
+// FP32: at most 42 registers (three 512-thread blocks per SM), as the single-box kernel; the
+// rare correction scatter would otherwise raise the whole kernel's register count
+// Tiles are taken from a per-group counter in chunks of kChunk (blocks that start late, e.g.
+// beside a bead block, simply take fewer); each block's tiles increase, so the replica search
+// only moves forward.  The counter of this step's parity was zeroed by the previous step's
+// bead kernel.
+constexpr unsigned kChunk = 2;
+
 template <class S, class R, bool DEV, bool NOISE>
-__global__ void __launch_bounds__(512) k_batch_lb(const __grid_constant__ BatchLB<S, R> B, int parity,
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 3 : 1) k_batch_lb(const __grid_constant__ BatchLB<S, R> B, int parity,
                                                    const uint32_t* __restrict__ d_step, uint32_t j) {
+  extern __shared__ __align__(16) unsigned char dsm[];  // staged corrections, 19 x T
+  __shared__ unsigned long long s_next;
   const uint32_t step = *d_step + j;
   const unsigned T = blockDim.x;
-  // contiguous chunk of tiles per block: consecutive tiles mostly share a replica
-  const unsigned long long per = (B.total_tiles + gridDim.x - 1) / gridDim.x;
-  const unsigned long long t_begin = blockIdx.x * per;
-  const unsigned long long t_end = t_begin + per < B.total_tiles ? t_begin + per : B.total_tiles;
+  const int pslot = parity ^ 1;  // the previous step's corrections
+  unsigned long long* ctr = B.counter + parity;
+  if (threadIdx.x == 0) s_next = atomicAdd(ctr, (unsigned long long)kChunk);
+  __syncthreads();
+  unsigned long long cur = s_next;
   int r = 0;
-  for (unsigned long long tile = t_begin; tile < t_end; ++tile) {
-    while (r + 1 < B.nrep && B.rep[r + 1].tile0 <= tile) ++r;  // uniform
-    const BatchRep<S>& rp = B.rep[r];
-    const unsigned long long node = (tile - rp.tile0) * T + threadIdx.x;
-    if (node < rp.nnodes) {
-      const unsigned L = rp.L;
-      unsigned x, y;
-      const unsigned t = div_small((unsigned)node, L, rp.invL, x);
-      const unsigned z = div_small(t, L, rp.invL, y);
-      lb_node_update<S, R, DEV, NOISE>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r], rp.nonpos,
-                                       step, x, y, z);
+  while (cur < B.total_tiles) {
+    __syncthreads();  // every thread has read s_next
+    if (threadIdx.x == 0) s_next = atomicAdd(ctr, (unsigned long long)kChunk);  // next chunk, early
+    const unsigned long long t_end = cur + kChunk < B.total_tiles ? cur + kChunk : B.total_tiles;
+    for (unsigned long long tile = cur; tile < t_end; ++tile) {
+      while (r + 1 < B.nrep && B.rep[r + 1].tile0 <= tile) ++r;  // uniform
+      const BatchRep<S, R>& rp = B.rep[r];
+      const unsigned long long n0 = (tile - rp.tile0) * T;
+      const unsigned long long node = n0 + threadIdx.x;
+      if (node < rp.nnodes) {
+        // a node of a segment stamped by the previous step adds that step's corrections to what
+        // it pulls (replicas without a chain have no correction field and are never stamped)
+        const bool stamped = rp.p_dense[pslot] != nullptr &&
+                             B.flags[pslot][rp.seg0 + ((unsigned)node >> kSegShift)] == (int)(step - 1u);
+        const unsigned L = rp.L;
+        unsigned x, y;
+        const unsigned t = div_small((unsigned)node, L, rp.invL, x);
+        const unsigned z = div_small(t, L, rp.invL, y);
+        if (stamped) {  // two inlined copies: the common one carries no correction code
+          R* col = reinterpret_cast<R*>(dsm) + threadIdx.x;
+          stage_corrections<R>(rp.p_dense[pslot], rp.plane, L, x, y, z, col, T);
+          lb_node_update<S, R, DEV, NOISE>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r],
+                                           rp.nonpos, step, x, y, z, col, T);
+        } else {
+          lb_node_update<S, R, DEV, NOISE>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r],
+                                           rp.nonpos, step, x, y, z);
+        }
+      }
     }
+    __syncthreads();
+    cur = s_next;
   }
 }
 
+// One 256-thread block per replica's chain: its registers (about 86 per thread) leave room
+// on its SM for a full complement of LB blocks.  Block 0 also zeroes the tile counters the
+// next step's LB launches will use.
 template <class S, class R, bool DEV>
-__global__ void __launch_bounds__(512) k_batch_bead(const ReplicaK<S, R>* __restrict__ reps, int parity,
-                                                     const uint32_t* __restrict__ d_step, uint32_t j) {
+__global__ void __launch_bounds__(256) k_batch_bead(const ReplicaK<S, R>* __restrict__ reps, int parity,
+                                                     const uint32_t* __restrict__ d_step, uint32_t j,
+                                                     unsigned long long* __restrict__ counters, int ngroups) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ FluidK<R> sP;
   __shared__ ChainK<R> sC;
+  allow_dependent_launch();
+  if (blockIdx.x == 0)
+    for (int g = threadIdx.x; g < ngroups; g += blockDim.x) counters[2 * g + (parity ^ 1)] = 0ull;
   const ReplicaK<S, R>& rp = reps[blockIdx.x];
   if (!rp.has_chain) return;
   {
@@ -117,18 +162,35 @@ __global__ void __launch_bounds__(512) k_batch_bead(const ReplicaK<S, R>* __rest
     for (unsigned w = threadIdx.x; w < sizeof(ChainK<R>) / 4; w += blockDim.x) d[w] = c[w];
   }
   __syncthreads();
-  bead_step_block<S, R, DEV>(rp.pop[parity], sP, sC, pend_complete(sC), *d_step + j, smem);
+  const uint32_t step = *d_step + j;
+  PendK<R> Pd = rp.pd[parity];
+  Pd.have_prev = 1;  // an empty list after a flush
+  Pd.cur_stamp = (int)step;
+  Pd.prev_stamp = (int)(step - 1u);
+  bead_step_block<S, R, DEV>(rp.pop[parity], sP, sC, Pd, step, smem);
 }
 
+// zero the counts of one pending slot of every replica (after the flush applied it)
 template <class S, class R>
-__global__ void __launch_bounds__(256) k_batch_apply(const ReplicaK<S, R>* __restrict__ reps, int parity) {
+__global__ void k_batch_clear(const ReplicaK<S, R>* __restrict__ reps, int nrep, int slot) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrep; r += gridDim.x * blockDim.x)
+    if (reps[r].has_chain) *reps[r].pd[slot].cur_count = 0;
+}
+
+// B[i][node] += dn_i for the pending list of `slot` of every replica, into buffer `buf`, and
+// those entries of the dense correction field back to zero
+template <class S, class R>
+__global__ void __launch_bounds__(256) k_batch_apply(const ReplicaK<S, R>* __restrict__ reps, int buf, int slot) {
   const ReplicaK<S, R>& rp = reps[blockIdx.z];
   if (!rp.has_chain) return;
+  const PendK<R>& pd = rp.pd[slot];
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= *rp.C.p_count) return;
+  if (u >= *pd.cur_count) return;
   const int i = blockIdx.y;
-  S* p = rp.pop[parity ^ 1] + (unsigned long long)i * rp.P.plane + (unsigned)rp.C.p_pos[u].x;
-  st<S, R>(p, ld<S, R>(p) + rp.C.p_dn[i * rp.C.cap + u]);
+  const unsigned long long off = (unsigned long long)i * rp.P.plane + (unsigned)pd.cur_pos[u].x;
+  S* p = rp.pop[buf] + off;
+  st<S, R>(p, ld<S, R>(p) + pd.cur_dn[i * pd.cap + u]);
+  pd.cur_dense[off] = R(0);
 }
 
 class Batch {
@@ -154,6 +216,15 @@ class BatchT final : public Batch {
       offs_.push_back(off);
       off += e->workspace_bytes();
     }
+    // stamps: one int per 32-node segment of every replica, two slots
+    max_segs_ = 0;
+    for (auto& e : eng_) max_segs_ += (e->nodes() + 31) >> kSegShift;
+    off = align_up(off, 256);
+    flags_off_ = off;
+    off += 2 * max_segs_ * sizeof(int);
+    off = align_up(off, 256);
+    counters_off_ = off;
+    off += 2 * (cfgs.size() / kBatchGroup + 1) * sizeof(unsigned long long);
     off = align_up(off, 256);
     table_off_ = off;
     off += cfgs.size() * sizeof(ReplicaK<S, R>);
@@ -164,10 +235,7 @@ class BatchT final : public Batch {
   }
   ~BatchT() override {
     if (graph_exec_) cudaGraphExecDestroy(graph_exec_);
-    if (side_) cudaStreamDestroy(side_);
     if (cap_) cudaStreamDestroy(cap_);
-    if (ev_ready_) cudaEventDestroy(ev_ready_);
-    if (ev_bead_) cudaEventDestroy(ev_bead_);
   }
 
   size_t workspace_bytes() const override { return bytes_; }
@@ -176,6 +244,9 @@ class BatchT final : public Batch {
     base_ = static_cast<unsigned char*>(base);
     for (size_t r = 0; r < eng_.size(); ++r) eng_[r]->bind(base_ + offs_[r]);
     d_reps_ = reinterpret_cast<ReplicaK<S, R>*>(base_ + table_off_);
+    flags_[0] = reinterpret_cast<int*>(base_ + flags_off_);
+    flags_[1] = flags_[0] + max_segs_;
+    counters_ = reinterpret_cast<unsigned long long*>(base_ + counters_off_);
     d_step_ = reinterpret_cast<uint32_t*>(base_ + step_off_);
   }
 
@@ -191,6 +262,19 @@ class BatchT final : public Batch {
                  "batch bead shared memory");
     cap_max_ = 8;
     for (auto& e : eng_) cap_max_ = e->pending_capacity() > cap_max_ ? e->pending_capacity() : cap_max_;
+    // the engines zeroed their pending counts; no tile carries a stamp a step can match
+    cuda_check(cudaMemsetAsync(flags_[0], 0xfe, 2 * max_segs_ * sizeof(int), s), "memset stamps");
+    const size_t lbsm = (size_t)Q * 512 * sizeof(R);
+    if (lbsm > 48 * 1024) {  // FP64: staged corrections of a 512-node run
+      cuda_check(cudaFuncSetAttribute(k_batch_lb<S, R, DEV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)lbsm),
+                 "batch LB shared memory");
+      cuda_check(cudaFuncSetAttribute(k_batch_lb<S, R, DEV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)lbsm),
+                 "batch LB shared memory");
+    }
+    cuda_check(cudaMemsetAsync(counters_, 0, 2 * (eng_.size() / kBatchGroup + 1) * sizeof(unsigned long long), s),
+               "memset tile counters");
     upload_table(s);
     drop_graph();
   }
@@ -220,6 +304,7 @@ class BatchT final : public Batch {
       k_add_step<<<1, 1, 0, s>>>(d_step_, (uint32_t)(n - done));
       cuda_check(cudaGetLastError(), "advance step");
     }
+    flush(s);
   }
 
   void autotune(cudaStream_t s, int* best_threads, int* best_bps) override {
@@ -238,11 +323,14 @@ class BatchT final : public Batch {
       for (int b : cand_b) {
         if (b > 0 && b * t > 2048) continue;
         set_shape(t, b);
+        // fresh stamps for every trial (the step counter restarts at 0)
+        cuda_check(cudaMemsetAsync(flags_[0], 0xfe, 2 * max_segs_ * sizeof(int), s), "memset stamps");
         upload_table(s);
         k_set_step<<<1, 1, 0, s>>>(d_step_, 0);
         for (int w = 0; w < 2; ++w) launch_step(s, 0, true);
         cuda_check(cudaEventRecord(e0, s), "event");
         for (int w = 0; w < 6; ++w) launch_step(s, 0, true);
+        flush(s);
         cuda_check(cudaEventRecord(e1, s), "event");
         cuda_check(cudaEventSynchronize(e1), "event sync");
         float ms = 0;
@@ -267,13 +355,20 @@ class BatchT final : public Batch {
   static constexpr int kGraph = 16;
 
   void ensure_streams() {
-    if (side_) return;
-    int least = 0, greatest = 0;
-    cuda_check(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
-    cuda_check(cudaStreamCreateWithPriority(&side_, cudaStreamNonBlocking, greatest), "side stream");
+    if (cap_) return;
     cuda_check(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking), "capture stream");
-    cuda_check(cudaEventCreateWithFlags(&ev_ready_, cudaEventDisableTiming), "event");
-    cuda_check(cudaEventCreateWithFlags(&ev_bead_, cudaEventDisableTiming), "event");
+  }
+
+  // apply the last step's corrections (slot = parity of that step) to the current buffer and
+  // empty that slot, so the next call's first step finds nothing pending
+  void flush(cudaStream_t s) {
+    const int par = eng_[0]->parity();
+    const int slot = par ^ 1;
+    const int R_ = (int)eng_.size();
+    k_batch_apply<S, R><<<dim3((cap_max_ + 255) / 256, Q, R_), 256, 0, s>>>(d_reps_, par, slot);
+    cuda_check(cudaGetLastError(), "batch apply");
+    k_batch_clear<S, R><<<1, 256, 0, s>>>(d_reps_, R_, slot);
+    cuda_check(cudaGetLastError(), "batch clear");
   }
 
   void drop_graph() {
@@ -283,7 +378,7 @@ class BatchT final : public Batch {
 
   void upload_table(cudaStream_t s) {
     std::vector<ReplicaK<S, R>> tab(eng_.size());
-    unsigned long long t = 0;
+    unsigned long long t = 0, segs = 0;
     for (size_t r = 0; r < eng_.size(); ++r) {
       ReplicaK<S, R>& q = tab[r];
       memset(&q, 0, sizeof(q));
@@ -295,6 +390,20 @@ class BatchT final : public Batch {
       q.tile0 = t;
       q.invL = 1.0f / (float)q.P.L;
       q.has_chain = eng_[r]->chain_length() > 0;
+      for (int jj = 0; jj < 2; ++jj) {
+        PendK<R>& pd = q.pd[jj];
+        pd.prev_flags = flags_[jj ^ 1];
+        pd.prev_dense = eng_[r]->pending_dense(jj ^ 1);
+        pd.cur_dense = eng_[r]->pending_dense(jj);
+        pd.plane = eng_[r]->plane();
+        pd.cur_pos = eng_[r]->pending_pos(jj);
+        pd.cur_dn = eng_[r]->pending_dn(jj);
+        pd.cur_count = eng_[r]->pending_count(jj);
+        pd.cur_flags = flags_[jj];
+        pd.cap = eng_[r]->pending_capacity();
+        pd.seg0 = (unsigned)segs;
+      }
+      segs += (q.nnodes + 31) >> kSegShift;
       noise_ = q.P.ncalls > 0;
       t += (q.nnodes + threads_ - 1) / threads_;
     }
@@ -307,8 +416,11 @@ class BatchT final : public Batch {
       unsigned long long tt = 0;
       const size_t g1 = g0 + kBatchGroup < eng_.size() ? g0 + kBatchGroup : eng_.size();
       G.nrep = (int)(g1 - g0);
+      G.flags[0] = flags_[0];
+      G.flags[1] = flags_[1];
+      G.counter = counters_ + 2 * groups_.size();
       for (size_t r = g0; r < g1; ++r) {
-        BatchRep<S>& q = G.rep[r - g0];
+        BatchRep<S, R>& q = G.rep[r - g0];
         q.pop[0] = tab[r].pop[0];
         q.pop[1] = tab[r].pop[1];
         q.nnodes = tab[r].nnodes;
@@ -317,6 +429,8 @@ class BatchT final : public Batch {
         q.nonpos = tab[r].P.nonpos;
         q.L = tab[r].P.L;
         q.invL = tab[r].invL;
+        q.seg0 = tab[r].pd[0].seg0;
+        for (int jj = 0; jj < 2; ++jj) q.p_dense[jj] = eng_[r]->pending_dense(jj);
         G.rk[r - g0] = tab[r].P.rk;
         tt += (q.nnodes + threads_ - 1) / threads_;
       }
@@ -329,30 +443,40 @@ class BatchT final : public Batch {
     table_threads_ = threads_;
   }
 
-  // one lockstep step; kernels read step = *d_step + j (advance: bump the counter after)
+  // one lockstep step; kernels read step = *d_step + j (advance: bump the counter after).
+  // The bead kernel releases the first LB launch at its start; the next step's bead kernel,
+  // an ordinary launch, waits for both.  The force corrections stay pending (see k_batch_lb).
   void launch_step(cudaStream_t s, uint32_t j, bool advance) {
     const int par = eng_[0]->parity();
     const int R_ = (int)eng_.size();
-    cuda_check(cudaEventRecord(ev_ready_, s), "record ready");
-    cuda_check(cudaStreamWaitEvent(side_, ev_ready_, 0), "wait ready");
-    k_batch_bead<S, R, DEV><<<R_, 512, smem_, side_>>>(d_reps_, par, d_step_, j);
+    k_batch_bead<S, R, DEV><<<R_, 256, smem_, s>>>(d_reps_, par, d_step_, j, counters_, (int)groups_.size());
     cuda_check(cudaGetLastError(), "batch bead");
-    cuda_check(cudaEventRecord(ev_bead_, side_), "record bead");
     int dev = 0, sms = 0;
     cuda_check(cudaGetDevice(&dev), "device");
     cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    bool first = true;
     for (const BatchLB<S, R>& G : groups_) {
       unsigned grid = (unsigned)G.total_tiles;
       if (bps_ > 0 && (unsigned long long)sms * bps_ < G.total_tiles) grid = (unsigned)(sms * bps_);
+      cudaLaunchConfig_t lc;
+      memset(&lc, 0, sizeof(lc));
+      lc.gridDim = dim3(grid);
+      lc.blockDim = dim3(threads_);
+      lc.dynamicSmemBytes = (size_t)Q * threads_ * sizeof(R);
+      lc.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[0].val.programmaticStreamSerializationAllowed = 1;
+      lc.attrs = at;
+      lc.numAttrs = first ? 1 : 0;
       if (noise_)
-        k_batch_lb<S, R, DEV, true><<<grid, threads_, 0, s>>>(G, par, d_step_, j);
+        cuda_check(cudaLaunchKernelEx(&lc, k_batch_lb<S, R, DEV, true>, G, par, (const uint32_t*)d_step_, j),
+                   "batch LB");
       else
-        k_batch_lb<S, R, DEV, false><<<grid, threads_, 0, s>>>(G, par, d_step_, j);
-      cuda_check(cudaGetLastError(), "batch LB");
+        cuda_check(cudaLaunchKernelEx(&lc, k_batch_lb<S, R, DEV, false>, G, par, (const uint32_t*)d_step_, j),
+                   "batch LB");
+      first = false;
     }
-    cuda_check(cudaStreamWaitEvent(s, ev_bead_, 0), "wait bead");
-    k_batch_apply<S, R><<<dim3((cap_max_ + 255) / 256, Q, R_), 256, 0, s>>>(d_reps_, par);
-    cuda_check(cudaGetLastError(), "batch apply");
     if (advance) k_add_step<<<1, 1, 0, s>>>(d_step_, 1);
     for (auto& e : eng_) e->flip();
   }
@@ -375,15 +499,17 @@ class BatchT final : public Batch {
   std::vector<BatchLB<S, R>> groups_;
   std::vector<std::vector<double>> x0_;
   std::vector<size_t> offs_;
-  size_t table_off_ = 0, step_off_ = 0, bytes_ = 0, smem_ = 0;
+  size_t table_off_ = 0, step_off_ = 0, flags_off_ = 0, counters_off_ = 0, bytes_ = 0, smem_ = 0;
+  unsigned long long* counters_ = nullptr;
+  size_t max_segs_ = 0;
+  int* flags_[2] = {nullptr, nullptr};
   unsigned char* base_ = nullptr;
   ReplicaK<S, R>* d_reps_ = nullptr;
   uint32_t* d_step_ = nullptr;
   unsigned long long total_tiles_ = 0;
   int threads_ = 256, bps_ = 0, table_threads_ = -1, cap_max_ = 8;
   bool noise_ = true;
-  cudaStream_t side_ = nullptr, cap_ = nullptr;
-  cudaEvent_t ev_ready_ = nullptr, ev_bead_ = nullptr;
+  cudaStream_t cap_ = nullptr;
   cudaGraphExec_t graph_exec_ = nullptr;
 };
 

@@ -110,38 +110,32 @@ struct ChainK {
   unsigned* status;
 };
 
-// Force corrections in flight between consecutive steps of a multi-step run: the bead kernel
-// of step k writes them (with the LB tiles whose pulls read a corrected node stamped k); the
-// LB kernel of step k+1 adds them to the populations it pulls from stamped tiles, and the bead
-// kernel of step k+1 to the populations it gathers.  One flush applies the last step's.
+// Force corrections in flight between consecutive steps of a multi-step run.  The bead kernel
+// of step k writes them twice: as a list (node, 19 deltas) for the final flush, and into a
+// dense correction field of the population layout [i][plane] that is zero except at pending
+// nodes; it also stamps every segment of 32 consecutive nodes (linear index / 32) holding a
+// node that pulls from a corrected node.  The LB kernel of step k+1 adds the dense field to
+// what it pulls at the nodes of stamped segments, and the bead kernel of step k+1 to what it
+// gathers.  Two slots alternate by step; a bead kernel first clears its slot's
+// entries from two steps before (its old list), and a flush clears the entries it applies.
 template <class R>
 struct PendK {
-  int have_prev;  // 0: the stored populations are complete (first step of a run)
+  int have_prev;          // 0: nothing pending (the stored populations are complete)
   int prev_stamp;
-  const int4* prev_pos;
-  const R* prev_dn;
-  const int* prev_count;
-  const int* prev_flags;
-  int4* cur_pos;
-  R* cur_dn;
+  const int* prev_flags;  // per LB tile: the step that last stamped it
+  const R* prev_dense;    // the previous step's corrections, dense
+  int4* cur_pos;          // this step's list: {node, x, y, z}
+  R* cur_dn;              // 19 deltas [i][cap]
   int* cur_count;
-  int* cur_flags;  // nullptr: do not stamp tiles
+  R* cur_dense;           // this step's slot of the dense field
+  int* cur_flags;         // nullptr: do not stamp
   int cur_stamp;
   int cap;
-  unsigned bx, by, tiles_x, tiles_y;  // LB kernel tile geometry
+  unsigned long long plane;  // element stride between the 19 planes
+  unsigned seg0;             // index of this box's first segment in the stamp arrays
 };
 
-// pending block of a complete step: no previous corrections, the new ones into the chain's
-// own list, no stamps
-template <class R>
-__host__ __device__ inline PendK<R> pend_complete(const ChainK<R>& C) {
-  PendK<R> Pd{};
-  Pd.cur_pos = C.p_pos;
-  Pd.cur_dn = C.p_dn;
-  Pd.cur_count = C.p_count;
-  Pd.cap = C.cap;
-  return Pd;
-}
+constexpr int kSegShift = 5;  // stamp segments of 32 consecutive nodes
 
 // ---------------------------------------------------------------------------------------
 // moment algebra
@@ -377,7 +371,7 @@ __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __r
     const unsigned idx = sxs[cx(i) + 1] + ry[cy(i) + 1] + rz[cz(i) + 1];
     n[i] = ld<S, R>(src + (unsigned long long)i * plane + idx);
   }
-  if (dcol) {  // previous step's force corrections at the pulled nodes (stamped tiles only)
+  if (dcol) {  // the previous step's corrections at the pulled nodes, staged by the caller
 #pragma unroll
     for (int i = 0; i < Q; ++i) n[i] += dcol[i * dstride];
   }
@@ -462,53 +456,56 @@ __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __r
   for (int i = 0; i < Q; ++i) st<S, R>(dst + (unsigned long long)i * plane + node, out[i]);
 }
 
+// Stage the previous step's corrections at the 19 pull sources of node (x, y, z) into
+// col[i * stride] (shared memory).  A rolled loop with the directions unpacked from constants
+// (this rare path must not raise the register count of the LB kernels), issuing asynchronous
+// global-to-shared copies (cp.async) so that the 19 loads are in flight together; the
+// calling thread waits for its own copies.
+template <class R>
+__device__ __forceinline__ void stage_corrections(const R* __restrict__ corr, unsigned long long plane, unsigned L,
+                                                  unsigned x, unsigned y, unsigned z, R* col, unsigned stride) {
+  static_assert(sizeof(R) == 4 || sizeof(R) == 8, "cp.async copies 4 or 8 bytes");
+  constexpr unsigned long long PX = pack_component(0), PY = pack_component(1), PZ = pack_component(2);
+#pragma unroll 1
+  for (int i = 0; i < Q; ++i) {
+    int sx = (int)x - unpack_component(PX, i), sy = (int)y - unpack_component(PY, i),
+        sz = (int)z - unpack_component(PZ, i);
+    sx = sx < 0 ? sx + (int)L : (sx >= (int)L ? sx - (int)L : sx);
+    sy = sy < 0 ? sy + (int)L : (sy >= (int)L ? sy - (int)L : sy);
+    sz = sz < 0 ? sz + (int)L : (sz >= (int)L ? sz - (int)L : sz);
+    const unsigned idx = (unsigned)sx + L * ((unsigned)sy + L * (unsigned)sz);
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(col + i * stride);
+    const R* src = corr + (unsigned long long)i * plane + idx;
+    if (sizeof(R) == 4)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // One LB tile: pull-stream + collide for the (blockDim.x x blockDim.y) nodes at
-// (tx, ty, z) (Sec. II B, Eq. 3).  In a tile stamped by the previous deferred step, that
-// step's force corrections are first scattered into a shared table D[i][thread] (each (i,
-// node) pair has at most one source node) and added to the pulled populations.  Shared
-// memory: 19 x blockDim.x x blockDim.y x sizeof(R) when Pd.have_prev.
+// (tx, ty, z) (Sec. II B, Eq. 3).  A node in a segment stamped by the previous deferred step
+// adds that step's corrections to the populations it pulls (staged per thread in shared
+// memory, 19 x blockDim.x x blockDim.y values).
 template <class S, class R, bool DEV, bool NOISE>
 __device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
                                         const PendK<R>& Pd, const uint32_t step, unsigned tx, unsigned ty,
-                                        unsigned z, unsigned tile, unsigned char* lsm) {
+                                        unsigned z, R* stage) {
   const unsigned L = P.L;
-  const unsigned bx = blockDim.x, by = blockDim.y;
-  const unsigned x = tx * bx + threadIdx.x;
-  const unsigned y = ty * by + threadIdx.y;
-  const unsigned T = bx * by;
-  const unsigned tid = threadIdx.x + bx * threadIdx.y;
-  R* D = nullptr;
-  if (Pd.have_prev && Pd.prev_flags[tile] == Pd.prev_stamp) {  // uniform over the block
-    D = reinterpret_cast<R*>(lsm);
-    for (unsigned j = tid; j < Q * T; j += T) D[j] = R(0);
-    __syncthreads();
-    const int cnt = *Pd.prev_count;
-    const int iL = (int)L;
-    const int x0 = (int)(tx * bx), y0 = (int)(ty * by), z0 = (int)z;
-    constexpr unsigned long long PX = pack_component(0), PY = pack_component(1), PZ = pack_component(2);
-    for (int u = (int)tid; u < cnt; u += (int)T) {
-      const int4 p = Pd.prev_pos[u];
-      // corrected node within one link of the tile (periodic)?
-      if ((p.w - z0 + 1 + iL) % iL > 2) continue;
-      if ((p.z - y0 + 1 + iL) % iL > (int)by + 1) continue;
-      if ((p.y - x0 + 1 + iL) % iL > (int)bx + 1) continue;
-      // a rolled loop keeps this rare path from raising the register count of the kernel
-#pragma unroll 1
-      for (int i = 0; i < Q; ++i) {
-        int rx = p.y + unpack_component(PX, i), ry = p.z + unpack_component(PY, i), rz = p.w + unpack_component(PZ, i);
-        rx = rx < 0 ? rx + iL : (rx >= iL ? rx - iL : rx);
-        ry = ry < 0 ? ry + iL : (ry >= iL ? ry - iL : ry);
-        rz = rz < 0 ? rz + iL : (rz >= iL ? rz - iL : rz);
-        const int lx = rx - x0, ly = ry - y0;
-        if (rz == z0 && lx >= 0 && lx < (int)bx && ly >= 0 && ly < (int)by)
-          D[i * T + ly * bx + lx] = Pd.prev_dn[i * Pd.cap + u];
-      }
-    }
-    __syncthreads();
-  }
+  const unsigned x = tx * blockDim.x + threadIdx.x;
+  const unsigned y = ty * blockDim.y + threadIdx.y;
   if (x >= L || y >= L) return;
-  lb_node_update<S, R, DEV, NOISE>(src, dst, P, P.L, P.plane, P.rk, P.nonpos, step, x, y, z,
-                                   D ? D + tid : nullptr, T);
+  const unsigned node = x + L * (y + L * z);
+  // two inlined copies of the update: the common one carries no correction code (one shared
+  // copy with a runtime branch measured 6 % slower)
+  if (Pd.have_prev && Pd.prev_flags[Pd.seg0 + (node >> kSegShift)] == Pd.prev_stamp) {
+    const unsigned T = blockDim.x * blockDim.y, tid = threadIdx.x + blockDim.x * threadIdx.y;
+    stage_corrections<R>(Pd.prev_dense, Pd.plane, L, x, y, z, stage + tid, T);
+    lb_node_update<S, R, DEV, NOISE>(src, dst, P, P.L, P.plane, P.rk, P.nonpos, step, x, y, z, stage + tid, T);
+  } else {
+    lb_node_update<S, R, DEV, NOISE>(src, dst, P, P.L, P.plane, P.rk, P.nonpos, step, x, y, z);
+  }
 }
 
 // LB kernel: 3D grid of (x-row segments) x (y rows) x z planes
@@ -516,8 +513,7 @@ template <class S, class R, bool DEV, bool NOISE>
 __global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* __restrict__ dst,
                                                   const FluidK<R> P, const PendK<R> Pd, const uint32_t step) {
   extern __shared__ __align__(16) unsigned char lsm[];
-  const unsigned tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  lb_tile<S, R, DEV, NOISE>(src, dst, P, Pd, step, blockIdx.x, blockIdx.y, blockIdx.z, tile, lsm);
+  lb_tile<S, R, DEV, NOISE>(src, dst, P, Pd, step, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<R*>(lsm));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -607,6 +603,21 @@ __device__ __forceinline__ void chain_forces_block(const R* __restrict__ sh, con
   }
 }
 
+constexpr int kGroupHashMax = 1024;  // entries grouped by hash table (else sorted)
+
+// Hash of a lattice node index onto a power-of-two table: the "lowbias32" integer finaliser
+// (xor-shift-multiply constants from C. Wellons' hash prospector).  Lattice neighbours differ
+// in few, structured bits, which a plain multiplicative hash maps to clustered low bits.
+__device__ __forceinline__ unsigned hash_node(int node, unsigned mask) {
+  unsigned h = (unsigned)node;
+  h ^= h >> 16;
+  h *= 0x7feb352du;
+  h ^= h >> 15;
+  h *= 0x846ca68bu;
+  h ^= h >> 16;
+  return h & mask;
+}
+
 // Bitonic sort (ascending) of M keys in shared memory, M a power of two >= 32, by a block of
 // nt threads (a multiple of 32).  Compare-exchange distances j >= 32 go through shared memory
 // with a barrier each; the distances j < 32 of every stage run in registers, each warp
@@ -644,59 +655,16 @@ __device__ __forceinline__ void bitonic_sort_block(unsigned long long* keys, int
   }
 }
 
-// open-addressing hash (node -> slot) of the previous step's corrected nodes, in shared
-// memory; probes are bounded by the table size
-__device__ __forceinline__ unsigned hash_node(int node, unsigned mask) {
-  // integer finaliser (xor-shift-multiply, the "lowbias32" constants of C. Wellons' hash
-  // prospector): lattice neighbours differ in few, structured
-  // bits, which a plain multiplicative hash would map to clustered low bits
-  unsigned h = (unsigned)node;
-  h ^= h >> 16;
-  h *= 0x7feb352du;
-  h ^= h >> 15;
-  h *= 0x846ca68bu;
-  h ^= h >> 16;
-  return h & mask;
-}
-// The first four probes are unrolled and branch-free (a data-dependent loop per lookup is
-// very slow in a warp); a lookup still unresolved after them continues in a bounded loop.
-__device__ __forceinline__ int hash_find(const int* __restrict__ hk, const int* __restrict__ hv, unsigned mask,
-                                         int node) {
-  const unsigned h = hash_node(node, mask);
-  int slot = -1;
-  bool stop = false;
-#pragma unroll
-  for (unsigned it = 0; it < 4; ++it) {
-    const unsigned hh = (h + it) & mask;
-    const int k = hk[hh];
-    slot = (!stop && k == node) ? (int)hh : slot;
-    stop = stop || k == node || k < 0;
-  }
-  if (!stop) {
-    for (unsigned it = 4; it <= mask; ++it) {
-      const unsigned hh = (h + it) & mask;
-      const int k = hk[hh];
-      if (k == node) {
-        slot = (int)hh;
-        break;
-      }
-      if (k < 0) break;
-    }
-  }
-  return slot >= 0 ? hv[slot] : -1;
-}
-
-// post-stream populations at node (qx,qy,qz): rho and lattice momentum; with a hash of the
-// previous step's corrections (hmask != 0), the corrections of the pulled nodes are included
+// post-stream populations at node (qx,qy,qz): rho and lattice momentum; with the dense field
+// of the previous step's corrections (corr != nullptr) added to the pulled populations
 template <class S, class R, bool DEV>
 __device__ __forceinline__ void gather_node_c(const S* __restrict__ pop, const FluidK<R>& P, int qx, int qy,
-                                              int qz, R mom[4], const int* hk, const int* hv, unsigned hmask,
-                                              const R* __restrict__ pdn, int cap) {
+                                              int qz, R mom[4], const R* __restrict__ corr) {
   const int L = (int)P.L;
   unsigned idx[Q];
   R v[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {  // all 19 loads in flight before any lookup
+  for (int i = 0; i < Q; ++i) {
     int sx = qx - cx(i), sy = qy - cy(i), sz = qz - cz(i);
     sx = sx < 0 ? sx + L : (sx >= L ? sx - L : sx);
     sy = sy < 0 ? sy + L : (sy >= L ? sy - L : sy);
@@ -704,17 +672,9 @@ __device__ __forceinline__ void gather_node_c(const S* __restrict__ pop, const F
     idx[i] = (unsigned)sx + (unsigned)L * ((unsigned)sy + (unsigned)L * (unsigned)sz);
     v[i] = ld<S, R>(pop + (unsigned long long)i * P.plane + idx[i]);
   }
-  if (hmask) {
-    // lookups first, then every correction load unconditionally (slot 0 stands in for a
-    // missing node and is multiplied by zero), so the loads overlap
-    int u[Q];
+  if (corr) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) u[i] = hash_find(hk, hv, hmask, (int)idx[i]);
-    R d[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = pdn[i * cap + (u[i] >= 0 ? u[i] : 0)];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) v[i] += u[i] >= 0 ? d[i] : R(0);
+    for (int i = 0; i < Q; ++i) v[i] += corr[(unsigned long long)i * P.plane + idx[i]];
   }
   R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
@@ -755,10 +715,70 @@ __device__ __forceinline__ void gather_node(const S* __restrict__ pop, const Flu
   mom[3] = jz;
 }
 
+// The pending correction of one node (the coupling of Sec. II B, spread back to the fluid): the sum
+// of its entries' reactions in entry order (ent(base) .. ent(base + cnt - 1) ascending),
+// turned into population corrections at pending-list index u, written to the list and the
+// dense field, and the LB tiles pulling from the node stamped.
+template <class R, class Ent>
+__device__ __forceinline__ void node_correction(const FluidK<R>& P, const ChainK<R>& C, const PendK<R>& Pd, int L,
+                                                int N, int u, int node, Ent ent, int base, int cnt) {
+  const int e0 = ent(base);
+  R f[3] = {R(0), R(0), R(0)};
+  for (int r = base; r < base + cnt; ++r) {
+    const int e = ent(r);
+    const R w = C.e_w[e] * C.spread;
+    const int sub = e / (8 * N), b = (e - sub * 8 * N) >> 3;
+    const R* fch = C.fc_hist + sub * 3 * N;
+    f[0] -= w * fch[3 * b + 0] * C.inv_a3;
+    f[1] -= w * fch[3 * b + 1] * C.inv_a3;
+    f[2] -= w * fch[3 * b + 2] * C.inv_a3;
+  }
+  const R rho = C.e_mom[e0], jx = C.e_mom[C.cap + e0], jy = C.e_mom[2 * C.cap + e0],
+          jz = C.e_mom[3 * C.cap + e0];
+  R dJ[3] = {f[0] * C.dJ_scale, f[1] * C.dJ_scale, f[2] * C.dJ_scale};
+  R dm[10];
+  if (P.body_on) {
+    // the LB kernel applies the body-force correction on every node; here add the
+    // difference between the correction for the total force and the body-only one
+    R dmb[10];
+    force_moments(rho, jx, jy, jz, P.body_dJ[0], P.body_dJ[1], P.body_dJ[2], P.gs, P.gb, dmb);
+    force_moments(rho, jx, jy, jz, dJ[0] + P.body_dJ[0], dJ[1] + P.body_dJ[1], dJ[2] + P.body_dJ[2],
+                  P.gs, P.gb, dm);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) dm[k] -= dmb[k];
+  } else {
+    force_moments(rho, jx, jy, jz, dJ[0], dJ[1], dJ[2], P.gs, P.gb, dm);
+  }
+  R dn[Q];
+  dmoments_to_dpops(dm, dn);
+  const int pz = node / (L * L), py = (node / L) % L, px = node % L;
+  Pd.cur_pos[u] = make_int4(node, px, py, pz);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    Pd.cur_dn[q * Pd.cap + u] = dn[q];
+    Pd.cur_dense[(unsigned long long)q * Pd.plane + (unsigned)node] = dn[q];
+  }
+  if (Pd.cur_flags) {  // stamp the segments of the nodes that pull from this node
+    // neighbour coordinates [c + 1] for c = -1, 0, +1 (periodic)
+    const int xs[3] = {px ? px - 1 : L - 1, px, px + 1 < L ? px + 1 : 0};
+    const int ys[3] = {py ? py - 1 : L - 1, py, py + 1 < L ? py + 1 : 0};
+    const int zs[3] = {pz ? pz - 1 : L - 1, pz, pz + 1 < L ? pz + 1 : 0};
+    unsigned last = 0xffffffffu;  // skip repeats of the segment just stamped
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const unsigned idx = (unsigned)xs[cx(q) + 1] + (unsigned)L * ((unsigned)ys[cy(q) + 1] + (unsigned)L * (unsigned)zs[cz(q) + 1]);
+      const unsigned seg = Pd.seg0 + (idx >> kSegShift);
+      if (seg != last) Pd.cur_flags[seg] = Pd.cur_stamp;
+      last = seg;
+    }
+  }
+}
+
 // One coupled bead step for one chain, run by one thread block (any size, multiple of 32):
 // velocity Verlet, FENE/WCA, interpolation of the post-stream flow at the 8 corners, friction
 // + Langevin force, and the deterministic spreading of the reaction into a list of
-// per-node population corrections.  `smem` holds max(6N R, sort keys) bytes.
+// per-node population corrections.  `smem` holds the positions (6N R), later the node
+// grouping table (or the sort keys), as sized by the host.
 template <class S, class R, bool DEV>
 __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const FluidK<R>& P, const ChainK<R>& C,
                                                 const PendK<R>& Pd, const uint32_t step, unsigned char* smem) {
@@ -768,32 +788,17 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
   const R h = C.h;
   R* sx = reinterpret_cast<R*>(smem);
   R* sl = sx + 3 * N;
-  // hash of the previous step's corrections (table after the positions, 16-byte aligned)
-  unsigned hmask = 0;
-  int* hk = reinterpret_cast<int*>(smem + ((6 * N * sizeof(R) + 15) & ~(size_t)15));
-  int* hv = nullptr;
-  if (Pd.have_prev) {
-    const int cnt = *Pd.prev_count;
-    unsigned H = 1;
-    while (H < 2u * (unsigned)(cnt > 0 ? cnt : 1)) H <<= 1;
-    hmask = H - 1;
-    hv = hk + H;
-    for (unsigned j = tid; j < H; j += nt) hk[j] = -1;
-    __syncthreads();
-    for (int u = tid; u < cnt; u += nt) {
-      const int node = Pd.prev_pos[u].x;
-      unsigned hh = hash_node(node, hmask);
-      for (unsigned it = 0; it <= hmask; ++it) {
-        const int old = atomicCAS(&hk[hh], -1, node);
-        if (old == -1 || old == node) {
-          hv[hh] = u;
-          break;
-        }
-        hh = (hh + 1) & hmask;
-      }
+  // clear this slot's dense entries of its old list (two steps back, or already applied);
+  // the new list overwrites the old one only in phase 5, after several barriers
+  {
+    const int old = *Pd.cur_count;
+    for (int u = tid; u < old; u += nt) {
+      R* d = Pd.cur_dense + (unsigned)Pd.cur_pos[u].x;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) d[(unsigned long long)i * Pd.plane] = R(0);
     }
-    __syncthreads();
   }
+  const R* corr = Pd.have_prev ? Pd.prev_dense : nullptr;
 
   // MD substeps against the frozen post-stream fluid (one for LB step = MD step)
   for (int sub = 0; sub < C.nsub; ++sub) {
@@ -853,7 +858,7 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
     const int qx = (cl[0] + dx) % L, qy = (cl[1] + dy) % L, qz = (cl[2] + dz) % L;
     const R w = (dx ? fr[0] : R(1) - fr[0]) * (dy ? fr[1] : R(1) - fr[1]) * (dz ? fr[2] : R(1) - fr[2]);
     R mom[4];
-    gather_node_c<S, R, DEV>(pop, P, qx, qy, qz, mom, hk, hv, hmask, Pd.prev_dn, Pd.cap);
+    gather_node_c<S, R, DEV>(pop, P, qx, qy, qz, mom, corr);
     C.e_node[e] = qx + L * (qy + L * qz);
     C.e_w[e] = w;
 #pragma unroll
@@ -889,76 +894,164 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
   __syncthreads();
   }  // substeps
 
-  // 5. deterministic spreading: sort (node, entry) keys, sum each node's contributions in
-  //    entry order, then turn the node force into population corrections
+  // 5. deterministic spreading: group the corner entries by node, sum each node's
+  //    contributions in entry order, then turn the node force into population corrections.
+  //    Up to kGroupHashMax entries the grouping uses a hash table in shared memory; the
+  //    table's slots number the nodes of the pending list (that order depends on the table
+  //    layout; no value does).  Beyond, a bitonic sort of (node, entry) keys.
   const int ne = 8 * N * C.nsub;
-  int M = 32;  // at least one warp-wide chunk; padding keys sort to the end
-  while (M < ne) M <<= 1;
-  unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem);
-  for (int i = tid; i < M; i += nt)
-    keys[i] = (i < ne) ? (((unsigned long long)(unsigned)C.e_node[i] << 32) | (unsigned)i) : ~0ull;
-  __syncthreads();
-  bitonic_sort_block(keys, M, tid, nt);
-  // leaders: first entry of each node run; slot = number of leaders before it
-  // (serial scan by one warp over chunks: ne <= 8192)
-  int* slot = reinterpret_cast<int*>(keys + M);
-  if (tid < 32) {
-    int base = 0;
-    for (int c0 = 0; c0 < ne; c0 += 32) {
-      const int i = c0 + tid;
-      int lead = 0;
-      if (i < ne) lead = (i == 0) || ((keys[i] >> 32) != (keys[i - 1] >> 32));
-      const unsigned mask = __ballot_sync(0xffffffffu, lead);
-      if (i < ne) slot[i] = lead ? base + __popc(mask & ((1u << tid) - 1u)) : -1;
-      base += __popc(mask);
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+  if (ne <= kGroupHashMax) {
+    int H = 64;
+    while (H < 2 * ne) H <<= 1;
+    int* tkey = reinterpret_cast<int*>(smem);  // node of the slot, -1 = empty
+    int* tcnt = tkey + H;                       // entries of the slot, then the fill cursor
+    int* toff = tcnt + H;                       // first list position of the slot's entries
+    int* lslot = toff + H;                      // slot of the u-th node of the pending list
+    int* eslot = lslot + H;                     // slot of each entry
+    int* elist = eslot + ne;                    // entries grouped by slot
+    int* wsum = elist + ne;                     // scan scratch: 2 x 32 warp totals, node count
+    for (int h = tid; h < H; h += nt) {
+      tkey[h] = -1;
+      tcnt[h] = 0;
     }
-    if (tid == 0) *Pd.cur_count = base;
-  }
-  __syncthreads();
-  for (int i = tid; i < ne; i += nt) {
-    const int u = slot[i];
-    if (u < 0) continue;
-    const int node = (int)(keys[i] >> 32);
-    const int e0 = (int)(keys[i] & 0xffffffffu);
-    R f[3] = {R(0), R(0), R(0)};
-    for (int r = i; r < ne && (int)(keys[r] >> 32) == node; ++r) {
-      const int e = (int)(keys[r] & 0xffffffffu);
-      const R w = C.e_w[e] * C.spread;
-      const int sub = e / (8 * N), b = (e - sub * 8 * N) >> 3;
-      const R* fch = C.fc_hist + sub * 3 * N;
-      f[0] -= w * fch[3 * b + 0] * C.inv_a3;
-      f[1] -= w * fch[3 * b + 1] * C.inv_a3;
-      f[2] -= w * fch[3 * b + 2] * C.inv_a3;
-    }
-    const R rho = C.e_mom[e0], jx = C.e_mom[C.cap + e0], jy = C.e_mom[2 * C.cap + e0],
-            jz = C.e_mom[3 * C.cap + e0];
-    R dJ[3] = {f[0] * C.dJ_scale, f[1] * C.dJ_scale, f[2] * C.dJ_scale};
-    R dm[10];
-    if (P.body_on) {
-      // the LB kernel applies the body-force correction on every node; here add the
-      // difference between the correction for the total force and the body-only one
-      R dmb[10];
-      force_moments(rho, jx, jy, jz, P.body_dJ[0], P.body_dJ[1], P.body_dJ[2], P.gs, P.gb, dmb);
-      force_moments(rho, jx, jy, jz, dJ[0] + P.body_dJ[0], dJ[1] + P.body_dJ[1], dJ[2] + P.body_dJ[2],
-                    P.gs, P.gb, dm);
-#pragma unroll
-      for (int k = 0; k < 10; ++k) dm[k] -= dmb[k];
-    } else {
-      force_moments(rho, jx, jy, jz, dJ[0], dJ[1], dJ[2], P.gs, P.gb, dm);
-    }
-    R dn[Q];
-    dmoments_to_dpops(dm, dn);
-    const int pz = node / (L * L), py = (node / L) % L, px = node % L;
-    Pd.cur_pos[u] = make_int4(node, px, py, pz);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) Pd.cur_dn[q * Pd.cap + u] = dn[q];
-    if (Pd.cur_flags) {  // stamp the LB tiles whose nodes pull from this node
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const int rx = (px + cx(q) + L) % L, ry = (py + cy(q) + L) % L, rz = (pz + cz(q) + L) % L;
-        const unsigned t = (unsigned)rx / Pd.bx + Pd.tiles_x * ((unsigned)ry / Pd.by + Pd.tiles_y * (unsigned)rz);
-        Pd.cur_flags[t] = Pd.cur_stamp;
+    __syncthreads();
+    for (int e = tid; e < ne; e += nt) {
+      const int node = C.e_node[e];
+      unsigned h = hash_node(node, (unsigned)H - 1);
+      for (int it = 0; it < H; ++it) {  // at most half full: a free slot or the node is found
+        const int old = atomicCAS(&tkey[h], -1, node);
+        if (old == -1 || old == node) break;
+        h = (h + 1) & (unsigned)(H - 1);
       }
+      eslot[e] = (int)h;
+      atomicAdd(&tcnt[h], 1);
+    }
+    __syncthreads();
+    // exclusive scans over the slots, in slot order: list offsets and node numbers.  Each
+    // thread owns a contiguous run of slots; warp scans, then a scan of the warp totals.
+    {
+      const int per = (H + nt - 1) / nt;
+      const int h0 = tid * per < H ? tid * per : H, h1 = h0 + per < H ? h0 + per : H;
+      int sc = 0, sl = 0;
+      for (int h = h0; h < h1; ++h) {
+        sc += tcnt[h];
+        sl += tcnt[h] > 0;
+      }
+      int ic = sc, il = sl;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int yc = __shfl_up_sync(0xffffffffu, ic, o), yl = __shfl_up_sync(0xffffffffu, il, o);
+        if (lane >= o) {
+          ic += yc;
+          il += yl;
+        }
+      }
+      if (lane == 31) {
+        wsum[warp] = ic;
+        wsum[32 + warp] = il;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        const int vc = lane < nwarp ? wsum[lane] : 0, vl = lane < nwarp ? wsum[32 + lane] : 0;
+        int jc = vc, jl = vl;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int yc = __shfl_up_sync(0xffffffffu, jc, o), yl = __shfl_up_sync(0xffffffffu, jl, o);
+          if (lane >= o) {
+            jc += yc;
+            jl += yl;
+          }
+        }
+        if (lane < nwarp) {
+          wsum[lane] = jc - vc;
+          wsum[32 + lane] = jl - vl;
+        }
+        if (lane == 31) {
+          *Pd.cur_count = jl;
+          wsum[64] = jl;
+        }
+      }
+      __syncthreads();
+      int bc = wsum[warp] + ic - sc, bl = wsum[32 + warp] + il - sl;
+      for (int h = h0; h < h1; ++h) {
+        const int c = tcnt[h];
+        toff[h] = bc;
+        if (c > 0) lslot[bl] = h;
+        tcnt[h] = bc;  // fill cursor
+        bc += c;
+        bl += c > 0;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < ne; e += nt) elist[atomicAdd(&tcnt[eslot[e]], 1)] = e;
+    __syncthreads();
+    const int nnode = wsum[64];
+    for (int u = tid; u < nnode; u += nt) {  // one thread per node, in list order
+      const int h = lslot[u];
+      const int base = toff[h], cnt = tcnt[h] - base;
+      for (int r = base + 1; r < base + cnt; ++r) {  // entry order (insertion sort of a short list)
+        const int e = elist[r];
+        int q = r - 1;
+        while (q >= base && elist[q] > e) {
+          elist[q + 1] = elist[q];
+          --q;
+        }
+        elist[q + 1] = e;
+      }
+      node_correction<R>(P, C, Pd, L, N, u, tkey[h], [&](int r) { return elist[r]; }, base, cnt);
+    }
+  } else {
+    int M = 32;  // at least one warp-wide chunk; padding keys sort to the end
+    while (M < ne) M <<= 1;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem);
+    for (int i = tid; i < M; i += nt)
+      keys[i] = (i < ne) ? (((unsigned long long)(unsigned)C.e_node[i] << 32) | (unsigned)i) : ~0ull;
+    __syncthreads();
+    bitonic_sort_block(keys, M, tid, nt);
+    // leaders: first entry of each node run, numbered in order (chunks of 32 entries: each
+    // warp counts the leaders of its chunks, warp 0 scans the chunk counts)
+    int* slot = reinterpret_cast<int*>(keys + M);
+    int* cbase = slot + ne;
+    const int nchunk = (ne + 31) >> 5;
+    for (int c = warp; c < nchunk; c += nwarp) {
+      const int i = (c << 5) + lane;
+      const int lead = i < ne && ((i == 0) || ((keys[i] >> 32) != (keys[i - 1] >> 32)));
+      const unsigned mask = __ballot_sync(0xffffffffu, lead);
+      if (lane == 0) cbase[c] = __popc(mask);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int base = 0;
+      for (int c0 = 0; c0 < nchunk; c0 += 32) {
+        const int c = c0 + lane;
+        const int v = c < nchunk ? cbase[c] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (c < nchunk) cbase[c] = base + incl - v;
+        base += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (lane == 0) *Pd.cur_count = base;
+    }
+    __syncthreads();
+    for (int c = warp; c < nchunk; c += nwarp) {
+      const int i = (c << 5) + lane;
+      const int lead = i < ne && ((i == 0) || ((keys[i] >> 32) != (keys[i - 1] >> 32)));
+      const unsigned mask = __ballot_sync(0xffffffffu, lead);
+      if (i < ne) slot[i] = lead ? cbase[c] + __popc(mask & ((1u << lane) - 1u)) : -1;
+    }
+    __syncthreads();
+    for (int i = tid; i < ne; i += nt) {
+      const int u = slot[i];
+      if (u < 0) continue;
+      const int node = (int)(keys[i] >> 32);
+      int cnt = 1;
+      while (i + cnt < ne && (int)(keys[i + cnt] >> 32) == node) ++cnt;
+      node_correction<R>(P, C, Pd, L, N, u, node, [&](int r) { return (int)(keys[r] & 0xffffffffu); }, i, cnt);
     }
   }
 }
@@ -977,18 +1070,21 @@ __global__ void __launch_bounds__(512) k_bead_step(const S* __restrict__ pop, co
   bead_step_block<S, R, DEV>(pop, P, C, Pd, step, smem);
 }
 
-// B[i][node] += dn_i at every pending node (each node appears once in the list); one thread
-// per (node, population): blockIdx.y is the population
+// B[i][node] += dn_i at every pending node (each node appears once in the list), and the
+// applied entries of the dense correction field back to zero; one thread per (node,
+// population): blockIdx.y is the population
 template <class S, class R>
 __global__ void __launch_bounds__(256) k_apply_pending(S* __restrict__ pop, const FluidK<R> P,
                                                         const int4* __restrict__ p_pos,
                                                         const R* __restrict__ p_dn,
-                                                        const int* __restrict__ p_count, int cap) {
+                                                        const int* __restrict__ p_count, int cap,
+                                                        R* __restrict__ dense) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= *p_count) return;
   const int i = blockIdx.y;
-  S* p = pop + (unsigned long long)i * P.plane + (unsigned)p_pos[u].x;
-  st<S, R>(p, ld<S, R>(p) + p_dn[i * cap + u]);
+  const unsigned long long off = (unsigned long long)i * P.plane + (unsigned)p_pos[u].x;
+  st<S, R>(pop + off, ld<S, R>(pop + off) + p_dn[i * cap + u]);
+  dense[off] = R(0);
 }
 
 // one trajectory frame: unwrapped positions x + xl + img * box in FP64, in the order (and

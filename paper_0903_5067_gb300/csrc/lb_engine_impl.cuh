@@ -35,18 +35,18 @@ class EngineT final : public Engine {
   void set_config(const Config& c) override { cfg_ = c; }
 
   void initialise(const double* x0, const double* v0, cudaStream_t s) override {
+    if ((size_t)Q * 256 * sizeof(R) > 48 * 1024) {  // FP64: staged corrections of a 256-node tile
+      cuda_check(cudaFuncSetAttribute(k_lb_step<S, R, DEV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(Q * 256 * sizeof(R))),
+                 "LB kernel shared memory");
+      cuda_check(cudaFuncSetAttribute(k_lb_step<S, R, DEV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(Q * 256 * sizeof(R))),
+                 "LB kernel shared memory");
+    }
     if (bead_smem() > 48 * 1024)
       cuda_check(cudaFuncSetAttribute(k_bead_step<S, R, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)bead_smem()),
                  "bead kernel shared memory");
-    if (lb_smem() > 48 * 1024) {
-      cuda_check(cudaFuncSetAttribute(k_lb_step<S, R, DEV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)lb_smem()),
-                 "LB kernel shared memory");
-      cuda_check(cudaFuncSetAttribute(k_lb_step<S, R, DEV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)lb_smem()),
-                 "LB kernel shared memory");
-    }
     const unsigned long long nb = (nnodes_ + 255) / 256;
     k_init_rest<S, R, DEV><<<(unsigned)nb, 256, 0, s>>>(pop_[0], nnodes_, plane_, (R)cfg_.rho);
     cuda_check(cudaGetLastError(), "init populations");
@@ -83,7 +83,10 @@ class EngineT final : public Engine {
       k_chain_init_forces<R><<<1, 512, 6 * N_ * sizeof(R), s>>>(C);
       cuda_check(cudaGetLastError(), "init forces");
     }
-    for (int j = 0; j < 2; ++j) cuda_check(cudaMemsetAsync(p_count_[j], 0, sizeof(int), s), "memset pending");
+    for (int j = 0; j < 2; ++j) {
+      cuda_check(cudaMemsetAsync(p_count_[j], 0, sizeof(int), s), "memset pending");
+      if (corr_[j]) cuda_check(cudaMemsetAsync(corr_[j], 0, (size_t)Q * plane_ * sizeof(R), s), "memset corrections");
+    }
     reset_stamps(s);
   }
 
@@ -306,6 +309,12 @@ class EngineT final : public Engine {
   void flip() { cur_ ^= 1; }
   unsigned long long nodes() const { return nnodes_; }
   int pending_capacity() const { return cap_; }
+  // pending-correction lists of slot j (the batched driver keeps its own slot order)
+  int4* pending_pos(int j) const { return p_pos_[j]; }
+  R* pending_dn(int j) const { return p_dn_[j]; }
+  int* pending_count(int j) const { return p_count_[j]; }
+  R* pending_dense(int j) const { return corr_[j]; }
+  unsigned long long plane() const { return plane_; }
   size_t bead_smem_bytes() const { return bead_smem(); }
   int chain_length() const { return N_; }
   const Config& config() const { return cfg_; }
@@ -468,7 +477,7 @@ class EngineT final : public Engine {
     memset(&lc, 0, sizeof(lc));
     lc.gridDim = grd;
     lc.blockDim = blk;
-    lc.dynamicSmemBytes = Pd.have_prev ? lb_smem() : 0;
+    lc.dynamicSmemBytes = Pd.have_prev ? (size_t)Q * blk.x * blk.y * sizeof(R) : 0;  // staged corrections
     lc.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -486,7 +495,7 @@ class EngineT final : public Engine {
 
   void apply(S* buf, const FluidK<R>& P, int slot, cudaStream_t s) {
     k_apply_pending<S, R><<<dim3((cap_ + 255) / 256, Q), 256, 0, s>>>(buf, P, p_pos_[slot], p_dn_[slot],
-                                                                     p_count_[slot], cap_);
+                                                                     p_count_[slot], cap_, corr_[slot]);
     cuda_check(cudaGetLastError(), "apply kernel");
   }
 
@@ -498,38 +507,27 @@ class EngineT final : public Engine {
     const int c = pslot_, p = pslot_ ^ 1;
     Pd.have_prev = (deferred && open_) ? 1 : 0;
     Pd.prev_stamp = stamp_ - 1;
-    Pd.prev_pos = p_pos_[p];
-    Pd.prev_dn = p_dn_[p];
-    Pd.prev_count = p_count_[p];
     Pd.prev_flags = flags_[p];
+    Pd.prev_dense = corr_[p];
+    Pd.cur_dense = corr_[c];
+    Pd.plane = plane_;
     Pd.cur_pos = p_pos_[c];
     Pd.cur_dn = p_dn_[c];
     Pd.cur_count = p_count_[c];
     Pd.cur_flags = deferred ? flags_[c] : nullptr;
     Pd.cur_stamp = stamp_;
     Pd.cap = cap_;
-    dim3 blk, grd;
-    lb_launch_shape(blk, grd);
-    Pd.bx = blk.x;
-    Pd.by = blk.y;
-    Pd.tiles_x = grd.x;
-    Pd.tiles_y = grd.y;
+    Pd.seg0 = 0;
     return Pd;
   }
 
   void reset_stamps(cudaStream_t s) {
     for (int j = 0; j < 2; ++j)
-      cuda_check(cudaMemsetAsync(flags_[j], 0xff, ntiles() * sizeof(int), s), "memset stamps");
+      cuda_check(cudaMemsetAsync(flags_[j], 0xff, nsegs() * sizeof(int), s), "memset stamps");
     stamp_ = 0;
   }
 
-  size_t ntiles() const {
-    dim3 blk, grd;
-    lb_launch_shape(blk, grd);
-    return (size_t)grd.x * grd.y * grd.z;
-  }
-
-  size_t lb_smem() const { return (size_t)Q * 256 * sizeof(R); }
+  size_t nsegs() const { return (size_t)((nnodes_ + 31) >> kSegShift); }
 
   void lb_launch_shape(dim3& blk, dim3& grd) const {
     unsigned bx = ((unsigned)L_ + 31) / 32 * 32;
@@ -540,15 +538,21 @@ class EngineT final : public Engine {
   }
 
   size_t bead_smem() const {
+    // phase 5: up to kGroupHashMax entries a node table (4 x H ints, H >= 2 x entries), entry
+    // slots and lists and scan scratch; beyond, sort keys, leader slots and chunk counts
     const size_t ne = 8 * (size_t)N_ * nsub_;
-    size_t M = 32;
-    while (M < ne) M <<= 1;
-    const size_t sortb = M * 8 + ne * 4;
-    // positions (hi, lo), then the hash of the previous step's corrections (2 x H ints)
-    size_t H = 1;
-    while (H < 2 * (size_t)cap_) H <<= 1;
-    const size_t posb = align_up(6 * (size_t)N_ * sizeof(R), 16) + 2 * H * sizeof(int);
-    return sortb > posb ? sortb : posb;
+    size_t groupb;
+    if (ne <= (size_t)kGroupHashMax) {
+      size_t H = 64;
+      while (H < 2 * ne) H <<= 1;
+      groupb = (4 * H + 2 * ne + 65) * sizeof(int);
+    } else {
+      size_t M = 32;
+      while (M < ne) M <<= 1;
+      groupb = M * 8 + ne * 4 + ((ne + 31) / 32) * 4;
+    }
+    const size_t posb = 6 * (size_t)N_ * sizeof(R);  // positions (hi, lo)
+    return groupb > posb ? groupb : posb;
   }
 
   FluidK<R> fluid() const {
@@ -699,7 +703,8 @@ class EngineT final : public Engine {
       p_pos_[j] = reinterpret_cast<int4*>(take(cap_ * sizeof(int4)));
       p_dn_[j] = reinterpret_cast<R*>(take((size_t)Q * cap_ * sizeof(R)));
       p_count_[j] = reinterpret_cast<int*>(take(sizeof(int)));
-      flags_[j] = reinterpret_cast<int*>(take(ntiles() * sizeof(int)));
+      flags_[j] = reinterpret_cast<int*>(take(nsegs() * sizeof(int)));
+      corr_[j] = N_ > 0 ? reinterpret_cast<R*>(take((size_t)Q * plane_ * sizeof(R))) : nullptr;
     }
     status_ = reinterpret_cast<unsigned*>(take(sizeof(unsigned)));
     nonpos_ = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long)));
@@ -724,7 +729,8 @@ class EngineT final : public Engine {
   int4* p_pos_[2] = {nullptr, nullptr};
   R* p_dn_[2] = {nullptr, nullptr};
   int* p_count_[2] = {nullptr, nullptr};
-  int* flags_[2] = {nullptr, nullptr};  // per LB tile: stamp of the last deferred step that corrected it
+  int* flags_[2] = {nullptr, nullptr};  // per 32-node segment: the last deferred step that stamped it
+  R* corr_[2] = {nullptr, nullptr};     // dense correction fields [i][plane], zero but at pending nodes
   int pslot_ = 0, stamp_ = 0;
   bool open_ = false;  // a deferred step's correction is pending
   unsigned* status_ = nullptr;

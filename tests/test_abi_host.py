@@ -109,3 +109,20 @@ def test_analysis_and_recording_validate_arguments(lblib):
     assert ei.value.code == lblib.LB_ERR_STATE
     assert lblib.lb_trajectory_frames(ctx) == 0
     lblib.lb_destroy(ctx)
+
+
+def test_chain_contexts_add_two_dense_correction_fields(lblib):
+    """With a chain, the deferred force corrections live in two dense fields of the
+    arithmetic type (FP32 for the 16-bit storage) beside the two population buffers."""
+    from paper_0903_5067_gb300 import inputs
+
+    L = 32
+    pop = lambda b: 19 * L ** 3 * b
+    for prec, s_b, r_b in ((lblib.LB_FP64, 8, 8), (lblib.LB_FP32, 4, 4), (lblib.LB_BF16, 2, 4)):
+        ctx = lblib.lb_create(L, 1.0, 3.0, 3.0, 1.0, 0.01, 1.0, 1, prec)
+        lblib.lb_add_chain(ctx, 16, 1.0, 20.8, 30.0, 1.5, 1.0, 1.0,
+                           x0=inputs.chain_walk(16, L=L, seed=1, self_avoiding=True))
+        size = lblib.lb_workspace_size(ctx)
+        lblib.lb_destroy(ctx)
+        expect = 2 * pop(s_b) + 2 * pop(r_b)
+        assert expect <= size < expect * 1.1, prec

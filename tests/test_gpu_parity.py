@@ -246,7 +246,8 @@ def test_md_substeps_with_paper_parameters(lblib):
     Case(L=12, N=24, steps=30, seed=3),
     Case(L=40, N=32, steps=12, seed=4, ext=(0.5, -0.2, 0.1), counter=True),
     Case(L=9, N=10, steps=15, seed=5, substeps=3),
-], ids=["L12", "L40_body_force", "L9_substeps"])
+    Case(L=12, N=48, steps=6, seed=6, substeps=3),
+], ids=["L12", "L40_body_force", "L9_substeps", "L12_sorted_spreading"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_deferred_corrections_are_bit_exact(lblib, case, prec):
     """A multi-step call keeps each step's bead force correction pending and adds it where the
@@ -279,3 +280,14 @@ def test_deferred_corrections_with_observable_stride(lblib):
     st = oracle_run(case)
     assert pop_rel_err(na, st.n) <= 1e-12
     a.close()
+
+
+def test_spreading_of_many_entries_matches_oracle(lblib):
+    """More than 1024 corner entries per step (N = 48 beads, 3 MD substeps: 1152) take the
+    sorted grouping instead of the shared-memory table; FP64 parity with the oracle."""
+    case = Case(L=12, N=48, steps=6, seed=6, substeps=3)
+    st = oracle_run(case)
+    n, x, v, obs = gpu_run(lblib, case, lblib.LB_FP64)
+    assert pop_rel_err(n, st.n) <= 1e-12
+    ex, ev = bead_errs(x, v, st, case)
+    assert ex <= 1e-12 and ev <= 1e-11
