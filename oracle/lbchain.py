@@ -9,7 +9,7 @@ arithmetic are written here from their definitions.
 
 Everything is float64 numpy; every array over the lattice has the node axes (z, y, x) so
 that the flat node index is ``x + L*(y + L*z)``.  Populations are partial mass densities
-(Sec. II B: "the (partial) fluid mass density at grid site r").  Where the paper is silent
+(Sec. II B: each n_i is a partial mass density of the fluid at its node).  Where the paper is silent
 (mode basis, relaxation rates, noise amplitudes, forcing, integrator, random numbers) the
 module follows the readings listed in the design notes; each function says which.
 

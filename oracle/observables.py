@@ -12,7 +12,7 @@ every origin t0 with t0 + lag inside the trajectory, as written out below; nothi
 blocked, windowed or reordered beyond the definitions.
 
 Readings (where the paper leaves a choice):
-- g1 and g2 use "the two innermost monomers" (Sec. III B): for a chain of N beads numbered
+- g1 and g2 average over the two monomers at the middle of the chain (Sec. III B): for N beads numbered
   0..N-1, the monomers floor((N-1)/2) and ceil((N-1)/2) (the same bead twice when N is
   odd); the caller may pass another pair.
 - The Rouse correlation is normalised by <X_p^2> averaged over all frames.
