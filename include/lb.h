@@ -234,6 +234,9 @@ void lb_batch_destroy(lb_batch* b);
  *   <X_p^2>, the normalisation of the paper's correlation function.  max_lag <= 65535.
  * lb_analysis_static_sk: S[nk] = (1/N) sum_{i,j} < sin(k r_ij) / (k r_ij) > over the T
  *   frames, for the nk wave numbers k[] (device array) (Sec. III A, S(k)).
+ * lb_analysis_inverse_radius: out[0] = <1/R_H> = (1/N^2) sum_{i != j} <1/r_ij> over the T
+ *   frames (Sec. III A, the hydrodynamic radius of the chain in an infinite medium); N >= 2
+ *   and no two beads at the same position.
  * lb_analysis_dynamic_sk: S[nk][max_lag+1] = (1/N) sum_{i,j} < sin(k d)/(k d) >,
  *   d = |r_i(t0+lag) - r_j(t0)|, over origins t0 = 0, s, 2s, ... (s = origin_stride)
  *   (Sec. III B, S(k,t); the isotropic average of exp(i k.[r_i(t) - r_j(0)])). */
@@ -241,6 +244,7 @@ int lb_analysis_msd(const double* traj, int T, int N, int max_lag, int i0, int i
 int lb_analysis_rouse_modes(const double* traj, int T, int N, int P, double* X, void* stream);
 int lb_analysis_rouse_correlation(const double* X, int T, int P, int max_lag, double* c, void* stream);
 int lb_analysis_static_sk(const double* traj, int T, int N, const double* k, int nk, double* S, void* stream);
+int lb_analysis_inverse_radius(const double* traj, int T, int N, double* out, void* stream);
 int lb_analysis_dynamic_sk(const double* traj, int T, int N, const double* k, int nk, int max_lag,
                            int origin_stride, double* S, void* stream);
 

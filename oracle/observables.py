@@ -139,6 +139,20 @@ def dynamic_structure_factor(traj: np.ndarray, ks, max_lag: int, origin_stride: 
     return out
 
 
+def inverse_hydrodynamic_radius(traj: np.ndarray) -> float:
+    """<1/R_H> = (1/N^2) sum_{i != j} <1/r_ij>, averaged over the frames (Sec. III A, the
+    infinite-medium hydrodynamic radius of the chain)."""
+    T, N, _ = traj.shape
+    s = 0.0
+    for t in range(T):
+        for i in range(N):
+            for j in range(N):
+                if i != j:
+                    d = traj[t, i] - traj[t, j]
+                    s += 1.0 / math.sqrt(float(d @ d))
+    return s / (N * N * T)
+
+
 def rouse_chain_trajectory(N: int, T: int, dt: float, b: float, zeta: float, kT: float, seed: int):
     """A Gaussian Rouse chain (harmonic springs of constant 3kT/b^2, no hydrodynamic or
     excluded-volume interaction, friction zeta per bead) sampled exactly: in its normal

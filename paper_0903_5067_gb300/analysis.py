@@ -89,3 +89,14 @@ def dynamic_sk(traj, ks, max_lag: int, origin_stride: int = 1):
     lb.lb_analysis_dynamic_sk(traj.data_ptr(), T, N, k.data_ptr(), k.numel(), max_lag, origin_stride, S.data_ptr(),
                               _stream())
     return S.cpu().numpy()
+
+
+def inverse_radius(traj) -> float:
+    """<1/R_H> = (1/N^2) sum_{i != j} <1/r_ij> over the frames."""
+    import torch
+
+    traj = _check_traj(traj)
+    T, N, _ = traj.shape
+    out = torch.empty(1, dtype=torch.float64, device=traj.device)
+    lb.lb_analysis_inverse_radius(traj.data_ptr(), T, N, out.data_ptr(), _stream())
+    return float(out.item())

@@ -170,6 +170,26 @@ __global__ void __launch_bounds__(kThreads) k_dynamic_sk(const double* __restric
   if (threadIdx.x == 0) S[(size_t)blockIdx.x * nlag + lag] = norig > 0 ? v[0] / ((double)N * norig) : 0.0;
 }
 
+// one block: 1/r_ij over the pairs i < j of every frame
+__global__ void __launch_bounds__(kThreads) k_inverse_radius(const double* __restrict__ traj, int T, int N,
+                                                             double* __restrict__ out) {
+  __shared__ double sh[1][kThreads];
+  const long long nn = (long long)N * N;
+  const long long total = nn * T;
+  double v[1] = {0};
+  for (long long u = threadIdx.x; u < total; u += kThreads) {
+    const int t = (int)(u / nn);
+    const int r = (int)(u - (long long)t * nn);
+    const int i = r / N, j = r - (r / N) * N;
+    if (i >= j) continue;
+    const double* f = traj + (size_t)t * N * 3;
+    const double dx = f[3 * i] - f[3 * j], dy = f[3 * i + 1] - f[3 * j + 1], dz = f[3 * i + 2] - f[3 * j + 2];
+    v[0] += 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  block_sum<1>(v, sh);
+  if (threadIdx.x == 0) out[0] = 2.0 * v[0] / ((double)N * N * T);
+}
+
 int launch_status() {
   const cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) return LB_OK;
@@ -201,6 +221,12 @@ int lb_analysis_rouse_correlation(const double* X, int T, int P, int max_lag, do
 int lb_analysis_static_sk(const double* traj, int T, int N, const double* k, int nk, double* S, void* stream) {
   if (!traj || !k || !S || T < 1 || N < 1 || nk < 1) return LB_ERR_ARG;
   k_static_sk<<<nk, kThreads, 0, (cudaStream_t)stream>>>(traj, T, N, k, S);
+  return launch_status();
+}
+
+int lb_analysis_inverse_radius(const double* traj, int T, int N, double* out, void* stream) {
+  if (!traj || !out || T < 1 || N < 2) return LB_ERR_ARG;
+  k_inverse_radius<<<1, kThreads, 0, (cudaStream_t)stream>>>(traj, T, N, out);
   return launch_status();
 }
 

@@ -50,6 +50,7 @@ _SIGS = {
     "lb_analysis_rouse_correlation": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
     "lb_analysis_static_sk": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_int, _vp, _vp]),
     "lb_analysis_dynamic_sk": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
+    "lb_analysis_inverse_radius": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp]),
     "lb_reset_reference": (C.c_int, [_vp]),
     "lb_save": (C.c_int, [_vp, C.c_char_p]),
     "lb_load": (C.c_int, [_vp, C.c_char_p]),
@@ -207,6 +208,10 @@ def lb_analysis_rouse_correlation(X_ptr, T, P, max_lag, c_ptr, stream):
 
 def lb_analysis_static_sk(traj_ptr, T, N, k_ptr, nk, S_ptr, stream):
     _check(_lib.lb_analysis_static_sk(traj_ptr, T, N, k_ptr, nk, S_ptr, stream), "lb_analysis_static_sk")
+
+
+def lb_analysis_inverse_radius(traj_ptr, T, N, out_ptr, stream):
+    _check(_lib.lb_analysis_inverse_radius(traj_ptr, T, N, out_ptr, stream), "lb_analysis_inverse_radius")
 
 
 def lb_analysis_dynamic_sk(traj_ptr, T, N, k_ptr, nk, max_lag, origin_stride, S_ptr, stream):

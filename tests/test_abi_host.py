@@ -126,3 +126,11 @@ def test_chain_contexts_add_two_dense_correction_fields(lblib):
         lblib.lb_destroy(ctx)
         expect = 2 * pop(s_b) + 2 * pop(r_b)
         assert expect <= size < expect * 1.1, prec
+
+
+def test_inverse_radius_validates_arguments(lblib):
+    for call in (lambda: lblib.lb_analysis_inverse_radius(None, 10, 4, 1, None),
+                 lambda: lblib.lb_analysis_inverse_radius(1, 10, 1, 1, None)):  # N < 2
+        with pytest.raises(lblib.LBError) as ei:
+            call()
+        assert ei.value.code == lblib.LB_ERR_ARG

@@ -77,6 +77,7 @@ def test_analysis_matches_oracle_on_an_lb_trajectory(lblib):
     ks = [0.2, 0.8, 1.7, 3.1]
     _close(an.static_sk(traj, ks), ob.static_structure_factor(t, ks))
     _close(an.dynamic_sk(traj, ks[:2], 6, origin_stride=3), ob.dynamic_structure_factor(t, ks[:2], 6, origin_stride=3))
+    assert an.inverse_radius(traj) == pytest.approx(ob.inverse_hydrodynamic_radius(t), rel=1e-12)
     assert torch.cuda.is_available()
 
 

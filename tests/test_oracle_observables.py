@@ -134,3 +134,16 @@ def test_rouse_correlation_of_a_gaussian_rouse_chain_decays_with_the_rouse_times
     # centre of mass diffuses with D = kT / (N zeta): g3 = 6 D t
     g1, g2, g3 = ob.msd(traj[:4000], 20)
     assert g3[20] == pytest.approx(6 * (1.0 / N) * 20 * dt, rel=0.1)
+
+
+def test_inverse_hydrodynamic_radius_closed_forms():
+    d = 1.7
+    two = np.array([[[0.0, 0, 0], [d, 0, 0]]])
+    assert ob.inverse_hydrodynamic_radius(two) == pytest.approx(2 / (4 * d), rel=1e-15)  # 2 ordered pairs / N^2
+    s = 1.3
+    tri = np.array([[[0.0, 0, 0], [s, 0, 0], [s / 2, s * math.sqrt(3) / 2, 0]]])
+    assert ob.inverse_hydrodynamic_radius(tri) == pytest.approx(6 / (9 * s), rel=1e-14)
+    # average over frames: a rod whose spacing doubles in the second frame
+    rod = np.array([[[0.0, 0, 0], [1.0, 0, 0], [2.0, 0, 0]], [[0.0, 0, 0], [2.0, 0, 0], [4.0, 0, 0]]])
+    one = 2 * (1 + 1 + 0.5) / 9
+    assert ob.inverse_hydrodynamic_radius(rod) == pytest.approx((one + one / 2) / 2, rel=1e-14)
