@@ -100,7 +100,10 @@ int lb_workspace_size(lb_ctx* ctx, size_t* bytes);
 int lb_bind_workspace(lb_ctx* ctx, void* device_ptr, size_t bytes);
 
 /* Advance n >= 0 coupled steps (Sec. II B, Eq. 3 for the fluid; velocity Verlet for the
- * beads, friction at the half-step velocity).  Asynchronous on the context stream. */
+ * beads, friction at the half-step velocity).  Asynchronous on the context stream.  The force
+ * correction of the last step is kept pending (the next step reads it where it pulls); every
+ * call that reads or replaces the fluid state (populations, observables, checkpoints, the
+ * adjoint) applies it first, so results never depend on how steps are split into calls. */
 int lb_step(lb_ctx* ctx, int64_t n);
 
 /* Wait for the context stream and return the latched device status. */

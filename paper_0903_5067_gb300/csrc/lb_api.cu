@@ -343,7 +343,8 @@ int lb_step(lb_ctx* ctx, int64_t n) {
         ctx->eng->observables(nullptr, ctx->step, 1, ctx->stream);
       if (ctx->traj && (ctx->step - ctx->traj_origin) % ctx->traj_stride == 0) record_frame(ctx);
     }
-    ctx->eng->flush(ctx->stream);
+    // the last step's force correction stays pending: every call that reads or replaces the
+    // fluid state applies it first
     return (int)LB_OK;
   });
 }

@@ -1096,6 +1096,17 @@ __global__ void k_record_frame(const R* __restrict__ x, const R* __restrict__ xl
     dst[t] = __dadd_rn(__dadd_rn((double)x[t], (double)xl[t]), __dmul_rn((double)img[t], box));
 }
 
+// bead read-back: out[0..n3) unwrapped positions as k_record_frame forms them, out[n3..2 n3)
+// velocities, FP64
+template <class R>
+__global__ void k_bead_readback(const R* __restrict__ x, const R* __restrict__ xl, const int* __restrict__ img,
+                                const R* __restrict__ v, int n3, double box, double* __restrict__ out) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += gridDim.x * blockDim.x) {
+    out[t] = __dadd_rn(__dadd_rn((double)x[t], (double)xl[t]), __dmul_rn((double)img[t], box));
+    out[n3 + t] = (double)v[t];
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // initial state, conversions, reductions
 // ---------------------------------------------------------------------------------------

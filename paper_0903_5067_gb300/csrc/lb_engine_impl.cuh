@@ -349,21 +349,17 @@ class EngineT final : public Engine {
     cuda_check(cudaStreamSynchronize(s), "sync upload");
   }
 
+  // bead arrays are final once the bead kernel of the last step has run (pending fluid
+  // corrections do not touch them): no flush.  One kernel forms the FP64 unwrapped positions
+  // and velocities in a device staging area, then one copy per output array.
   void get_beads(double* x, double* v, cudaStream_t s) override {
-    flush(s);
     if (N_ == 0) return;
-    std::vector<R> xw(3 * N_), xlo(3 * N_), vv(3 * N_);
-    std::vector<int> im(3 * N_);
-    cuda_check(cudaMemcpyAsync(xw.data(), x_, 3 * N_ * sizeof(R), cudaMemcpyDeviceToHost, s), "dl x");
-    cuda_check(cudaMemcpyAsync(xlo.data(), xl_, 3 * N_ * sizeof(R), cudaMemcpyDeviceToHost, s), "dl xl");
-    cuda_check(cudaMemcpyAsync(im.data(), img_, 3 * N_ * sizeof(int), cudaMemcpyDeviceToHost, s), "dl img");
-    cuda_check(cudaMemcpyAsync(vv.data(), v_, 3 * N_ * sizeof(R), cudaMemcpyDeviceToHost, s), "dl v");
+    const int n3 = 3 * N_;
+    k_bead_readback<R><<<(n3 + 255) / 256, 256, 0, s>>>(x_, xl_, img_, v_, n3, cfg_.L * cfg_.a, rb_);
+    cuda_check(cudaGetLastError(), "bead read-back");
+    if (x) cuda_check(cudaMemcpyAsync(x, rb_, n3 * sizeof(double), cudaMemcpyDeviceToHost, s), "dl x");
+    if (v) cuda_check(cudaMemcpyAsync(v, rb_ + n3, n3 * sizeof(double), cudaMemcpyDeviceToHost, s), "dl v");
     cuda_check(cudaStreamSynchronize(s), "sync beads");
-    const double box = cfg_.L * cfg_.a;
-    for (int t = 0; t < 3 * N_; ++t) {
-      if (x) x[t] = (double)xw[t] + (double)xlo[t] + (double)im[t] * box;
-      if (v) v[t] = (double)vv[t];
-    }
   }
 
   void observables(double* out, int64_t step, int accumulate, cudaStream_t s) override {
@@ -401,7 +397,6 @@ class EngineT final : public Engine {
   }
 
   unsigned read_status(cudaStream_t s) override {
-    flush(s);
     unsigned st = 0;
     cuda_check(cudaMemcpyAsync(&st, status_, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "status");
     cuda_check(cudaStreamSynchronize(s), "sync status");
@@ -696,6 +691,7 @@ class EngineT final : public Engine {
     fcons_ = reinterpret_cast<R*>(take(n3 * sizeof(R)));
     fch_ = reinterpret_cast<R*>(take(n3 * nsub_ * sizeof(R)));
     xref_ = reinterpret_cast<double*>(take(n3 * sizeof(double)));
+    rb_ = reinterpret_cast<double*>(take(2 * n3 * sizeof(double)));
     e_node_ = reinterpret_cast<int*>(take(cap_ * sizeof(int)));
     e_w_ = reinterpret_cast<R*>(take(cap_ * sizeof(R)));
     e_mom_ = reinterpret_cast<R*>(take(4 * cap_ * sizeof(R)));
@@ -724,6 +720,7 @@ class EngineT final : public Engine {
   R *x_ = nullptr, *xl_ = nullptr, *v_ = nullptr, *F_ = nullptr, *Fc_ = nullptr, *vh_ = nullptr, *fcons_ = nullptr;
   int* img_ = nullptr;
   double* xref_ = nullptr;
+  double* rb_ = nullptr;  // bead read-back staging: 3N positions, 3N velocities (FP64)
   int* e_node_ = nullptr;
   R *e_w_ = nullptr, *e_mom_ = nullptr;
   int4* p_pos_[2] = {nullptr, nullptr};

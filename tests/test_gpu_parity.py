@@ -250,10 +250,11 @@ def test_md_substeps_with_paper_parameters(lblib):
 ], ids=["L12", "L40_body_force", "L9_substeps", "L12_sorted_spreading"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_deferred_corrections_are_bit_exact(lblib, case, prec):
-    """A multi-step call keeps each step's bead force correction pending and adds it where the
-    next step reads the populations (LB kernel in the stamped tiles, bead gather through a
-    hash).  In FP64 and FP32 that is the same arithmetic as applying it at the end of every
-    step, so one call of K steps and K calls of one step agree bit for bit."""
+    """Consecutive steps keep each step's bead force correction pending and add it where the
+    next step reads the populations (LB kernel at the nodes of stamped segments, bead gather
+    from the dense correction field).  In FP64 and FP32 that is the same arithmetic as
+    applying it at the end of every step: K deferred steps and K steps each completed by a
+    read of the fluid agree bit for bit."""
     p = getattr(lblib, "LB_" + prec.upper())
     a = gpu_sim(lblib, case, p)
     a.step(case.steps)
@@ -262,6 +263,7 @@ def test_deferred_corrections_are_bit_exact(lblib, case, prec):
     b = gpu_sim(lblib, case, p)
     for _ in range(case.steps):
         b.step(1)
+        b.observables()  # reads the fluid: applies the pending correction (a complete step)
     nb = b.populations()
     xb, vb = b.beads()
     a.close()
