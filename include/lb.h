@@ -121,6 +121,16 @@ int lb_set_populations(lb_ctx* ctx, const double* in, size_t count);
  * NULL.  Synchronising.  Before the first device call it returns the staged initial chain
  * (given or generated by lb_add_chain) without touching the device. */
 int lb_get_beads(lb_ctx* ctx, double* x, double* v, size_t cap);
+/* The same read-back enqueued on the context stream without waiting, so that the caller can
+ * keep steps queued while earlier results travel: x, v (3N doubles each, v may be NULL) must
+ * stay valid until the read-back completes and should be pinned (page-locked) host memory for
+ * the copies to be asynchronous.  *ticket identifies the read-back; lb_wait(ctx, ticket)
+ * blocks until it (and everything enqueued before it) has completed and returns the device
+ * status latched at that point.  Tickets older than the last 8 remain valid (a later
+ * read-back completes after them).  Needs a chain and a live context (LB_ERR_ARG otherwise:
+ * a bad pointer, size or ticket). */
+int lb_get_beads_async(lb_ctx* ctx, double* x, double* v, size_t cap, int64_t* ticket);
+int lb_wait(lb_ctx* ctx, int64_t ticket);
 
 /* FP64 observables (Sec. III A-B), cap >= LB_NOBS:
  *  [0] step  [1] mass a^3 sum n  [2..4] total momentum (fluid + beads + h/2 sum F_c)

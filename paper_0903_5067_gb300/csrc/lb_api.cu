@@ -56,6 +56,11 @@ struct lb_ctx {
   std::unique_ptr<Engine> eng;
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+  // asynchronous bead read-backs: a ring of events and pinned status words by ticket
+  static constexpr int kTickets = 8;
+  cudaEvent_t tev[kTickets] = {};
+  unsigned* tstatus = nullptr;
+  int64_t tickets = 0;
   double timed_ms = 0.0;
   int64_t timed_launches = 0;
 };
@@ -399,6 +404,35 @@ int lb_get_beads(lb_ctx* ctx, double* x, double* v, size_t cap) {
   });
 }
 
+int lb_get_beads_async(lb_ctx* ctx, double* x, double* v, size_t cap, int64_t* ticket) {
+  if (!ctx || !ticket) return LB_ERR_ARG;
+  if (cap < 3 * (size_t)ctx->cfg.N) return fail(LB_ERR_ARG, "bead buffer too small");
+  return guarded([&] {
+    materialise(ctx);
+    if (!ctx->tstatus) {
+      cuda_check(cudaMallocHost(&ctx->tstatus, lb_ctx::kTickets * sizeof(unsigned)), "pinned status");
+      for (int j = 0; j < lb_ctx::kTickets; ++j)
+        cuda_check(cudaEventCreateWithFlags(&ctx->tev[j], cudaEventDisableTiming), "event");
+    }
+    const int slot = (int)(ctx->tickets % lb_ctx::kTickets);
+    ctx->eng->enqueue_beads(x, v, ctx->stream);
+    ctx->eng->enqueue_status(ctx->tstatus + slot, ctx->stream);
+    cuda_check(cudaEventRecord(ctx->tev[slot], ctx->stream), "record read-back");
+    *ticket = ctx->tickets++;
+    return (int)LB_OK;
+  });
+}
+
+int lb_wait(lb_ctx* ctx, int64_t ticket) {
+  if (!ctx || ticket < 0 || ticket >= ctx->tickets) return LB_ERR_ARG;
+  return guarded([&] {
+    const int slot = (int)(ticket % lb_ctx::kTickets);
+    // a later read-back in the same slot completes after this one: waiting on it suffices
+    cuda_check(cudaEventSynchronize(ctx->tev[slot]), "wait read-back");
+    return status_from_device(ctx->tstatus[slot]);
+  });
+}
+
 int lb_get_observables(lb_ctx* ctx, double* out, size_t cap) {
   if (!ctx || !out) return LB_ERR_ARG;
   if (cap < LB_NOBS) return fail(LB_ERR_ARG, "observable buffer too small");
@@ -537,6 +571,12 @@ void lb_destroy(lb_ctx* ctx) {
   try {
     drain_timing(ctx);
   } catch (...) {
+  }
+  if (ctx->tstatus) {  // asynchronous read-backs may still be in flight
+    if (ctx->live) cudaStreamSynchronize(ctx->stream);
+    for (int j = 0; j < lb_ctx::kTickets; ++j)
+      if (ctx->tev[j]) cudaEventDestroy(ctx->tev[j]);
+    cudaFreeHost(ctx->tstatus);
   }
   if (ctx->ws_owned && ctx->ws) cudaFree(ctx->ws);
   delete ctx;

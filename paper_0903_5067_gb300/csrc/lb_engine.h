@@ -59,6 +59,11 @@ class Engine {
   virtual void get_populations(double* out, cudaStream_t s) = 0;
   virtual void set_populations(const double* in, cudaStream_t s) = 0;
   virtual void get_beads(double* x, double* v, cudaStream_t s) = 0;
+  // the same read-back enqueued on s without waiting (x, v: host memory that stays valid
+  // until the stream reaches the copies; pinned memory makes them asynchronous)
+  virtual void enqueue_beads(double* x, double* v, cudaStream_t s) = 0;
+  // enqueue a copy of the device status word to host memory
+  virtual void enqueue_status(unsigned* host, cudaStream_t s) = 0;
   virtual void observables(double* out, int64_t step, int accumulate, cudaStream_t s) = 0;
   virtual void reset_reference(cudaStream_t s) = 0;
   // write the current unwrapped bead positions (3N doubles) to device memory

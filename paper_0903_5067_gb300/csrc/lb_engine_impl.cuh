@@ -354,12 +354,21 @@ class EngineT final : public Engine {
   // and velocities in a device staging area, then one copy per output array.
   void get_beads(double* x, double* v, cudaStream_t s) override {
     if (N_ == 0) return;
+    enqueue_beads(x, v, s);
+    cuda_check(cudaStreamSynchronize(s), "sync beads");
+  }
+
+  void enqueue_beads(double* x, double* v, cudaStream_t s) override {
+    if (N_ == 0) return;
     const int n3 = 3 * N_;
     k_bead_readback<R><<<(n3 + 255) / 256, 256, 0, s>>>(x_, xl_, img_, v_, n3, cfg_.L * cfg_.a, rb_);
     cuda_check(cudaGetLastError(), "bead read-back");
     if (x) cuda_check(cudaMemcpyAsync(x, rb_, n3 * sizeof(double), cudaMemcpyDeviceToHost, s), "dl x");
     if (v) cuda_check(cudaMemcpyAsync(v, rb_ + n3, n3 * sizeof(double), cudaMemcpyDeviceToHost, s), "dl v");
-    cuda_check(cudaStreamSynchronize(s), "sync beads");
+  }
+
+  void enqueue_status(unsigned* host, cudaStream_t s) override {
+    cuda_check(cudaMemcpyAsync(host, status_, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "status");
   }
 
   void observables(double* out, int64_t step, int accumulate, cudaStream_t s) override {

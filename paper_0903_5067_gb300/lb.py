@@ -41,6 +41,8 @@ _SIGS = {
     "lb_get_populations": (C.c_int, [_vp, _dp, C.c_size_t]),
     "lb_set_populations": (C.c_int, [_vp, _dp, C.c_size_t]),
     "lb_get_beads": (C.c_int, [_vp, _dp, _dp, C.c_size_t]),
+    "lb_get_beads_async": (C.c_int, [_vp, _dp, _dp, C.c_size_t, C.POINTER(C.c_int64)]),
+    "lb_wait": (C.c_int, [_vp, C.c_int64]),
     "lb_get_observables": (C.c_int, [_vp, _dp, C.c_size_t]),
     "lb_set_obs_stride": (C.c_int, [_vp, C.c_int]),
     "lb_record_trajectory": (C.c_int, [_vp, _vp, C.c_int, C.c_int]),
@@ -172,6 +174,19 @@ def lb_set_populations(ctx, arr: np.ndarray):
 
 def lb_get_beads(ctx, x: np.ndarray | None, v: np.ndarray | None, cap: int):
     _check(_lib.lb_get_beads(ctx, _dbuf(x), _dbuf(v), cap), "lb_get_beads")
+
+
+def lb_get_beads_async(ctx, x: np.ndarray, v, cap: int) -> int:
+    """Enqueue a bead read-back into x (and v) without waiting; returns the ticket for
+    lb_wait.  The arrays must stay alive (and should be pinned) until then."""
+    t = C.c_int64()
+    _check(_lib.lb_get_beads_async(ctx, _dbuf(x), _dbuf(v), cap, C.byref(t)),
+           "lb_get_beads_async")
+    return t.value
+
+
+def lb_wait(ctx, ticket: int):
+    _check(_lib.lb_wait(ctx, int(ticket)), "lb_wait")
 
 
 def lb_get_observables(ctx) -> np.ndarray:

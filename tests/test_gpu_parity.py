@@ -293,3 +293,32 @@ def test_spreading_of_many_entries_matches_oracle(lblib):
     assert pop_rel_err(n, st.n) <= 1e-12
     ex, ev = bead_errs(x, v, st, case)
     assert ex <= 1e-12 and ev <= 1e-11
+
+
+def test_asynchronous_bead_read_back(lblib):
+    """lb_get_beads_async + lb_wait return what lb_get_beads returns, step after step, with
+    reads queued behind later steps; a ticket not yet issued is an argument error."""
+    import torch
+
+    case = Case(L=10, N=12, steps=0, seed=12)
+    a = gpu_sim(lblib, case, lblib.LB_FP32)
+    b = gpu_sim(lblib, case, lblib.LB_FP32)
+    a._bind()
+    bufs = [(torch.empty((12, 3), dtype=torch.float64, pin_memory=True).numpy(),
+             torch.empty((12, 3), dtype=torch.float64, pin_memory=True).numpy()) for _ in range(3)]
+    tickets, ref = [], {}
+    for k in range(9):
+        a.step(1)
+        tickets.append(lblib.lb_get_beads_async(a.ctx, bufs[k % 3][0], bufs[k % 3][1], 36))
+        b.step(1)
+        xr, vr = b.beads()
+        ref[k] = (xr.copy(), vr.copy())
+        if k >= 2:  # the read-back of step k-2 while steps k-1 and k are queued behind it
+            lblib.lb_wait(a.ctx, tickets[k - 2])
+            xo, vo = bufs[(k - 2) % 3]
+            assert np.array_equal(xo, ref[k - 2][0]) and np.array_equal(vo, ref[k - 2][1])
+    with pytest.raises(lblib.LBError) as ei:
+        lblib.lb_wait(a.ctx, len(tickets))
+    assert ei.value.code == lblib.LB_ERR_ARG
+    a.close()
+    b.close()
