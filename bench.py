@@ -314,6 +314,38 @@ def run_ours(args):
                  "hbm_frac": BYTES_PER_NODE["f32"] * nodes / (tb / kb) / 1e9 / measured_peaks()[0],
                  "workload": "64 replicas, L in {16,24,32,48,64}, N in {8,16,32,64}, FP32, graph-captured"}
 
+    # the same kernel without noise (fluid and beads): the memory-bound reference point; and
+    # the FP32 coupled step at L=256 (16.8 M nodes, 2.55 GB of populations) far above L2
+    variants = None
+    if not args.no_variants:
+        def timed_steps(sim, k):
+            sim.step(3)
+            sim.sync()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            sim.step(k)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            return a0.elapsed_time(a1) / 1e3 / k
+
+        sq = make(lb.LB_FP32)
+        sq.set_options(noise_fluid=0, noise_beads=0)
+        kq = max(20, args.steps // 5)
+        tq = timed_steps(sq, kq)
+        sq.close()
+        s256 = lb.Simulation(L=256, seed=seed, precision=lb.LB_FP32, **PARAMS)
+        s256.add_chain(N, x0=inputs.chain_walk(N, L=256, bond=0.97, seed=seed, self_avoiding=True), **CHAIN)
+        k256 = max(10, args.steps // 40)
+        t256 = timed_steps(s256, k256)
+        s256.close()
+        peak_q = measured_peaks()[0]
+        variants = {
+            "noise_off_L128": {"value": L ** 3 / tq / 1e6, "unit": "MLUPS", "ms_per_step": tq * 1e3, "steps": kq,
+                               "hbm_frac": BYTES_PER_NODE["f32"] * L ** 3 / tq / 1e9 / peak_q},
+            "L256": {"value": 256 ** 3 / t256 / 1e6, "unit": "MLUPS", "ms_per_step": t256 * 1e3, "steps": k256,
+                     "hbm_frac": BYTES_PER_NODE["f32"] * 256 ** 3 / t256 / 1e9 / peak_q},
+        }
+
     # chain observables (Sec. III A/B) on a recorded trajectory: 1000 frames of the N=128
     # chain in an L=32 box; each analysis kernel timed once after a warm-up call
     observ = None
@@ -408,6 +440,7 @@ def run_ours(args):
         "bead_steps_per_s": N * args.steps * ws / tmax,
         "batch_c4": batch,
         "observables_f3": observ,
+        "variants": variants,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "C ABI, pinned host buffers: set_populations, K x (step + asynchronous bead read-back, each waited for one step later), get_populations"},
         "gpu_launches": 2 * args.steps + 1,
@@ -429,6 +462,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-observables", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
