@@ -261,6 +261,30 @@ int lb_analysis_inverse_radius(const double* traj, int T, int N, double* out, vo
 int lb_analysis_dynamic_sk(const double* traj, int T, int N, const double* k, int nk, int max_lag,
                            int origin_stride, double* S, void* stream);
 
+/* --- Brownian dynamics with hydrodynamic interaction (Sec. II C) -----------------------------
+ * `replicas` independent chains of N beads in an infinite medium, advanced by the Ito-Euler
+ * update r += (D/kT) F dt + sqrt(2 dt) B.W with D/kT = zeta^-1 1 on the diagonal blocks and the
+ * regularised Rotne-Prager-Yamakawa tensor (Stokes radius zeta / (6 pi eta_s)) between beads
+ * (hi = 0: free draining), B.W from Fixman's Chebyshev expansion of sqrt(D) of the given
+ * degree (1..64) on spectral bounds from `power_iters` power iterations per step.  Forces:
+ * FENE bonds (k_fene, R0) and WCA (eps, sigma) between all pairs.  Units as given (the
+ * paper's comparison uses MD/LB units with zeta = zeta_eff, Sec. II D).  Noise: Philox4x32-10,
+ * key (seed, 3 | replica << 8), counter (step, bead, 0, 0).  x0: replicas x N x 3 doubles.
+ * precision: LB_FP64 (N <= 52) or LB_FP32 (N <= 74) arithmetic; positions are kept in FP64.
+ * The library allocates its device memory; work runs on the stream set with lb_bd_set_stream.
+ * lb_bd_get_beads copies all replicas' positions (replicas x N x 3) and synchronises; a FENE
+ * bond at or beyond R0 is reported as LB_ERR_FENE by lb_bd_sync and lb_bd_get_beads. */
+typedef struct lb_bd lb_bd;
+int lb_bd_create(lb_bd** out, int replicas, int N, double kT, double zeta, double eta_s, double dt,
+                 double k_fene, double R0, double eps, double sigma, int hi, int degree, int power_iters,
+                 uint64_t seed, const double* x0, int precision);
+int lb_bd_set_stream(lb_bd* b, void* stream);
+int lb_bd_step(lb_bd* b, int64_t n);
+int lb_bd_sync(lb_bd* b);
+int lb_bd_get_beads(lb_bd* b, double* x, size_t cap);
+int64_t lb_bd_get_step(lb_bd* b);
+void lb_bd_destroy(lb_bd* b);
+
 /* --- allocation-free variant ---------------------------------------------------------
  * Fluid mass and momentum of a population field, like lb_get_observables' entries [1] and
  * [5..7], for callers that cannot allocate device memory where they need these sums: code

@@ -53,6 +53,15 @@ _SIGS = {
     "lb_analysis_static_sk": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_int, _vp, _vp]),
     "lb_analysis_dynamic_sk": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
     "lb_analysis_inverse_radius": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp]),
+    "lb_bd_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                               C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
+                               C.c_uint64, _dp, C.c_int]),
+    "lb_bd_set_stream": (C.c_int, [_vp, _vp]),
+    "lb_bd_step": (C.c_int, [_vp, C.c_int64]),
+    "lb_bd_sync": (C.c_int, [_vp]),
+    "lb_bd_get_beads": (C.c_int, [_vp, _dp, C.c_size_t]),
+    "lb_bd_get_step": (C.c_int64, [_vp]),
+    "lb_bd_destroy": (None, [_vp]),
     "lb_reset_reference": (C.c_int, [_vp]),
     "lb_save": (C.c_int, [_vp, C.c_char_p]),
     "lb_load": (C.c_int, [_vp, C.c_char_p]),
@@ -521,3 +530,91 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+# --- Brownian dynamics (Sec. II C) --------------------------------------------------------
+def lb_bd_create(replicas, N, kT, zeta, eta_s, dt, k_fene, R0, eps, sigma, hi, degree, power_iters, seed, x0,
+                 precision):
+    b = _vp()
+    x = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1)
+    if x.size != replicas * N * 3:
+        raise ValueError("x0 must hold replicas x N x 3 positions")
+    _check(_lib.lb_bd_create(C.byref(b), int(replicas), int(N), kT, zeta, eta_s, dt, k_fene, R0, eps, sigma,
+                             int(hi), int(degree), int(power_iters), int(seed), _dbuf(x), int(precision)),
+           "lb_bd_create")
+    return b
+
+
+def lb_bd_set_stream(b, stream):
+    _check(_lib.lb_bd_set_stream(b, stream), "lb_bd_set_stream")
+
+
+def lb_bd_step(b, n):
+    _check(_lib.lb_bd_step(b, int(n)), "lb_bd_step")
+
+
+def lb_bd_sync(b):
+    _check(_lib.lb_bd_sync(b), "lb_bd_sync")
+
+
+def lb_bd_get_beads(b, out: np.ndarray):
+    _check(_lib.lb_bd_get_beads(b, _dbuf(out), out.size), "lb_bd_get_beads")
+
+
+def lb_bd_get_step(b) -> int:
+    return _lib.lb_bd_get_step(b)
+
+
+def lb_bd_destroy(b):
+    _lib.lb_bd_destroy(b)
+
+
+class BD:
+    """Brownian-dynamics chains with hydrodynamic interaction (Sec. II C) on the current CUDA
+    device, on torch's current stream.  Parameters in the units the caller chooses; the
+    defaults are the paper's production chain in MD/LB units with zeta = zeta_eff (Sec. II D)
+    and the time step 0.005 tau_k."""
+
+    def __init__(self, x0, kT=1.2, zeta=None, eta_s=0.864 * 2.8, dt=None, k_fene=7.0, R0=2.0, eps=1.0, sigma=1.0,
+                 hi=True, degree=20, power_iters=20, seed=1, precision=LB_FP32):
+        import torch
+
+        x0 = np.asarray(x0, dtype=np.float64)
+        if x0.ndim == 2:
+            x0 = x0[None]
+        self.R, self.N = x0.shape[0], x0.shape[1]
+        if zeta is None:
+            zeta = zeta_eff(20.8, eta_s)
+        if dt is None:
+            dt = 0.005 * zeta / (4.0 * k_fene)
+        self.b = lb_bd_create(self.R, self.N, kT, zeta, eta_s, dt, k_fene, R0, eps, sigma, int(hi), degree,
+                              power_iters, seed, x0, precision)
+        lb_bd_set_stream(self.b, torch.cuda.current_stream().cuda_stream)
+
+    def step(self, n=1):
+        lb_bd_step(self.b, n)
+
+    def sync(self):
+        lb_bd_sync(self.b)
+
+    def beads(self) -> np.ndarray:
+        out = np.empty((self.R, self.N, 3))
+        lb_bd_get_beads(self.b, out)
+        return out
+
+    def close(self):
+        if self.b:
+            lb_bd_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def zeta_eff(zeta_bare: float, eta_s: float, a: float = 1.0, g: float = 25.0) -> float:
+    """Long-time friction of a point particle coupled to the LB fluid (Sec. II D): 1/zeta_eff =
+    1/zeta_bare + 1/(g eta_s a), g ~ 25 for linear interpolation to the nearest nodes."""
+    return 1.0 / (1.0 / zeta_bare + 1.0 / (g * eta_s * a))

@@ -134,3 +134,14 @@ def test_inverse_radius_validates_arguments(lblib):
         with pytest.raises(lblib.LBError) as ei:
             call()
         assert ei.value.code == lblib.LB_ERR_ARG
+
+
+def test_bd_create_validates_arguments(lblib):
+    x = np.zeros((1, 4, 3))
+    base = dict(replicas=1, N=4, kT=1.2, zeta=15.5, eta_s=2.4, dt=0.003, k_fene=7.0, R0=2.0, eps=1.0, sigma=1.0,
+                hi=1, degree=20, power_iters=20, seed=1, x0=x, precision=lblib.LB_FP32)
+    for bad in (dict(degree=0), dict(degree=65), dict(power_iters=0), dict(kT=0.0), dict(precision=2),
+                dict(N=80, x0=np.zeros((1, 80, 3))), dict(N=53, x0=np.zeros((1, 53, 3)), precision=lblib.LB_FP64)):
+        with pytest.raises(lblib.LBError) as ei:
+            lblib.lb_bd_create(**dict(base, **bad))
+        assert ei.value.code == lblib.LB_ERR_ARG, bad
