@@ -8,8 +8,8 @@
 //   - k_batch_bead: one thread block per replica's chain; it releases the LB kernel of the
 //     same step at its start (programmatic dependent launch, one stream),
 //   - k_batch_lb: a tile table over all replicas' nodes, persistent thread blocks walking it;
-//     tiles stamped by the previous step's bead kernel add its force corrections to what
-//     they pull, the bead kernel adds them to its gathers,
+//     nodes marked by the previous step's bead kernel add its force corrections to what they
+//     pull, the bead kernel adds them to its gathers,
 //   - k_batch_apply: the last step's force corrections, once at the end of each call.
 // Step indices come from a device counter so that a captured CUDA graph of G steps (G even)
 // can be replayed; the tile size and the number of persistent blocks are chosen by a
@@ -77,7 +77,7 @@ struct BatchLB {
   FluidK<R> P;
   int nrep;
   unsigned long long total_tiles;
-  const int* flags[2];           // per 32-node segment: the step that last stamped it, by slot
+  const unsigned* mask[2];       // marks of the nodes that pull from pending nodes, by slot
   unsigned long long* counter;   // this group's two tile counters (by step parity)
   BatchRep<S, R> rep[kBatchGroup];
   RoundKeys rk[kBatchGroup];
@@ -114,10 +114,10 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 3 : 1) k_batch_lb(const 
       const unsigned long long n0 = (tile - rp.tile0) * T;
       const unsigned long long node = n0 + threadIdx.x;
       if (node < rp.nnodes) {
-        // a node of a segment stamped by the previous step adds that step's corrections to what
-        // it pulls (replicas without a chain have no correction field and are never stamped)
+        // a node marked by the previous step adds that step's corrections to what it pulls
+        // (replicas without a chain have no correction field and are never marked)
         const bool stamped = rp.p_dense[pslot] != nullptr &&
-                             B.flags[pslot][rp.seg0 + ((unsigned)node >> kSegShift)] == (int)(step - 1u);
+                             ((B.mask[pslot][rp.seg0 + ((unsigned)node >> kSegShift)] >> ((unsigned)node & 31u)) & 1u);
         const unsigned L = rp.L;
         unsigned x, y;
         const unsigned t = div_small((unsigned)node, L, rp.invL, x);
@@ -138,11 +138,11 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 3 : 1) k_batch_lb(const 
   }
 }
 
-// One 256-thread block per replica's chain: its registers (about 86 per thread) leave room
-// on its SM for a full complement of LB blocks.  Block 0 also zeroes the tile counters the
-// next step's LB launches will use.
+// One 256-thread block per replica's chain: in FP32 at most 80 registers per thread, which
+// leaves room on its SM for four 256-thread LB blocks.  Block 0 also zeroes the tile
+// counters the next step's LB launches will use.
 template <class S, class R, bool DEV>
-__global__ void __launch_bounds__(256) k_batch_bead(const ReplicaK<S, R>* __restrict__ reps, int parity,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_batch_bead(const ReplicaK<S, R>* __restrict__ reps, int parity,
                                                      const uint32_t* __restrict__ d_step, uint32_t j,
                                                      unsigned long long* __restrict__ counters, int ngroups) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -165,8 +165,6 @@ __global__ void __launch_bounds__(256) k_batch_bead(const ReplicaK<S, R>* __rest
   const uint32_t step = *d_step + j;
   PendK<R> Pd = rp.pd[parity];
   Pd.have_prev = 1;  // an empty list after a flush
-  Pd.cur_stamp = (int)step;
-  Pd.prev_stamp = (int)(step - 1u);
   bead_step_block<S, R, DEV>(rp.pop[parity], sP, sC, Pd, step, smem);
 }
 
@@ -187,10 +185,12 @@ __global__ void __launch_bounds__(256) k_batch_apply(const ReplicaK<S, R>* __res
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= *pd.cur_count) return;
   const int i = blockIdx.y;
-  const unsigned long long off = (unsigned long long)i * rp.P.plane + (unsigned)pd.cur_pos[u].x;
+  const int4 q = pd.cur_pos[u];
+  const unsigned long long off = (unsigned long long)i * rp.P.plane + (unsigned)q.x;
   S* p = rp.pop[buf] + off;
   st<S, R>(p, ld<S, R>(p) + pd.cur_dn[i * pd.cap + u]);
   pd.cur_dense[off] = R(0);
+  if (i == 0) clear_marks(pd.cur_mask, pd.seg0, (int)rp.P.L, q.y, q.z, q.w);
 }
 
 class Batch {
@@ -216,12 +216,12 @@ class BatchT final : public Batch {
       offs_.push_back(off);
       off += e->workspace_bytes();
     }
-    // stamps: one int per 32-node segment of every replica, two slots
+    // marks: one 32-bit word per 32 nodes of every replica, two slots
     max_segs_ = 0;
     for (auto& e : eng_) max_segs_ += (e->nodes() + 31) >> kSegShift;
     off = align_up(off, 256);
     flags_off_ = off;
-    off += 2 * max_segs_ * sizeof(int);
+    off += 2 * max_segs_ * sizeof(unsigned);
     off = align_up(off, 256);
     counters_off_ = off;
     off += 2 * (cfgs.size() / kBatchGroup + 1) * sizeof(unsigned long long);
@@ -244,7 +244,7 @@ class BatchT final : public Batch {
     base_ = static_cast<unsigned char*>(base);
     for (size_t r = 0; r < eng_.size(); ++r) eng_[r]->bind(base_ + offs_[r]);
     d_reps_ = reinterpret_cast<ReplicaK<S, R>*>(base_ + table_off_);
-    flags_[0] = reinterpret_cast<int*>(base_ + flags_off_);
+    flags_[0] = reinterpret_cast<unsigned*>(base_ + flags_off_);
     flags_[1] = flags_[0] + max_segs_;
     counters_ = reinterpret_cast<unsigned long long*>(base_ + counters_off_);
     d_step_ = reinterpret_cast<uint32_t*>(base_ + step_off_);
@@ -263,7 +263,7 @@ class BatchT final : public Batch {
     cap_max_ = 8;
     for (auto& e : eng_) cap_max_ = e->pending_capacity() > cap_max_ ? e->pending_capacity() : cap_max_;
     // the engines zeroed their pending counts; no tile carries a stamp a step can match
-    cuda_check(cudaMemsetAsync(flags_[0], 0xfe, 2 * max_segs_ * sizeof(int), s), "memset stamps");
+    cuda_check(cudaMemsetAsync(flags_[0], 0, 2 * max_segs_ * sizeof(unsigned), s), "memset marks");
     const size_t lbsm = (size_t)Q * 512 * sizeof(R);
     if (lbsm > 48 * 1024) {  // FP64: staged corrections of a 512-node run
       cuda_check(cudaFuncSetAttribute(k_batch_lb<S, R, DEV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -323,8 +323,6 @@ class BatchT final : public Batch {
       for (int b : cand_b) {
         if (b > 0 && b * t > 2048) continue;
         set_shape(t, b);
-        // fresh stamps for every trial (the step counter restarts at 0)
-        cuda_check(cudaMemsetAsync(flags_[0], 0xfe, 2 * max_segs_ * sizeof(int), s), "memset stamps");
         upload_table(s);
         k_set_step<<<1, 1, 0, s>>>(d_step_, 0);
         for (int w = 0; w < 2; ++w) launch_step(s, 0, true);
@@ -392,14 +390,15 @@ class BatchT final : public Batch {
       q.has_chain = eng_[r]->chain_length() > 0;
       for (int jj = 0; jj < 2; ++jj) {
         PendK<R>& pd = q.pd[jj];
-        pd.prev_flags = flags_[jj ^ 1];
+        pd.prev_mask = flags_[jj ^ 1];
         pd.prev_dense = eng_[r]->pending_dense(jj ^ 1);
         pd.cur_dense = eng_[r]->pending_dense(jj);
         pd.plane = eng_[r]->plane();
         pd.cur_pos = eng_[r]->pending_pos(jj);
         pd.cur_dn = eng_[r]->pending_dn(jj);
         pd.cur_count = eng_[r]->pending_count(jj);
-        pd.cur_flags = flags_[jj];
+        pd.cur_mask = flags_[jj];
+        pd.mark = 1;
         pd.cap = eng_[r]->pending_capacity();
         pd.seg0 = (unsigned)segs;
       }
@@ -416,8 +415,8 @@ class BatchT final : public Batch {
       unsigned long long tt = 0;
       const size_t g1 = g0 + kBatchGroup < eng_.size() ? g0 + kBatchGroup : eng_.size();
       G.nrep = (int)(g1 - g0);
-      G.flags[0] = flags_[0];
-      G.flags[1] = flags_[1];
+      G.mask[0] = flags_[0];
+      G.mask[1] = flags_[1];
       G.counter = counters_ + 2 * groups_.size();
       for (size_t r = g0; r < g1; ++r) {
         BatchRep<S, R>& q = G.rep[r - g0];
@@ -502,7 +501,7 @@ class BatchT final : public Batch {
   size_t table_off_ = 0, step_off_ = 0, flags_off_ = 0, counters_off_ = 0, bytes_ = 0, smem_ = 0;
   unsigned long long* counters_ = nullptr;
   size_t max_segs_ = 0;
-  int* flags_[2] = {nullptr, nullptr};
+  unsigned* flags_[2] = {nullptr, nullptr};  // node marks by slot
   unsigned char* base_ = nullptr;
   ReplicaK<S, R>* d_reps_ = nullptr;
   uint32_t* d_step_ = nullptr;

@@ -113,29 +113,29 @@ struct ChainK {
 // Force corrections in flight between consecutive steps of a multi-step run.  The bead kernel
 // of step k writes them twice: as a list (node, 19 deltas) for the final flush, and into a
 // dense correction field of the population layout [i][plane] that is zero except at pending
-// nodes; it also stamps every segment of 32 consecutive nodes (linear index / 32) holding a
-// node that pulls from a corrected node.  The LB kernel of step k+1 adds the dense field to
-// what it pulls at the nodes of stamped segments, and the bead kernel of step k+1 to what it
-// gathers.  Two slots alternate by step; a bead kernel first clears its slot's
-// entries from two steps before (its old list), and a flush clears the entries it applies.
+// nodes; it also marks, in a bit mask over the nodes (one 32-bit word per 32 consecutive
+// linear indices), every node that pulls from a corrected node.  The LB kernel of step k+1
+// adds the dense field to what it pulls at marked nodes, and the bead kernel of step k+1 to
+// what it gathers.  Two slots alternate by step; a bead kernel first clears its slot's dense
+// entries and mask words of the list from two steps before, and a flush clears what it
+// applies.
 template <class R>
 struct PendK {
   int have_prev;          // 0: nothing pending (the stored populations are complete)
-  int prev_stamp;
-  const int* prev_flags;  // per LB tile: the step that last stamped it
+  const unsigned* prev_mask;  // nodes that pull from the previous step's corrected nodes
   const R* prev_dense;    // the previous step's corrections, dense
   int4* cur_pos;          // this step's list: {node, x, y, z}
   R* cur_dn;              // 19 deltas [i][cap]
   int* cur_count;
   R* cur_dense;           // this step's slot of the dense field
-  int* cur_flags;         // nullptr: do not stamp
-  int cur_stamp;
+  unsigned* cur_mask;     // this step's slot of the mask (cleared of the old list)
+  int mark;               // 1: mark the pulling nodes of this step's list (deferred steps)
   int cap;
   unsigned long long plane;  // element stride between the 19 planes
-  unsigned seg0;             // index of this box's first segment in the stamp arrays
+  unsigned seg0;             // index of this box's first word in the mask arrays
 };
 
-constexpr int kSegShift = 5;  // stamp segments of 32 consecutive nodes
+constexpr int kSegShift = 5;  // mask words of 32 consecutive nodes
 
 // ---------------------------------------------------------------------------------------
 // moment algebra
@@ -485,9 +485,9 @@ __device__ __forceinline__ void stage_corrections(const R* __restrict__ corr, un
 }
 
 // One LB tile: pull-stream + collide for the (blockDim.x x blockDim.y) nodes at
-// (tx, ty, z) (Sec. II B, Eq. 3).  A node in a segment stamped by the previous deferred step
-// adds that step's corrections to the populations it pulls (staged per thread in shared
-// memory, 19 x blockDim.x x blockDim.y values).
+// (tx, ty, z) (Sec. II B, Eq. 3).  A node marked by the previous deferred step adds that
+// step's corrections to the populations it pulls (staged per thread in shared memory,
+// 19 x blockDim.x x blockDim.y values).
 template <class S, class R, bool DEV, bool NOISE>
 __device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
                                         const PendK<R>& Pd, const uint32_t step, unsigned tx, unsigned ty,
@@ -499,7 +499,7 @@ __device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict
   const unsigned node = x + L * (y + L * z);
   // two inlined copies of the update: the common one carries no correction code (one shared
   // copy with a runtime branch measured 6 % slower)
-  if (Pd.have_prev && Pd.prev_flags[Pd.seg0 + (node >> kSegShift)] == Pd.prev_stamp) {
+  if (Pd.have_prev && ((Pd.prev_mask[Pd.seg0 + (node >> kSegShift)] >> (node & 31u)) & 1u)) {
     const unsigned T = blockDim.x * blockDim.y, tid = threadIdx.x + blockDim.x * threadIdx.y;
     stage_corrections<R>(Pd.prev_dense, Pd.plane, L, x, y, z, stage + tid, T);
     lb_node_update<S, R, DEV, NOISE>(src, dst, P, P.L, P.plane, P.rk, P.nonpos, step, x, y, z, stage + tid, T);
@@ -718,7 +718,7 @@ __device__ __forceinline__ void gather_node(const S* __restrict__ pop, const Flu
 // The pending correction of one node (the coupling of Sec. II B, spread back to the fluid): the sum
 // of its entries' reactions in entry order (ent(base) .. ent(base + cnt - 1) ascending),
 // turned into population corrections at pending-list index u, written to the list and the
-// dense field, and the LB tiles pulling from the node stamped.
+// dense field, and the nodes pulling from it marked.
 template <class R, class Ent>
 __device__ __forceinline__ void node_correction(const FluidK<R>& P, const ChainK<R>& C, const PendK<R>& Pd, int L,
                                                 int N, int u, int node, Ent ent, int base, int cnt) {
@@ -758,19 +758,32 @@ __device__ __forceinline__ void node_correction(const FluidK<R>& P, const ChainK
     Pd.cur_dn[q * Pd.cap + u] = dn[q];
     Pd.cur_dense[(unsigned long long)q * Pd.plane + (unsigned)node] = dn[q];
   }
-  if (Pd.cur_flags) {  // stamp the segments of the nodes that pull from this node
+  if (Pd.mark) {  // mark the nodes that pull from this node
     // neighbour coordinates [c + 1] for c = -1, 0, +1 (periodic)
     const int xs[3] = {px ? px - 1 : L - 1, px, px + 1 < L ? px + 1 : 0};
     const int ys[3] = {py ? py - 1 : L - 1, py, py + 1 < L ? py + 1 : 0};
     const int zs[3] = {pz ? pz - 1 : L - 1, pz, pz + 1 < L ? pz + 1 : 0};
-    unsigned last = 0xffffffffu;  // skip repeats of the segment just stamped
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const unsigned idx = (unsigned)xs[cx(q) + 1] + (unsigned)L * ((unsigned)ys[cy(q) + 1] + (unsigned)L * (unsigned)zs[cz(q) + 1]);
-      const unsigned seg = Pd.seg0 + (idx >> kSegShift);
-      if (seg != last) Pd.cur_flags[seg] = Pd.cur_stamp;
-      last = seg;
+      atomicOr(&Pd.cur_mask[Pd.seg0 + (idx >> kSegShift)], 1u << (idx & 31u));
     }
+  }
+}
+
+// Clear the mask words of the nodes that pull from node (px, py, pz) (whole words: in its slot
+// a word holds marks of one list only)
+__device__ __forceinline__ void clear_marks(unsigned* mask, unsigned seg0, int L, int px, int py, int pz) {
+  const int xs[3] = {px ? px - 1 : L - 1, px, px + 1 < L ? px + 1 : 0};
+  const int ys[3] = {py ? py - 1 : L - 1, py, py + 1 < L ? py + 1 : 0};
+  const int zs[3] = {pz ? pz - 1 : L - 1, pz, pz + 1 < L ? pz + 1 : 0};
+  unsigned last = 0xffffffffu;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const unsigned idx = (unsigned)xs[cx(q) + 1] + (unsigned)L * ((unsigned)ys[cy(q) + 1] + (unsigned)L * (unsigned)zs[cz(q) + 1]);
+    const unsigned w = seg0 + (idx >> kSegShift);
+    if (w != last) mask[w] = 0u;
+    last = w;
   }
 }
 
@@ -793,9 +806,11 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
   {
     const int old = *Pd.cur_count;
     for (int u = tid; u < old; u += nt) {
-      R* d = Pd.cur_dense + (unsigned)Pd.cur_pos[u].x;
+      const int4 p = Pd.cur_pos[u];
+      R* d = Pd.cur_dense + (unsigned)p.x;
 #pragma unroll
       for (int i = 0; i < Q; ++i) d[(unsigned long long)i * Pd.plane] = R(0);
+      if (Pd.cur_mask) clear_marks(Pd.cur_mask, Pd.seg0, L, p.y, p.z, p.w);
     }
   }
   const R* corr = Pd.have_prev ? Pd.prev_dense : nullptr;
@@ -1071,20 +1086,23 @@ __global__ void __launch_bounds__(512) k_bead_step(const S* __restrict__ pop, co
 }
 
 // B[i][node] += dn_i at every pending node (each node appears once in the list), and the
-// applied entries of the dense correction field back to zero; one thread per (node,
-// population): blockIdx.y is the population
+// applied entries of the dense correction field and the list's mask words (mask may be null)
+// back to zero; one thread per (node, population): blockIdx.y is the population
 template <class S, class R>
 __global__ void __launch_bounds__(256) k_apply_pending(S* __restrict__ pop, const FluidK<R> P,
                                                         const int4* __restrict__ p_pos,
                                                         const R* __restrict__ p_dn,
                                                         const int* __restrict__ p_count, int cap,
-                                                        R* __restrict__ dense) {
+                                                        R* __restrict__ dense, unsigned* __restrict__ mask,
+                                                        unsigned seg0) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= *p_count) return;
   const int i = blockIdx.y;
-  const unsigned long long off = (unsigned long long)i * P.plane + (unsigned)p_pos[u].x;
+  const int4 p = p_pos[u];
+  const unsigned long long off = (unsigned long long)i * P.plane + (unsigned)p.x;
   st<S, R>(pop + off, ld<S, R>(pop + off) + p_dn[i * cap + u]);
   dense[off] = R(0);
+  if (mask && i == 0) clear_marks(mask, seg0, (int)P.L, p.y, p.z, p.w);
 }
 
 // one trajectory frame: unwrapped positions x + xl + img * box in FP64, in the order (and

@@ -87,7 +87,8 @@ class EngineT final : public Engine {
       cuda_check(cudaMemsetAsync(p_count_[j], 0, sizeof(int), s), "memset pending");
       if (corr_[j]) cuda_check(cudaMemsetAsync(corr_[j], 0, (size_t)Q * plane_ * sizeof(R), s), "memset corrections");
     }
-    reset_stamps(s);
+    for (int j = 0; j < 2; ++j)
+      cuda_check(cudaMemsetAsync(masks_[j], 0, nsegs() * sizeof(unsigned), s), "memset marks");
   }
 
   // One coupled step, complete on return: the bead kernel (one CTA), then the LB kernel,
@@ -116,7 +117,6 @@ class EngineT final : public Engine {
       step(k, s, ev0, ev1);
       return;
     }
-    if (!open_ && stamp_ > (1 << 30)) reset_stamps(s);
     const FluidK<R> P = fluid();
     const S* A = pop_[cur_];
     S* Bo = pop_[cur_ ^ 1];
@@ -124,7 +124,6 @@ class EngineT final : public Engine {
     const PendK<R> Pd = pend(true);
     launch_bead(A, P, Pd, k, s);
     launch_lb(A, Bo, P, Pd, k, s, ev0, ev1);
-    ++stamp_;
     open_ = true;
     cur_ ^= 1;
   }
@@ -499,7 +498,8 @@ class EngineT final : public Engine {
 
   void apply(S* buf, const FluidK<R>& P, int slot, cudaStream_t s) {
     k_apply_pending<S, R><<<dim3((cap_ + 255) / 256, Q), 256, 0, s>>>(buf, P, p_pos_[slot], p_dn_[slot],
-                                                                     p_count_[slot], cap_, corr_[slot]);
+                                                                     p_count_[slot], cap_, corr_[slot],
+                                                                     masks_[slot], 0u);
     cuda_check(cudaGetLastError(), "apply kernel");
   }
 
@@ -510,25 +510,18 @@ class EngineT final : public Engine {
     memset(&Pd, 0, sizeof(Pd));
     const int c = pslot_, p = pslot_ ^ 1;
     Pd.have_prev = (deferred && open_) ? 1 : 0;
-    Pd.prev_stamp = stamp_ - 1;
-    Pd.prev_flags = flags_[p];
+    Pd.prev_mask = masks_[p];
     Pd.prev_dense = corr_[p];
     Pd.cur_dense = corr_[c];
     Pd.plane = plane_;
     Pd.cur_pos = p_pos_[c];
     Pd.cur_dn = p_dn_[c];
     Pd.cur_count = p_count_[c];
-    Pd.cur_flags = deferred ? flags_[c] : nullptr;
-    Pd.cur_stamp = stamp_;
+    Pd.cur_mask = masks_[c];
+    Pd.mark = deferred ? 1 : 0;
     Pd.cap = cap_;
     Pd.seg0 = 0;
     return Pd;
-  }
-
-  void reset_stamps(cudaStream_t s) {
-    for (int j = 0; j < 2; ++j)
-      cuda_check(cudaMemsetAsync(flags_[j], 0xff, nsegs() * sizeof(int), s), "memset stamps");
-    stamp_ = 0;
   }
 
   size_t nsegs() const { return (size_t)((nnodes_ + 31) >> kSegShift); }
@@ -708,7 +701,7 @@ class EngineT final : public Engine {
       p_pos_[j] = reinterpret_cast<int4*>(take(cap_ * sizeof(int4)));
       p_dn_[j] = reinterpret_cast<R*>(take((size_t)Q * cap_ * sizeof(R)));
       p_count_[j] = reinterpret_cast<int*>(take(sizeof(int)));
-      flags_[j] = reinterpret_cast<int*>(take(nsegs() * sizeof(int)));
+      masks_[j] = reinterpret_cast<unsigned*>(take(nsegs() * sizeof(unsigned)));
       corr_[j] = N_ > 0 ? reinterpret_cast<R*>(take((size_t)Q * plane_ * sizeof(R))) : nullptr;
     }
     status_ = reinterpret_cast<unsigned*>(take(sizeof(unsigned)));
@@ -735,9 +728,9 @@ class EngineT final : public Engine {
   int4* p_pos_[2] = {nullptr, nullptr};
   R* p_dn_[2] = {nullptr, nullptr};
   int* p_count_[2] = {nullptr, nullptr};
-  int* flags_[2] = {nullptr, nullptr};  // per 32-node segment: the last deferred step that stamped it
+  unsigned* masks_[2] = {nullptr, nullptr};  // marks of the nodes that pull from pending nodes, by slot
   R* corr_[2] = {nullptr, nullptr};     // dense correction fields [i][plane], zero but at pending nodes
-  int pslot_ = 0, stamp_ = 0;
+  int pslot_ = 0;
   bool open_ = false;  // a deferred step's correction is pending
   unsigned* status_ = nullptr;
   unsigned long long* nonpos_ = nullptr;
