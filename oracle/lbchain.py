@@ -190,23 +190,43 @@ def uniform01(x: np.ndarray) -> np.ndarray:
 
 
 def box_muller(u0: np.ndarray, u1: np.ndarray):
-    """Box & Muller (1958): two independent standard normals from two uniforms."""
+    """Box & Muller (1958): two independent standard normals from two uniforms, the angle
+    taken in (-pi, pi): r = sqrt(-2 ln u0), theta = 2 pi (u1 - 1/2)."""
     r = np.sqrt(-2.0 * np.log(u0))
-    return r * np.cos(2.0 * np.pi * u1), r * np.sin(2.0 * np.pi * u1)
+    theta = 2.0 * np.pi * (u1 - 0.5)
+    return r * np.cos(theta), r * np.sin(theta)
 
 
-def gaussians16(seed, tag, replica, step, index):
-    """16 standard normals per index from 4 Philox calls with counter (step, index, call, 0):
-    call c yields g[4c..4c+3] (Box-Muller on (u0,u1) and (u2,u3))."""
+FLUID_CALLS = 3
+
+
+def fluid_uniforms(seed, tag, replica, step, index, ncalls=FLUID_CALLS):
+    """(6 ncalls, ...) uniforms per index.  Call c (counter (step, index, c, 0)) gives four
+    words, read as a 128-bit string (word j holds bits 32j .. 32j+31, least significant
+    first); uniform 6c + i takes its bits 21i .. 21i+20 as the integer k: u = (k + 1/2) 2^-21."""
     k0, k1 = philox_key(seed, tag, replica)
     index = np.asarray(index, dtype=np.uint64)
     out = []
-    for call in range(4):
-        x = philox4x32_10(np.uint64(step) & _MASK, index, np.uint64(call), np.uint64(0), k0, k1)
-        u = [uniform01(v) for v in x]
-        g0, g1 = box_muller(u[0], u[1])
-        g2, g3 = box_muller(u[2], u[3])
-        out += [g0, g1, g2, g3]
+    for call in range(ncalls):
+        w = [v.astype(np.uint64) for v in
+             philox4x32_10(np.uint64(step) & _MASK, index, np.uint64(call), np.uint64(0), k0, k1)]
+        for i in range(6):
+            q, s = divmod(21 * i, 32)
+            two = w[q] | ((w[q + 1] << np.uint64(32)) if q < 3 else np.uint64(0))
+            k = (two >> np.uint64(s)) & np.uint64(0x1FFFFF)
+            out.append((k.astype(np.float64) + 0.5) * 2.0 ** -21)
+    return np.array(out)
+
+
+def fluid_gaussians(seed, tag, replica, step, index):
+    """18 standard normals per index: pair p = 0..8 is Box-Muller on the uniforms (2p, 2p+1)
+    of fluid_uniforms.  Mode k = 4..18 takes g[k - 4]; the stress modes 4..9 thus depend on
+    the first call only."""
+    u = fluid_uniforms(seed, tag, replica, step, index)
+    out = []
+    for p in range(9):
+        g0, g1 = box_muller(u[2 * p], u[2 * p + 1])
+        out += [g0, g1]
     return np.array(out)
 
 
@@ -284,7 +304,7 @@ def collide(n: np.ndarray, fp: FluidParams, step: int, force_density=None, repli
         mstar[k] = meq[k] + gam[k] * (m[k] - meq[k])
     if fp.noise_fluid and fp.kT > 0.0:
         mu = mu_thermal(fp)
-        g = gaussians16(fp.seed, TAG_FLUID, replica, step, np.arange(L ** 3))
+        g = fluid_gaussians(fp.seed, TAG_FLUID, replica, step, np.arange(L ** 3))
         rho_pos = np.where(rho > 0.0, rho, 0.0)
         if stats is not None:
             stats["nonpositive_rho"] = stats.get("nonpositive_rho", 0) + int((rho <= 0.0).sum())
@@ -554,7 +574,7 @@ def node_update(npost: np.ndarray, fp: FluidParams, step_k: int, node, force=Non
     if fp.noise_fluid and fp.kT > 0.0:
         mu = mu_thermal(fp)
         idx = x + L * (y + L * z)
-        g = gaussians16(fp.seed, TAG_FLUID, replica, step_k, np.array([idx]))[:, 0]
+        g = fluid_gaussians(fp.seed, TAG_FLUID, replica, step_k, np.array([idx]))[:, 0]
         kmax = 10 if fp.stress_only else Q
         for kk in range(4, kmax):
             ms[kk] += math.sqrt(mu * max(rho, 0.0) * B[kk] * (1.0 - gam[kk] ** 2)) * g[kk - 4]

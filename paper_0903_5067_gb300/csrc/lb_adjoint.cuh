@@ -175,19 +175,9 @@ __global__ void __launch_bounds__(256) k_adj_lb(const S* __restrict__ state, con
   mb[3] += (R(2) * jz * Eb[4] - R(2) * jz * Eb[5] - R(2) * jz * Eb[6] + jy * Eb[8] + jx * Eb[9]) * ir;
   if (NOISE && rho > R(0)) {
     // a_k += ag_k sqrt(rho) g_k:  d/drho = ag_k g_k / (2 sqrt(rho))
-    R g[4], acc = R(0);
-    const R one = R(1);
-    gauss4_rk<R>(step, node, 0u, P.rk, one, g);
-    acc += P.ag[4] * g[0] * ab[4] + P.ag[5] * g[1] * ab[5] + P.ag[6] * g[2] * ab[6] + P.ag[7] * g[3] * ab[7];
-    gauss4_rk<R>(step, node, 1u, P.rk, one, g);
-    acc += P.ag[8] * g[0] * ab[8] + P.ag[9] * g[1] * ab[9];
-    if (P.ncalls > 2) {
-      acc += P.ag[10] * g[2] * ab[10] + P.ag[11] * g[3] * ab[11];
-      gauss4_rk<R>(step, node, 2u, P.rk, one, g);
-      acc += P.ag[12] * g[0] * ab[12] + P.ag[13] * g[1] * ab[13] + P.ag[14] * g[2] * ab[14] + P.ag[15] * g[3] * ab[15];
-      gauss4_rk<R>(step, node, 3u, P.rk, one, g);
-      acc += P.ag[16] * g[0] * ab[16] + P.ag[17] * g[1] * ab[17] + P.ag[18] * g[2] * ab[18];
-    }
+    R acc = R(0);
+    fluid_noise<R>(step, node, P.rk, P.ncalls > 1, NoiseScale<R>(R(1)),
+                   [&](int j, R g) { acc += P.ag[4 + j] * g * ab[4 + j]; });
     mb[0] += acc * R(0.5) / sqrt(rho);
   }
   // nbar_ps,i = sum_k e_k(c_i) mb_k, pushed to r - e_i

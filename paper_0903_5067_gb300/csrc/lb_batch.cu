@@ -125,11 +125,11 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 3 : 1) k_batch_lb(const 
         if (stamped) {  // two inlined copies: the common one carries no correction code
           R* col = reinterpret_cast<R*>(dsm) + threadIdx.x;
           stage_corrections<R>(rp.p_dense[pslot], rp.plane, L, x, y, z, col, T);
-          lb_node_update<S, R, DEV, NOISE>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r],
-                                           rp.nonpos, step, x, y, z, col, T);
+          lb_node_update<S, R, DEV, NOISE, unsigned>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r],
+                                                     rp.nonpos, step, x, y, z, col, T);
         } else {
-          lb_node_update<S, R, DEV, NOISE>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r],
-                                           rp.nonpos, step, x, y, z);
+          lb_node_update<S, R, DEV, NOISE, unsigned>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r],
+                                                     rp.nonpos, step, x, y, z);
         }
       }
     }

@@ -41,16 +41,12 @@ __device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat16* p, float
 template <>
 __device__ __forceinline__ void st<__half, float>(__half* p, float v) { *p = __float2half_rn(v); }
 
-// 1/x and sqrt(x) for the LB kernel: hardware reciprocal / reciprocal square root in single
-// precision (2 ulp), correctly rounded operations in double
+// 1/rho for the LB kernel: the hardware reciprocal in single precision (1 ulp; the density is
+// a normal number), correctly rounded division in double
 template <class R>
 __device__ __forceinline__ R lb_rcp(R x) { return R(1) / x; }
 template <>
-__device__ __forceinline__ float lb_rcp<float>(float x) { return __fdividef(1.0f, x); }
-template <class R>
-__device__ __forceinline__ R lb_sqrt_pos(R x) { return sqrt(x); }
-template <>
-__device__ __forceinline__ float lb_sqrt_pos<float>(float x) { return x * rsqrtf(x); }
+__device__ __forceinline__ float lb_rcp<float>(float x) { return approx_rcp(x); }
 
 // ---------------------------------------------------------------------------------------
 // kernel parameter blocks (passed by value)
@@ -70,7 +66,7 @@ struct FluidK {
   R wam[Q], wae[Q], wag[Q];
   uint32_t k0, k1; // Philox key of the fluid stream
   RoundKeys rk;    // its ten round keys
-  int ncalls;      // Philox calls per node: 0 (noise off), 2 (stress modes only), 4 (all)
+  int ncalls;      // Philox calls per node: 0 (noise off), 1 (stress modes only), 3 (all)
   int body_on;     // uniform body force
   R body_dJ[3];    // lattice momentum it adds per step and node: f h^2 / a
   unsigned long long* nonpos;  // counter of non-positive densities met by the noise
@@ -349,7 +345,9 @@ __host__ __device__ __forceinline__ void pops_from_w2scaled(const R a[Q], R n[Q]
 // collide, write the 19 post-collision populations of node (x, y, z) to dst.
 // (L, plane, rk, nonpos: the box's size, plane stride, noise keys and counter, which the
 // batched kernel takes per replica; P: the remaining, shared parameters)
-template <class S, class R, bool DEV, bool NOISE>
+// I: the type of element offsets within the population array (unsigned when all 19 planes fit
+// in 32 bits, which makes each address one wide multiply-add)
+template <class S, class R, bool DEV, bool NOISE, class I = unsigned long long>
 __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
                                                const unsigned L, const unsigned long long plane,
                                                const RoundKeys& rk, unsigned long long* nonpos,
@@ -365,11 +363,12 @@ __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __r
   const unsigned rz[3] = {zp * LL, z * LL, zm * LL};
   const unsigned sxs[3] = {xp, x, xm};
 
+  const I pl = (I)plane;
   R n[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const unsigned idx = sxs[cx(i) + 1] + ry[cy(i) + 1] + rz[cz(i) + 1];
-    n[i] = ld<S, R>(src + (unsigned long long)i * plane + idx);
+    n[i] = ld<S, R>(src + ((I)i * pl + (I)idx));
   }
   if (dcol) {  // the previous step's corrections at the pulled nodes, staged by the caller
 #pragma unroll
@@ -406,34 +405,9 @@ __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __r
   for (int k = 10; k < Q; ++k) a[k] = R(0);
 
   if (NOISE) {
-    R sr = R(0);
-    if (rho > R(0)) {
-      sr = lb_sqrt_pos<R>(rho);
-    } else {
-      atomicAdd(nonpos, 1ull);
-    }
-    R g[4];  // sqrt(rho) g
-    gauss4_rk<R>(step, node, 0u, rk, sr, g);
-    a[4] += P.wag[4] * g[0];
-    a[5] += P.wag[5] * g[1];
-    a[6] += P.wag[6] * g[2];
-    a[7] += P.wag[7] * g[3];
-    gauss4_rk<R>(step, node, 1u, rk, sr, g);
-    a[8] += P.wag[8] * g[0];
-    a[9] += P.wag[9] * g[1];
-    if (P.ncalls > 2) {
-      a[10] = P.wag[10] * g[2];
-      a[11] = P.wag[11] * g[3];
-      gauss4_rk<R>(step, node, 2u, rk, sr, g);
-      a[12] = P.wag[12] * g[0];
-      a[13] = P.wag[13] * g[1];
-      a[14] = P.wag[14] * g[2];
-      a[15] = P.wag[15] * g[3];
-      gauss4_rk<R>(step, node, 3u, rk, sr, g);
-      a[16] = P.wag[16] * g[0];
-      a[17] = P.wag[17] * g[1];
-      a[18] = P.wag[18] * g[2];
-    }
+    if (!(rho > R(0))) atomicAdd(nonpos, 1ull);
+    fluid_noise<R>(step, node, rk, P.ncalls > 1, NoiseScale<R>(rho),
+                   [&](int j, R g) { a[4 + j] += P.wag[4 + j] * g; });
   }
 
   if (P.body_on) {
@@ -453,7 +427,7 @@ __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __r
   R out[Q];
   pops_from_w2scaled<R>(a, out);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) st<S, R>(dst + (unsigned long long)i * plane + node, out[i]);
+  for (int i = 0; i < Q; ++i) st<S, R>(dst + ((I)i * pl + (I)node), out[i]);
 }
 
 // Stage the previous step's corrections at the 19 pull sources of node (x, y, z) into
@@ -488,7 +462,7 @@ __device__ __forceinline__ void stage_corrections(const R* __restrict__ corr, un
 // (tx, ty, z) (Sec. II B, Eq. 3).  A node marked by the previous deferred step adds that
 // step's corrections to the populations it pulls (staged per thread in shared memory,
 // 19 x blockDim.x x blockDim.y values).
-template <class S, class R, bool DEV, bool NOISE>
+template <class S, class R, bool DEV, bool NOISE, class I>
 __device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
                                         const PendK<R>& Pd, const uint32_t step, unsigned tx, unsigned ty,
                                         unsigned z, R* stage) {
@@ -502,18 +476,18 @@ __device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict
   if (Pd.have_prev && ((Pd.prev_mask[Pd.seg0 + (node >> kSegShift)] >> (node & 31u)) & 1u)) {
     const unsigned T = blockDim.x * blockDim.y, tid = threadIdx.x + blockDim.x * threadIdx.y;
     stage_corrections<R>(Pd.prev_dense, Pd.plane, L, x, y, z, stage + tid, T);
-    lb_node_update<S, R, DEV, NOISE>(src, dst, P, P.L, P.plane, P.rk, P.nonpos, step, x, y, z, stage + tid, T);
+    lb_node_update<S, R, DEV, NOISE, I>(src, dst, P, P.L, P.plane, P.rk, P.nonpos, step, x, y, z, stage + tid, T);
   } else {
-    lb_node_update<S, R, DEV, NOISE>(src, dst, P, P.L, P.plane, P.rk, P.nonpos, step, x, y, z);
+    lb_node_update<S, R, DEV, NOISE, I>(src, dst, P, P.L, P.plane, P.rk, P.nonpos, step, x, y, z);
   }
 }
 
 // LB kernel: 3D grid of (x-row segments) x (y rows) x z planes
-template <class S, class R, bool DEV, bool NOISE>
+template <class S, class R, bool DEV, bool NOISE, class I>
 __global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* __restrict__ dst,
                                                   const FluidK<R> P, const PendK<R> Pd, const uint32_t step) {
   extern __shared__ __align__(16) unsigned char lsm[];
-  lb_tile<S, R, DEV, NOISE>(src, dst, P, Pd, step, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<R*>(lsm));
+  lb_tile<S, R, DEV, NOISE, I>(src, dst, P, Pd, step, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<R*>(lsm));
 }
 
 // ---------------------------------------------------------------------------------------

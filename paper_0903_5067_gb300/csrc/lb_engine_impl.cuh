@@ -36,12 +36,10 @@ class EngineT final : public Engine {
 
   void initialise(const double* x0, const double* v0, cudaStream_t s) override {
     if ((size_t)Q * 256 * sizeof(R) > 48 * 1024) {  // FP64: staged corrections of a 256-node tile
-      cuda_check(cudaFuncSetAttribute(k_lb_step<S, R, DEV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(Q * 256 * sizeof(R))),
-                 "LB kernel shared memory");
-      cuda_check(cudaFuncSetAttribute(k_lb_step<S, R, DEV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(Q * 256 * sizeof(R))),
-                 "LB kernel shared memory");
+      for (int v = 0; v < 4; ++v)
+        cuda_check(cudaFuncSetAttribute(lb_kernel(v & 1, v >> 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(Q * 256 * sizeof(R))),
+                   "LB kernel shared memory");
     }
     if (bead_smem() > 48 * 1024)
       cuda_check(cudaFuncSetAttribute(k_bead_step<S, R, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -488,10 +486,7 @@ class EngineT final : public Engine {
     lc.attrs = at;
     lc.numAttrs = N_ > 0 ? 1 : 0;
     if (ev0) cudaEventRecord(ev0, s);
-    if (P.ncalls > 0)
-      cuda_check(cudaLaunchKernelEx(&lc, k_lb_step<S, R, DEV, true>, A, Bo, P, Pd, k), "LB kernel");
-    else
-      cuda_check(cudaLaunchKernelEx(&lc, k_lb_step<S, R, DEV, false>, A, Bo, P, Pd, k), "LB kernel");
+    cuda_check(cudaLaunchKernelEx(&lc, lb_kernel(P.ncalls > 0, narrow_offsets()), A, Bo, P, Pd, k), "LB kernel");
     if (ev1) cudaEventRecord(ev1, s);
     cuda_check(cudaGetLastError(), "LB kernel");
   }
@@ -525,6 +520,15 @@ class EngineT final : public Engine {
   }
 
   size_t nsegs() const { return (size_t)((nnodes_ + 31) >> kSegShift); }
+
+  // the LB kernel for noise on/off and 32-bit (all 19 planes below 2^32 elements) or 64-bit
+  // element offsets
+  using LbKernel = void (*)(const S*, S*, const FluidK<R>, const PendK<R>, const uint32_t);
+  static LbKernel lb_kernel(bool noise, bool narrow) {
+    if (noise) return narrow ? k_lb_step<S, R, DEV, true, unsigned> : k_lb_step<S, R, DEV, true, unsigned long long>;
+    return narrow ? k_lb_step<S, R, DEV, false, unsigned> : k_lb_step<S, R, DEV, false, unsigned long long>;
+  }
+  bool narrow_offsets() const { return (unsigned long long)Q * plane_ <= 0xFFFFFFFFull; }
 
   void lb_launch_shape(dim3& blk, dim3& grd) const {
     unsigned bx = ((unsigned)L_ + 31) / 32 * 32;
@@ -566,7 +570,7 @@ class EngineT final : public Engine {
     P.gs = (R)gs;
     P.gb = (R)gb;
     const bool noise = c.noise_fluid && c.kT > 0.0;
-    P.ncalls = noise ? (c.stress_only ? 2 : 4) : 0;
+    P.ncalls = noise ? (c.stress_only ? 1 : 3) : 0;
     const double mu = 3.0 * c.kT * c.h * c.h / pow(c.a, 5);
     for (int k = 0; k < Q; ++k) {
       double g = 0.0;

@@ -88,20 +88,51 @@ def test_uniform_transform_is_exact_in_float32_and_open():
     assert np.array_equal(o.uniform01((k << np.uint64(9)).astype(np.uint32)), (k + 0.5) * 2.0 ** -23)
 
 
+def test_box_muller_special_angles_and_radius():
+    """u0 = exp(-1/2) gives radius 1; the angle 2 pi (u1 - 1/2) is 0, pi/2 and -pi/2 at
+    u1 = 1/2, 3/4 and 1/4."""
+    u0 = np.full(3, np.exp(-0.5))
+    g0, g1 = o.box_muller(u0, np.array([0.5, 0.75, 0.25]))
+    assert np.allclose(g0, [1.0, 0.0, 0.0], atol=1e-15)
+    assert np.allclose(g1, [0.0, 1.0, -1.0], atol=1e-15)
+
+
+def test_fluid_uniforms_cut_each_call_into_six_21_bit_fields():
+    """Against the 128-bit string of each call built as one Python integer."""
+    idx = np.array([0, 1, 77, 2 ** 21 + 5, 2 ** 32 - 1], dtype=np.uint64)
+    u = o.fluid_uniforms(9, o.TAG_FLUID, 3, 41, idx)
+    assert u.shape == (18, idx.size)
+    k0, k1 = o.philox_key(9, o.TAG_FLUID, 3)
+    for c in range(3):
+        w = o.philox4x32_10(41, idx, c, 0, k0, k1)
+        for n in range(idx.size):
+            big = sum(int(w[j][n]) << (32 * j) for j in range(4))
+            for i in range(6):
+                k = (big >> (21 * i)) & (2 ** 21 - 1)
+                assert u[6 * c + i, n] == (k + 0.5) / 2 ** 21
+    assert np.all(u > 0) and np.all(u < 1)
+    # exact in single precision: k + 1/2 needs 22 significant bits
+    assert np.array_equal(u.astype(np.float32).astype(np.float64), u)
+
+
 def test_box_muller_is_standard_normal():
-    g = o.gaussians16(seed=3, tag=o.TAG_FLUID, replica=0, step=11, index=np.arange(20000))
+    g = o.fluid_gaussians(seed=3, tag=o.TAG_FLUID, replica=0, step=11, index=np.arange(20000))
+    assert g.shape == (18, 20000)
     flat = g.reshape(-1)
     assert stats.kstest(flat, "norm").pvalue > 1e-3
     assert abs(flat.mean()) < 4 / np.sqrt(flat.size)
     assert abs(flat.var() - 1) < 4 * np.sqrt(2 / flat.size)
     c = np.corrcoef(g[:, :5000])
-    assert np.max(np.abs(c - np.eye(16))) < 0.07
+    assert np.max(np.abs(c - np.eye(18))) < 0.07
+    # the pair angles are uniform on (-pi, pi)
+    ang = np.arctan2(g[1::2], g[0::2]).reshape(-1)
+    assert stats.kstest(ang, "uniform", args=(-np.pi, 2 * np.pi)).pvalue > 1e-3
 
 
 def test_noise_streams_depend_on_every_key_and_counter_field():
-    base = o.gaussians16(1, o.TAG_FLUID, 0, 5, np.arange(8))
+    base = o.fluid_gaussians(1, o.TAG_FLUID, 0, 5, np.arange(8))
     for args in [(2, o.TAG_FLUID, 0, 5), (1, o.TAG_BEAD, 0, 5), (1, o.TAG_FLUID, 1, 5), (1, o.TAG_FLUID, 0, 6)]:
-        assert not np.allclose(o.gaussians16(*args, np.arange(8)), base)
+        assert not np.allclose(o.fluid_gaussians(*args, np.arange(8)), base)
 
 
 def _equilibrium_run(L, nsteps, warm, fp, every=2):
