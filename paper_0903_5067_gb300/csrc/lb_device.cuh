@@ -70,6 +70,8 @@ struct FluidK {
   int body_on;     // uniform body force
   R body_dJ[3];    // lattice momentum it adds per step and node: f h^2 / a
   unsigned long long* nonpos;  // counter of non-positive densities met by the noise
+  int pdl;         // launch chaining of the LB kernel: bit 0 waits for the previous grid before
+                   // reading, bit 1 waits for it before completing (see k_lb_step)
 };
 
 template <class R>
@@ -341,41 +343,12 @@ __host__ __device__ __forceinline__ void pops_from_w2scaled(const R a[Q], R n[Q]
 // ---------------------------------------------------------------------------------------
 // LB kernel: pull-stream + collide for every node (Sec. II B, Eq. 3)
 // ---------------------------------------------------------------------------------------
-// One node of the LB step: pull the 19 populations from the neighbours in src (periodic),
-// collide, write the 19 post-collision populations of node (x, y, z) to dst.
-// (L, plane, rk, nonpos: the box's size, plane stride, noise keys and counter, which the
-// batched kernel takes per replica; P: the remaining, shared parameters)
-// I: the type of element offsets within the population array (unsigned when all 19 planes fit
-// in 32 bits, which makes each address one wide multiply-add)
-template <class S, class R, bool DEV, bool NOISE, class I = unsigned long long>
-__device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
-                                               const unsigned L, const unsigned long long plane,
-                                               const RoundKeys& rk, unsigned long long* nonpos,
-                                               const uint32_t step, const unsigned x, const unsigned y,
-                                               const unsigned z, const R* __restrict__ dcol = nullptr,
-                                               unsigned dstride = 0) {
-  const unsigned xm = x ? x - 1 : L - 1, xp = (x + 1 < L) ? x + 1 : 0;
-  const unsigned ym = y ? y - 1 : L - 1, yp = (y + 1 < L) ? y + 1 : 0;
-  const unsigned zm = z ? z - 1 : L - 1, zp = (z + 1 < L) ? z + 1 : 0;
-  const unsigned LL = L * L;
-  // row offsets of the source rows: [dy+1][dz+1] for a pull from y - dy, z - dz
-  const unsigned ry[3] = {yp * L, y * L, ym * L};
-  const unsigned rz[3] = {zp * LL, z * LL, zm * LL};
-  const unsigned sxs[3] = {xp, x, xm};
-
-  const I pl = (I)plane;
-  R n[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const unsigned idx = sxs[cx(i) + 1] + ry[cy(i) + 1] + rz[cz(i) + 1];
-    n[i] = ld<S, R>(src + ((I)i * pl + (I)idx));
-  }
-  if (dcol) {  // the previous step's corrections at the pulled nodes, staged by the caller
-#pragma unroll
-    for (int i = 0; i < Q; ++i) n[i] += dcol[i * dstride];
-  }
-  const unsigned node = x + y * L + z * LL;
-
+// Collide the 19 pulled populations n of one node (Sec. II B, Eq. 3) and write its 19
+// post-collision populations to dst (element offset i * pl + node for population i).
+template <class S, class R, bool DEV, bool NOISE, class I>
+__device__ __forceinline__ void lb_collide_store(const R* n, S* __restrict__ dst, const FluidK<R>& P, const I pl,
+                                                 const RoundKeys& rk, unsigned long long* nonpos,
+                                                 const uint32_t step, const unsigned node) {
   // moments 0..9 (the kinetic modes relax to zero and are not needed)
   R m[10];
   moments_0_9<R>(n, m);
@@ -430,6 +403,42 @@ __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __r
   for (int i = 0; i < Q; ++i) st<S, R>(dst + ((I)i * pl + (I)node), out[i]);
 }
 
+// One node of the LB step: pull the 19 populations from the neighbours in src (periodic),
+// collide, write the 19 post-collision populations of node (x, y, z) to dst.
+// (L, plane, rk, nonpos: the box's size, plane stride, noise keys and counter, which the
+// batched kernel takes per replica; P: the remaining, shared parameters)
+// I: the type of element offsets within the population array (unsigned when all 19 planes fit
+// in 32 bits, which makes each address one wide multiply-add)
+template <class S, class R, bool DEV, bool NOISE, class I = unsigned long long>
+__device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
+                                               const unsigned L, const unsigned long long plane,
+                                               const RoundKeys& rk, unsigned long long* nonpos,
+                                               const uint32_t step, const unsigned x, const unsigned y,
+                                               const unsigned z, const R* __restrict__ dcol = nullptr,
+                                               unsigned dstride = 0) {
+  const unsigned xm = x ? x - 1 : L - 1, xp = (x + 1 < L) ? x + 1 : 0;
+  const unsigned ym = y ? y - 1 : L - 1, yp = (y + 1 < L) ? y + 1 : 0;
+  const unsigned zm = z ? z - 1 : L - 1, zp = (z + 1 < L) ? z + 1 : 0;
+  const unsigned LL = L * L;
+  // row offsets of the source rows: [dy+1][dz+1] for a pull from y - dy, z - dz
+  const unsigned ry[3] = {yp * L, y * L, ym * L};
+  const unsigned rz[3] = {zp * LL, z * LL, zm * LL};
+  const unsigned sxs[3] = {xp, x, xm};
+
+  const I pl = (I)plane;
+  R n[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const unsigned idx = sxs[cx(i) + 1] + ry[cy(i) + 1] + rz[cz(i) + 1];
+    n[i] = ld<S, R>(src + ((I)i * pl + (I)idx));
+  }
+  if (dcol) {  // the previous step's corrections at the pulled nodes, staged by the caller
+#pragma unroll
+    for (int i = 0; i < Q; ++i) n[i] += dcol[i * dstride];
+  }
+  lb_collide_store<S, R, DEV, NOISE, I>(n, dst, P, pl, rk, nonpos, step, x + y * L + z * LL);
+}
+
 // Stage the previous step's corrections at the 19 pull sources of node (x, y, z) into
 // col[i * stride] (shared memory).  A rolled loop with the directions unpacked from constants
 // (this rare path must not raise the register count of the LB kernels), issuing asynchronous
@@ -482,11 +491,31 @@ __device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict
   }
 }
 
-// LB kernel: 3D grid of (x-row segments) x (y rows) x z planes
+// Programmatic dependent launch (a grid launched with programmatic stream serialization may
+// start before the previous grid in the stream has completed): `wait` blocks until that
+// previous grid has completed and its writes are visible; `release` lets the next grid start.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// LB kernel: 3D grid of (x-row segments) x (y rows) x z planes, plus (when it follows the
+// bead kernel of its step) one more plane of blocks that only wait.  Every grid releases the
+// next one at once.  Launched after the previous LB kernel (no chain): it waits for that grid
+// before reading (P.pdl bit 0), so that only the launch latency and block scheduling overlap.
+// Launched after the bead kernel of the same step: it reads nothing that kernel writes and
+// runs beside it; the blocks of plane z = L, scheduled last, wait for it (bit 1), so that the
+// grid completes only after the bead kernel and whatever comes next may take this grid's
+// completion for both.  (A wait at the end of every block raised the register count.)
 template <class S, class R, bool DEV, bool NOISE, class I>
 __global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* __restrict__ dst,
                                                   const FluidK<R> P, const PendK<R> Pd, const uint32_t step) {
   extern __shared__ __align__(16) unsigned char lsm[];
+  if (blockIdx.z >= P.L) {  // a waiting block
+    allow_dependent_launch();
+    if (P.pdl & 2) grid_dependency_wait();
+    return;
+  }
+  if (P.pdl & 1) grid_dependency_wait();
+  allow_dependent_launch();
   lb_tile<S, R, DEV, NOISE, I>(src, dst, P, Pd, step, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<R*>(lsm));
 }
 
@@ -1045,16 +1074,15 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
   }
 }
 
-// Lets the next kernel in the stream, when launched with programmatic stream serialization
-// (the LB kernel of the same step), start while this grid still runs.
-__device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-// The bead step as its own one-CTA grid.  The LB kernel of the same step reads neither its
-// outputs nor anything it writes, so it is released at once and runs alongside.
+// The bead step as its own one-CTA grid.  Launched with programmatic stream serialization
+// after the previous step's LB kernel (which completes only after the previous bead kernel),
+// it waits for that grid before reading; then it releases the LB kernel of the same step,
+// which reads neither its outputs nor anything it writes and runs alongside.
 template <class S, class R, bool DEV>
 __global__ void __launch_bounds__(512) k_bead_step(const S* __restrict__ pop, const FluidK<R> P,
                                                     const ChainK<R> C, const PendK<R> Pd, const uint32_t step) {
   extern __shared__ __align__(16) unsigned char smem[];
+  grid_dependency_wait();
   allow_dependent_launch();
   bead_step_block<S, R, DEV>(pop, P, C, Pd, step, smem);
 }

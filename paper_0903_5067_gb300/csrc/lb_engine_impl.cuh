@@ -98,7 +98,7 @@ class EngineT final : public Engine {
     const S* A = pop_[cur_];
     S* Bo = pop_[cur_ ^ 1];
     const PendK<R> Pd = pend(false);
-    if (N_ > 0) launch_bead(A, P, Pd, k, s);
+    if (N_ > 0) launch_bead(A, P, Pd, k, s, ev0 == nullptr);
     launch_lb(A, Bo, P, Pd, k, s, ev0, ev1);
     if (N_ > 0) apply(Bo, P, pslot_, s);
     cur_ ^= 1;
@@ -120,7 +120,7 @@ class EngineT final : public Engine {
     S* Bo = pop_[cur_ ^ 1];
     if (open_) pslot_ ^= 1;
     const PendK<R> Pd = pend(true);
-    launch_bead(A, P, Pd, k, s);
+    launch_bead(A, P, Pd, k, s, ev0 == nullptr);
     launch_lb(A, Bo, P, Pd, k, s, ev0, ev1);
     open_ = true;
     cur_ ^= 1;
@@ -460,22 +460,39 @@ class EngineT final : public Engine {
     return p;
   }
 
-  void launch_bead(const S* A, const FluidK<R>& P, const PendK<R>& Pd, uint32_t k, cudaStream_t s) {
-    k_bead_step<S, R, DEV><<<1, 512, bead_smem(), s>>>(A, P, chain(), Pd, k);
+  // Bead kernel of step k: with `chained`, launched with programmatic stream serialization
+  // (it waits for the previous grid before reading, so only its launch overlaps).
+  void launch_bead(const S* A, const FluidK<R>& P, const PendK<R>& Pd, uint32_t k, cudaStream_t s, bool chained) {
+    cudaLaunchConfig_t lc;
+    memset(&lc, 0, sizeof(lc));
+    lc.gridDim = dim3(1);
+    lc.blockDim = dim3(512);
+    lc.dynamicSmemBytes = bead_smem();
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = chained ? 1 : 0;
+    cuda_check(cudaLaunchKernelEx(&lc, k_bead_step<S, R, DEV>, A, P, chain(), Pd, k), "bead kernel");
     cuda_check(cudaGetLastError(), "bead kernel");
   }
 
-  // LB kernel.  After the bead kernel of the same step it is launched with programmatic
-  // stream serialization and may start once the bead kernel has signalled (at its start); the
-  // LB kernel reads nothing the bead kernel writes.  Otherwise (no chain) it is an ordinary
-  // launch, which waits for the previous step's LB kernel to complete.  Timing events, when
-  // given, bracket it.
-  void launch_lb(const S* A, S* Bo, const FluidK<R>& P, const PendK<R>& Pd, uint32_t k, cudaStream_t s,
+  // LB kernel, launched with programmatic stream serialization.  After the bead kernel of the
+  // same step it may start once the bead kernel has signalled (at its start; the LB kernel
+  // reads nothing the bead kernel writes) and waits for it before completing.  Without a
+  // chain it follows the previous LB kernel and waits for that grid before reading.  Timing
+  // events, when given, bracket it, and then every launch is an ordinary one.
+  void launch_lb(const S* A, S* Bo, const FluidK<R>& P0, const PendK<R>& Pd, uint32_t k, cudaStream_t s,
                  cudaEvent_t ev0, cudaEvent_t ev1) {
+    FluidK<R> P = P0;
+    const bool chained = ev0 == nullptr;
+    P.pdl = chained ? (N_ > 0 ? 2 : 1) : 0;
     dim3 blk, grd;
     lb_launch_shape(blk, grd);
     cudaLaunchConfig_t lc;
     memset(&lc, 0, sizeof(lc));
+    if (P.pdl & 2) grd.z += 1;  // the plane of waiting blocks
     lc.gridDim = grd;
     lc.blockDim = blk;
     lc.dynamicSmemBytes = Pd.have_prev ? (size_t)Q * blk.x * blk.y * sizeof(R) : 0;  // staged corrections
@@ -484,7 +501,7 @@ class EngineT final : public Engine {
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = at;
-    lc.numAttrs = N_ > 0 ? 1 : 0;
+    lc.numAttrs = chained ? 1 : 0;
     if (ev0) cudaEventRecord(ev0, s);
     cuda_check(cudaLaunchKernelEx(&lc, lb_kernel(P.ncalls > 0, narrow_offsets()), A, Bo, P, Pd, k), "LB kernel");
     if (ev1) cudaEventRecord(ev1, s);

@@ -251,8 +251,8 @@ def test_md_substeps_with_paper_parameters(lblib):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_deferred_corrections_are_bit_exact(lblib, case, prec):
     """Consecutive steps keep each step's bead force correction pending and add it where the
-    next step reads the populations (LB kernel at the nodes of stamped segments, bead gather
-    from the dense correction field).  In FP64 and FP32 that is the same arithmetic as
+    next step reads the populations (LB kernel at the marked nodes, bead gather from the dense
+    correction field).  In FP64 and FP32 that is the same arithmetic as
     applying it at the end of every step: K deferred steps and K steps each completed by a
     read of the fluid agree bit for bit."""
     p = getattr(lblib, "LB_" + prec.upper())
@@ -270,6 +270,30 @@ def test_deferred_corrections_are_bit_exact(lblib, case, prec):
     b.close()
     assert np.array_equal(na, nb)
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+@pytest.mark.parametrize("N", [0, 24], ids=["fluid", "chain"])
+def test_chained_and_ordinary_launches_agree_bit_for_bit(lblib, N):
+    """Without timing, consecutive kernels are chained by programmatic dependent launch (each
+    grid released at the start of the one before it, waiting for it before it reads; the LB
+    kernel beside the bead kernel of its step waits for it before completing).  With
+    lb_set_timing every launch is an ordinary one.  The two give the same state bit for bit."""
+    case = Case(L=24, N=N, steps=25, seed=12)
+    a = gpu_sim(lblib, case, lblib.LB_FP32)
+    a.step(case.steps)
+    na = a.populations()
+    b = gpu_sim(lblib, case, lblib.LB_FP32)
+    lblib.lb_set_timing(b.ctx, True)
+    b.step(case.steps)
+    lblib.lb_set_timing(b.ctx, False)
+    nb = b.populations()
+    assert np.array_equal(na, nb)
+    if N:
+        xa, va = a.beads()
+        xb, vb = b.beads()
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    a.close()
+    b.close()
 
 
 def test_deferred_corrections_with_observable_stride(lblib):
