@@ -567,20 +567,22 @@ __device__ __forceinline__ R pair_coef(R r2, bool bonded, const ChainK<R>& C, un
   return coef;
 }
 
-// Conservative forces (FENE + WCA + external) on every bead from positions staged in shared
-// memory; `lanes` threads per bead split the partners and combine in a fixed shuffle tree.
+// Conservative forces (FENE + WCA + external) on the beads bb0 .. bb1-1 from the positions of
+// all beads staged in shared memory; `lanes` threads per bead split the partners and combine
+// in a fixed shuffle tree.
 template <class R>
 __device__ __forceinline__ void chain_forces_block(const R* __restrict__ sh, const R* __restrict__ sl,
-                                                   const ChainK<R>& C, R* __restrict__ out) {
+                                                   const ChainK<R>& C, R* __restrict__ out, const int bb0,
+                                                   const int bb1) {
   const int N = C.N, nt = blockDim.x * blockDim.y, tid = threadIdx.x + blockDim.x * threadIdx.y;
   int lanes = 1;
-  while (lanes < 32 && lanes * 2 * N <= nt) lanes *= 2;
+  while (lanes < 32 && lanes * 2 * (bb1 - bb0) <= nt) lanes *= 2;
   const int per = nt / lanes;
   const int lane = tid % lanes;
-  for (int base = 0; base < N; base += per) {
+  for (int base = bb0; base < bb1; base += per) {
     const int b = base + tid / lanes;
     R f[3] = {R(0), R(0), R(0)};
-    if (b < N) {
+    if (b < bb1) {
       for (int j = lane; j < N; j += lanes) {
         if (j == b) continue;
         const bool bonded = (j == b - 1) || (j == b + 1);
@@ -599,7 +601,7 @@ __device__ __forceinline__ void chain_forces_block(const R* __restrict__ sh, con
 #pragma unroll
       for (int q = 0; q < 3; ++q) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o, lanes);
     }
-    if (b < N && lane == 0) {
+    if (b < bb1 && lane == 0) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) out[3 * b + q] = f[q] + C.ext[q];
     }
@@ -790,25 +792,51 @@ __device__ __forceinline__ void clear_marks(unsigned* mask, unsigned seg0, int L
   }
 }
 
-// One coupled bead step for one chain, run by one thread block (any size, multiple of 32):
-// velocity Verlet, FENE/WCA, interpolation of the post-stream flow at the 8 corners, friction
-// + Langevin force, and the deterministic spreading of the reaction into a list of
-// per-node population corrections.  `smem` holds the positions (6N R), later the node
-// grouping table (or the sort keys), as sized by the host.
+// Generic address of the same shared-memory location in block 0 of the cluster
+template <class T>
+__device__ __forceinline__ const T* cluster_rank0(const T* p) {
+  unsigned long long d;
+  asm volatile("mapa.u64 %0, %1, 0;" : "=l"(d) : "l"(reinterpret_cast<unsigned long long>(p)));
+  return reinterpret_cast<const T*>(d);
+}
+
+// Barrier over the thread blocks of a cluster; release/acquire order every memory access
+// before it (shared, distributed shared and global) before every access after it.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// One coupled bead step for one chain: velocity Verlet, FENE/WCA, interpolation of the
+// post-stream flow at the 8 corners, friction + Langevin force, and the deterministic
+// spreading of the reaction into a list of per-node population corrections.  Run by one
+// thread block (any size, multiple of 32), or by the G blocks of a cluster (rank: this
+// block's): each block computes the drift of every bead into its shared memory and then
+// takes a contiguous share of the beads (forces, corners and gathers, friction), of the old
+// list (clearing) and of the new list's nodes (corrections); block 0 writes the positions
+// and groups the corner entries by node in its shared memory, which the others read.
+// Most of this work is scattered global memory traffic, which G blocks issue from G SMs.
+// `smem` holds the positions (6N R; with G > 1 also the half-step velocities and image
+// counters, 9N R + 3N int), later the node grouping table (or the sort keys, G = 1 only), as
+// sized by the host.
 template <class S, class R, bool DEV>
 __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const FluidK<R>& P, const ChainK<R>& C,
-                                                const PendK<R>& Pd, const uint32_t step, unsigned char* smem) {
+                                                const PendK<R>& Pd, const uint32_t step, unsigned char* smem,
+                                                const int rank = 0, const int G = 1) {
   const int N = C.N;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
   const int L = (int)P.L;
   const R h = C.h;
   R* sx = reinterpret_cast<R*>(smem);
   R* sl = sx + 3 * N;
+  R* svh = sl + 3 * N;                             // G > 1: half-step velocities
+  int* simg = reinterpret_cast<int*>(svh + 3 * N);  // G > 1: image counters
+  const R* vhp = G > 1 ? svh : C.vh;
+  const int b0 = rank * N / G, b1 = (rank + 1) * N / G;  // this block's beads
   // clear this slot's dense entries of its old list (two steps back, or already applied);
   // the new list overwrites the old one only in phase 5, after several barriers
   {
     const int old = *Pd.cur_count;
-    for (int u = tid; u < old; u += nt) {
+    for (int u = tid + rank * nt; u < old; u += G * nt) {
       const int4 p = Pd.cur_pos[u];
       R* d = Pd.cur_dense + (unsigned)p.x;
 #pragma unroll
@@ -846,20 +874,35 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
       hi -= C.box;
       ++im;
     }
-    C.vh[t] = vh;
-    C.x[t] = hi;
-    C.xl[t] = lo;
-    C.img[t] = im;
+    if (G == 1) {
+      C.vh[t] = vh;
+      C.x[t] = hi;
+      C.xl[t] = lo;
+      C.img[t] = im;
+    } else {
+      svh[t] = vh;
+      simg[t] = im;
+    }
     sx[t] = hi;
     sl[t] = lo;
   }
   __syncthreads();
+  if (G > 1) {
+    cluster_sync();  // every block has read the state of the previous (sub)step
+    if (rank == 0)
+      for (int t = tid; t < 3 * N; t += nt) {
+        C.vh[t] = svh[t];
+        C.x[t] = sx[t];
+        C.xl[t] = sl[t];
+        C.img[t] = simg[t];
+      }
+  }
 
   // 2. conservative forces at x': FENE on bonds, WCA on all pairs, minimum image
-  chain_forces_block<R>(sx, sl, C, C.fcons);
+  chain_forces_block<R>(sx, sl, C, C.fcons, b0, b1);
 
-  // 3. corners of every bead: cell, trilinear weight, post-stream rho and J at the node
-  for (int e0 = tid; e0 < 8 * N; e0 += nt) {
+  // 3. corners of the block's beads: cell, trilinear weight, post-stream rho and J at the node
+  for (int e0 = 8 * b0 + tid; e0 < 8 * b1; e0 += nt) {
     const int b = e0 >> 3, c = e0 & 7, e = eoff + e0;
     const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
     R fr[3];
@@ -885,7 +928,7 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
   __syncthreads();
 
   // 4. friction + Langevin force, second half kick
-  for (int b = tid; b < N; b += nt) {
+  for (int b = b0 + tid; b < b1; b += nt) {
     R ub[3] = {R(0), R(0), R(0)};
     for (int c = 0; c < 8; ++c) {
       const int e = eoff + 8 * b + c;
@@ -900,7 +943,7 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const int t = 3 * b + q;
-      const R vh = C.vh[t];
+      const R vh = vhp[t];
       const R fc = -C.zeta * (vh - ub[q] * C.u_scale) + C.amp * g[q];
       const R Ft = C.fcons[t] + fc;
       C.Fc[t] = fc;
@@ -910,6 +953,7 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
     }
   }
   __syncthreads();
+  if (G > 1) cluster_sync();  // every bead is done
   }  // substeps
 
   // 5. deterministic spreading: group the corner entries by node, sum each node's
@@ -929,97 +973,114 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
     int* eslot = lslot + H;                     // slot of each entry
     int* elist = eslot + ne;                    // entries grouped by slot
     int* wsum = elist + ne;                     // scan scratch: 2 x 32 warp totals, node count
-    for (int h = tid; h < H; h += nt) {
-      tkey[h] = -1;
-      tcnt[h] = 0;
-    }
-    __syncthreads();
-    for (int e = tid; e < ne; e += nt) {
-      const int node = C.e_node[e];
-      unsigned h = hash_node(node, (unsigned)H - 1);
-      for (int it = 0; it < H; ++it) {  // at most half full: a free slot or the node is found
-        const int old = atomicCAS(&tkey[h], -1, node);
-        if (old == -1 || old == node) break;
-        h = (h + 1) & (unsigned)(H - 1);
-      }
-      eslot[e] = (int)h;
-      atomicAdd(&tcnt[h], 1);
-    }
-    __syncthreads();
-    // exclusive scans over the slots, in slot order: list offsets and node numbers.  Each
-    // thread owns a contiguous run of slots; warp scans, then a scan of the warp totals.
-    {
-      const int per = (H + nt - 1) / nt;
-      const int h0 = tid * per < H ? tid * per : H, h1 = h0 + per < H ? h0 + per : H;
-      int sc = 0, sl = 0;
-      for (int h = h0; h < h1; ++h) {
-        sc += tcnt[h];
-        sl += tcnt[h] > 0;
-      }
-      int ic = sc, il = sl;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int yc = __shfl_up_sync(0xffffffffu, ic, o), yl = __shfl_up_sync(0xffffffffu, il, o);
-        if (lane >= o) {
-          ic += yc;
-          il += yl;
-        }
-      }
-      if (lane == 31) {
-        wsum[warp] = ic;
-        wsum[32 + warp] = il;
+    if (rank == 0) {  // block 0 groups the entries
+      for (int h = tid; h < H; h += nt) {
+        tkey[h] = -1;
+        tcnt[h] = 0;
       }
       __syncthreads();
-      if (warp == 0) {
-        const int vc = lane < nwarp ? wsum[lane] : 0, vl = lane < nwarp ? wsum[32 + lane] : 0;
-        int jc = vc, jl = vl;
+      for (int e = tid; e < ne; e += nt) {
+        const int node = C.e_node[e];
+        unsigned h = hash_node(node, (unsigned)H - 1);
+        for (int it = 0; it < H; ++it) {  // at most half full: a free slot or the node is found
+          const int old = atomicCAS(&tkey[h], -1, node);
+          if (old == -1 || old == node) break;
+          h = (h + 1) & (unsigned)(H - 1);
+        }
+        eslot[e] = (int)h;
+        atomicAdd(&tcnt[h], 1);
+      }
+      __syncthreads();
+      // exclusive scans over the slots, in slot order: list offsets and node numbers.  Each
+      // thread owns a contiguous run of slots; warp scans, then a scan of the warp totals.
+      {
+        const int per = (H + nt - 1) / nt;
+        const int h0 = tid * per < H ? tid * per : H, h1 = h0 + per < H ? h0 + per : H;
+        int sc = 0, sl = 0;
+        for (int h = h0; h < h1; ++h) {
+          sc += tcnt[h];
+          sl += tcnt[h] > 0;
+        }
+        int ic = sc, il = sl;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          const int yc = __shfl_up_sync(0xffffffffu, jc, o), yl = __shfl_up_sync(0xffffffffu, jl, o);
+          const int yc = __shfl_up_sync(0xffffffffu, ic, o), yl = __shfl_up_sync(0xffffffffu, il, o);
           if (lane >= o) {
-            jc += yc;
-            jl += yl;
+            ic += yc;
+            il += yl;
           }
         }
-        if (lane < nwarp) {
-          wsum[lane] = jc - vc;
-          wsum[32 + lane] = jl - vl;
-        }
         if (lane == 31) {
-          *Pd.cur_count = jl;
-          wsum[64] = jl;
+          wsum[warp] = ic;
+          wsum[32 + warp] = il;
+        }
+        __syncthreads();
+        if (warp == 0) {
+          const int vc = lane < nwarp ? wsum[lane] : 0, vl = lane < nwarp ? wsum[32 + lane] : 0;
+          int jc = vc, jl = vl;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int yc = __shfl_up_sync(0xffffffffu, jc, o), yl = __shfl_up_sync(0xffffffffu, jl, o);
+            if (lane >= o) {
+              jc += yc;
+              jl += yl;
+            }
+          }
+          if (lane < nwarp) {
+            wsum[lane] = jc - vc;
+            wsum[32 + lane] = jl - vl;
+          }
+          if (lane == 31) {
+            *Pd.cur_count = jl;
+            wsum[64] = jl;
+          }
+        }
+        __syncthreads();
+        int bc = wsum[warp] + ic - sc, bl = wsum[32 + warp] + il - sl;
+        for (int h = h0; h < h1; ++h) {
+          const int c = tcnt[h];
+          toff[h] = bc;
+          if (c > 0) lslot[bl] = h;
+          tcnt[h] = bc;  // fill cursor
+          bc += c;
+          bl += c > 0;
         }
       }
       __syncthreads();
-      int bc = wsum[warp] + ic - sc, bl = wsum[32 + warp] + il - sl;
-      for (int h = h0; h < h1; ++h) {
-        const int c = tcnt[h];
-        toff[h] = bc;
-        if (c > 0) lslot[bl] = h;
-        tcnt[h] = bc;  // fill cursor
-        bc += c;
-        bl += c > 0;
-      }
-    }
-    __syncthreads();
-    for (int e = tid; e < ne; e += nt) elist[atomicAdd(&tcnt[eslot[e]], 1)] = e;
-    __syncthreads();
-    const int nnode = wsum[64];
-    for (int u = tid; u < nnode; u += nt) {  // one thread per node, in list order
-      const int h = lslot[u];
-      const int base = toff[h], cnt = tcnt[h] - base;
-      for (int r = base + 1; r < base + cnt; ++r) {  // entry order (insertion sort of a short list)
-        const int e = elist[r];
-        int q = r - 1;
-        while (q >= base && elist[q] > e) {
-          elist[q + 1] = elist[q];
-          --q;
+      for (int e = tid; e < ne; e += nt) elist[atomicAdd(&tcnt[eslot[e]], 1)] = e;
+      __syncthreads();
+      for (int u = tid; u < wsum[64]; u += nt) {  // each node's entries in entry order
+        const int h = lslot[u];
+        const int base = toff[h], cnt = tcnt[h] - base;
+        for (int r = base + 1; r < base + cnt; ++r) {  // (insertion sort of a short list)
+          const int e = elist[r];
+          int q = r - 1;
+          while (q >= base && elist[q] > e) {
+            elist[q + 1] = elist[q];
+            --q;
+          }
+          elist[q + 1] = e;
         }
-        elist[q + 1] = e;
       }
-      node_correction<R>(P, C, Pd, L, N, u, tkey[h], [&](int r) { return elist[r]; }, base, cnt);
+    }  // block 0
+    __syncthreads();
+    if (G > 1) cluster_sync();  // block 0's table is complete
+    // the table of block 0, read by every block of the cluster (distributed shared memory)
+    const int* tk = G > 1 ? cluster_rank0(tkey) : tkey;
+    const int* to = G > 1 ? cluster_rank0(toff) : toff;
+    const int* tc = G > 1 ? cluster_rank0(tcnt) : tcnt;
+    const int* ls = G > 1 ? cluster_rank0(lslot) : lslot;
+    const int* el = G > 1 ? cluster_rank0(elist) : elist;
+    const int nnode = (G > 1 ? cluster_rank0(wsum) : wsum)[64];
+    const int u0 = rank * nnode / G, u1 = (rank + 1) * nnode / G;  // this block's nodes
+    for (int u = u0 + tid; u < u1; u += nt) {  // one thread per node, in list order
+      const int h = ls[u];
+      const int base = to[h], cnt = tc[h] - base;
+      node_correction<R>(P, C, Pd, L, N, u, tk[h], [&](int r) { return el[r]; }, base, cnt);
     }
-  } else {
+    if (G > 1) cluster_sync();  // block 0's table is read until here
+  } else {  // (one block: the host launches G = 1 beyond kGroupHashMax entries)
+    if (rank != 0) return;
     int M = 32;  // at least one warp-wide chunk; padding keys sort to the end
     while (M < ne) M <<= 1;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem);
@@ -1074,17 +1135,21 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
   }
 }
 
-// The bead step as its own one-CTA grid.  Launched with programmatic stream serialization
+// The bead step as its own grid.  Launched with programmatic stream serialization
 // after the previous step's LB kernel (which completes only after the previous bead kernel),
 // it waits for that grid before reading; then it releases the LB kernel of the same step,
 // which reads neither its outputs nor anything it writes and runs alongside.
+// The grid is one cluster of G blocks (G = 1: a single block).
 template <class S, class R, bool DEV>
 __global__ void __launch_bounds__(512) k_bead_step(const S* __restrict__ pop, const FluidK<R> P,
                                                     const ChainK<R> C, const PendK<R> Pd, const uint32_t step) {
   extern __shared__ __align__(16) unsigned char smem[];
+  unsigned rank, G;
+  asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(G));
   grid_dependency_wait();
   allow_dependent_launch();
-  bead_step_block<S, R, DEV>(pop, P, C, Pd, step, smem);
+  bead_step_block<S, R, DEV>(pop, P, C, Pd, step, smem, (int)rank, (int)G);
 }
 
 // B[i][node] += dn_i at every pending node (each node appears once in the list), and the
@@ -1334,7 +1399,7 @@ __global__ void __launch_bounds__(512) k_chain_init_forces(const ChainK<R> C) {
     sl[t] = C.xl[t];
   }
   __syncthreads();
-  chain_forces_block<R>(sx, sl, C, C.F);
+  chain_forces_block<R>(sx, sl, C, C.F, 0, C.N);
   __syncthreads();
   for (int t = threadIdx.x; t < 3 * C.N; t += blockDim.x) C.Fc[t] = R(0);
 }

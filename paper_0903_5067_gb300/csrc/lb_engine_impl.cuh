@@ -460,20 +460,31 @@ class EngineT final : public Engine {
     return p;
   }
 
-  // Bead kernel of step k: with `chained`, launched with programmatic stream serialization
-  // (it waits for the previous grid before reading, so only its launch overlaps).
+  // Bead kernel of step k: one cluster of bead_cluster() blocks; with `chained`, launched with
+  // programmatic stream serialization (it waits for the previous grid before reading, so only
+  // its launch overlaps).
   void launch_bead(const S* A, const FluidK<R>& P, const PendK<R>& Pd, uint32_t k, cudaStream_t s, bool chained) {
+    const int G = bead_cluster();
     cudaLaunchConfig_t lc;
     memset(&lc, 0, sizeof(lc));
-    lc.gridDim = dim3(1);
+    lc.gridDim = dim3((unsigned)G);
     lc.blockDim = dim3(512);
     lc.dynamicSmemBytes = bead_smem();
     lc.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute at[2];
+    int na = 0;
+    at[na].id = cudaLaunchAttributeClusterDimension;
+    at[na].val.clusterDim.x = (unsigned)G;
+    at[na].val.clusterDim.y = 1;
+    at[na].val.clusterDim.z = 1;
+    ++na;
+    if (chained) {
+      at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[na].val.programmaticStreamSerializationAllowed = 1;
+      ++na;
+    }
     lc.attrs = at;
-    lc.numAttrs = chained ? 1 : 0;
+    lc.numAttrs = (unsigned)na;
     cuda_check(cudaLaunchKernelEx(&lc, k_bead_step<S, R, DEV>, A, P, chain(), Pd, k), "bead kernel");
     cuda_check(cudaGetLastError(), "bead kernel");
   }
@@ -569,8 +580,18 @@ class EngineT final : public Engine {
       while (M < ne) M <<= 1;
       groupb = M * 8 + ne * 4 + ((ne + 31) / 32) * 4;
     }
-    const size_t posb = 6 * (size_t)N_ * sizeof(R);  // positions (hi, lo)
+    // positions (hi, lo); in a cluster also half-step velocities and image counters
+    const size_t posb = bead_cluster() > 1 ? 9 * (size_t)N_ * sizeof(R) + 3 * (size_t)N_ * sizeof(int)
+                                           : 6 * (size_t)N_ * sizeof(R);
     return groupb > posb ? groupb : posb;
+  }
+
+  // Blocks of the bead kernel's cluster: one per 16 beads, at most 8 (the portable cluster
+  // size); one block when the entries need the sorted grouping
+  int bead_cluster() const {
+    if (8 * (size_t)N_ * nsub_ > (size_t)kGroupHashMax) return 1;
+    const int g = N_ / 16;
+    return g < 1 ? 1 : (g > 8 ? 8 : g);
   }
 
   FluidK<R> fluid() const {
