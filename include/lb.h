@@ -212,6 +212,10 @@ int lb_batch_create(lb_batch** out, int R, const int* L, const int* N, const uin
 int lb_batch_set_stream(lb_batch* b, void* stream);
 int lb_batch_workspace_size(lb_batch* b, size_t* bytes);
 int lb_batch_bind_workspace(lb_batch* b, void* device_ptr, size_t bytes);
+/* Noise switches of every replica, as lb_set_options (stress_only: noise on the six stress
+ * modes only, the thermalization of Table 1 note b).  Only before the batch's workspace is
+ * bound by its first use (step, autotune, read); LB_ERR_STATE after. */
+int lb_batch_set_options(lb_batch* b, int noise_fluid, int noise_beads, int stress_only);
 /* Tile size of the batched LB kernel (128, 256 or 512 threads) and persistent thread blocks
  * per SM (0 = one block per tile).  Results do not depend on the shape. */
 int lb_batch_set_shape(lb_batch* b, int threads, int blocks_per_sm);

@@ -203,11 +203,23 @@ class Batch {
   virtual Engine& replica(int r) = 0;
   virtual void autotune(cudaStream_t s, int* threads, int* blocks_per_sm) = 0;
   virtual void set_shape(int threads, int blocks_per_sm) = 0;
+  virtual void set_options(int noise_fluid, int noise_beads, int stress_only) = 0;
 };
 
 template <class S, class R, bool DEV>
 class BatchT final : public Batch {
  public:
+  // noise switches of every replica (before initialise: the kernels' tables take them then)
+  void set_options(int noise_fluid, int noise_beads, int stress_only) override {
+    for (auto& e : eng_) {
+      Config c = e->config();
+      c.noise_fluid = noise_fluid ? 1 : 0;
+      c.noise_beads = noise_beads ? 1 : 0;
+      c.stress_only = stress_only ? 1 : 0;
+      e->set_config(c);
+    }
+  }
+
   BatchT(const std::vector<Config>& cfgs, const std::vector<std::vector<double>>& x0) : x0_(x0) {
     for (const Config& c : cfgs) eng_.emplace_back(new EngineT<S, R, DEV>(c));
     size_t off = 0;
@@ -649,6 +661,18 @@ int lb_batch_autotune(lb_batch* bt, int* threads, int* blocks_per_sm) {
     bt->b->autotune(bt->stream, threads, blocks_per_sm);
     return (int)LB_OK;
   });
+}
+
+int lb_batch_set_options(lb_batch* bt, int noise_fluid, int noise_beads, int stress_only) {
+  if (!bt) return LB_ERR_ARG;
+  if (bt->live) return LB_ERR_STATE;
+  for (Config& c : bt->cfgs) {
+    c.noise_fluid = noise_fluid ? 1 : 0;
+    c.noise_beads = noise_beads ? 1 : 0;
+    c.stress_only = stress_only ? 1 : 0;
+  }
+  bt->b->set_options(noise_fluid, noise_beads, stress_only);
+  return LB_OK;
 }
 
 int lb_batch_set_shape(lb_batch* bt, int threads, int blocks_per_sm) {

@@ -82,6 +82,7 @@ _SIGS = {
     "lb_batch_workspace_size": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
     "lb_batch_bind_workspace": (C.c_int, [_vp, _vp, C.c_size_t]),
     "lb_batch_set_shape": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "lb_batch_set_options": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
     "lb_batch_autotune": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "lb_batch_step": (C.c_int, [_vp, C.c_int64]),
     "lb_batch_sync": (C.c_int, [_vp]),
@@ -334,6 +335,10 @@ def lb_batch_set_shape(b, threads: int, blocks_per_sm: int):
     _check(_lib.lb_batch_set_shape(b, int(threads), int(blocks_per_sm)), "lb_batch_set_shape")
 
 
+def lb_batch_set_options(b, noise_fluid=1, noise_beads=1, stress_only=0):
+    _check(_lib.lb_batch_set_options(b, int(noise_fluid), int(noise_beads), int(stress_only)), "lb_batch_set_options")
+
+
 def lb_batch_autotune(b):
     t, k = C.c_int(), C.c_int()
     _check(_lib.lb_batch_autotune(b, C.byref(t), C.byref(k)), "lb_batch_autotune")
@@ -375,7 +380,7 @@ class Batch:
     workspace in a torch tensor, work on torch's current stream."""
 
     def __init__(self, L, N, seeds, X0, rho=1.0, eta=3.0, eta_b=3.0, kT=1.0, h=0.01, a=1.0, m=1.0, zeta=20.8,
-                 k_fene=30.0, R0=1.5, eps=1.0, sigma=1.0, precision=LB_FP32, md_substeps=1):
+                 k_fene=30.0, R0=1.5, eps=1.0, sigma=1.0, precision=LB_FP32, md_substeps=1, stress_only=False):
         import torch
 
         self.L = [int(v) for v in L]
@@ -388,6 +393,8 @@ class Batch:
         nbytes = lb_batch_workspace_size(self.b)
         self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         lb_batch_bind_workspace(self.b, self._ws.data_ptr(), nbytes)
+        if stress_only:
+            lb_batch_set_options(self.b, 1, 1, 1)
 
     def step(self, n=1):
         lb_batch_step(self.b, n)

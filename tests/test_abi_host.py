@@ -145,3 +145,16 @@ def test_bd_create_validates_arguments(lblib):
         with pytest.raises(lblib.LBError) as ei:
             lblib.lb_bd_create(**dict(base, **bad))
         assert ei.value.code == lblib.LB_ERR_ARG, bad
+
+
+def test_batch_options_before_first_use(lblib):
+    """lb_batch_set_options is taken before the batch's first use (no GPU needed) and checks
+    its handle."""
+    b = lblib.lb_batch_create([8, 12], [0, 0], [1, 2], 1.0, 3.0, 3.0, 1.0, 0.01, 1.0, 1.0, 20.8, 30.0, 1.5, 1.0,
+                              1.0, None, lblib.LB_FP32, 1)
+    try:
+        lblib.lb_batch_set_options(b, 1, 1, 1)
+        lblib.lb_batch_set_options(b, 0, 1, 0)
+    finally:
+        lblib.lb_batch_destroy(b)
+    assert lblib._lib.lb_batch_set_options(None, 1, 1, 1) == lblib.LB_ERR_ARG

@@ -22,8 +22,8 @@ def _ensemble():
     return L, N, seeds, X
 
 
-def _oracle_replica(r, L, N, seed, X0, steps):
-    fp = o.FluidParams(L=L, rho=1.0, eta=3.0, eta_b=3.0, kT=1.0, h=0.01, a=1.0, seed=seed)
+def _oracle_replica(r, L, N, seed, X0, steps, stress_only=False):
+    fp = o.FluidParams(L=L, rho=1.0, eta=3.0, eta_b=3.0, kT=1.0, h=0.01, a=1.0, seed=seed, stress_only=stress_only)
     cp = o.ChainParams(N=N) if N > 0 else None
     st = o.init_state(fp, cp, X0 if N > 0 else None)
     return o.run(st, fp, cp, steps, replica=r)
@@ -44,6 +44,22 @@ def test_batch_replicas_match_oracle(lblib, prec):
         if N[r] > 0:
             x, v = b.beads(r)
             assert np.max(np.abs(x - st.X)) / L[r] <= tol, r
+    b.close()
+
+
+def test_batch_stress_only_replicas_match_oracle(lblib):
+    """lb_batch_set_options(stress_only): noise on the six stress modes of every replica
+    (Table 1, note b), FP64 against the oracle."""
+    L, N, seeds, X = _ensemble()
+    b = lblib.Batch(L, N, seeds, X, precision=lblib.LB_FP64, stress_only=True, **PARAMS)
+    b.step(20)
+    b.sync()
+    for r in range(len(L)):
+        st = _oracle_replica(r, L[r], N[r], seeds[r], X[r], 20, stress_only=True)
+        assert pop_rel_err(b.populations(r), st.n) <= 1e-12, r
+        if N[r] > 0:
+            x, v = b.beads(r)
+            assert np.max(np.abs(x - st.X)) / L[r] <= 1e-12, r
     b.close()
 
 

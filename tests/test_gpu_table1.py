@@ -38,15 +38,18 @@ def _fit_slope(t, y):
     return float(np.linalg.lstsq(A, y, rcond=None)[0][0])
 
 
-@pytest.mark.parametrize("L", [10, 15, 25])
-def test_chain_properties_match_table1(lblib, L):
+def _production(lblib, L, stress_only=False):
+    """64 replicas of the paper's production run in an L box: per-replica time averages of
+    R_g^2 and R_e^2, and from the recorded trajectories <1/R_H>, D_CM and the g1, g3
+    exponents."""
     import torch
     from paper_0903_5067_gb300 import analysis as an
 
     R, N = 64, 32
     seeds = [1000 * L + r for r in range(R)]
     X = [inputs.chain_walk(N, L=L, bond=0.97, seed=s, self_avoiding=True) for s in seeds]
-    b = lblib.Batch([L] * R, [N] * R, seeds, X, precision=lblib.LB_FP32, md_substeps=2, **PAPER)
+    b = lblib.Batch([L] * R, [N] * R, seeds, X, precision=lblib.LB_FP32, md_substeps=2, stress_only=stress_only,
+                    **PAPER)
     b.step(40000)  # equilibration: 800 time units
     frames = []
     for k in range(1600):  # sampling: 3200 time units per replica
@@ -58,11 +61,6 @@ def test_chain_properties_match_table1(lblib, L):
     obs = np.array([b.observables(r) for r in range(R)])
     b.close()
     traj = np.stack(frames, axis=1)  # (R, T, N, 3), unwrapped
-    # statics
-    rg2, re2 = obs[:, 18], obs[:, 19]
-    re2_p, dre2_p, rg2_p, drg2_p = _rows("table1_lb_statics.txt")[L]
-    se_rg, se_re = rg2.std(ddof=1) / np.sqrt(R), re2.std(ddof=1) / np.sqrt(R)
-    # dynamics and the hydrodynamic radius, per replica on the GPU
     rh, dcm, e1, e3 = [], [], [], []
     dt = FRAME * PAPER["h"]
     lags = np.arange(0, 201)
@@ -76,9 +74,22 @@ def test_chain_properties_match_table1(lblib, L):
         dcm.append(_fit_slope(t[fit], g3[fit]) / 6.0)
         e1.append(_fit_slope(np.log(t[sub]), np.log(g1[sub])))
         e3.append(_fit_slope(np.log(t[sub]), np.log(g3[sub])))
-    rh, dcm, e1, e3 = map(np.array, (rh, dcm, e1, e3))
+    return dict(R=R, rg2=obs[:, 18], re2=obs[:, 19], rh=np.array(rh), dcm=np.array(dcm), e1=np.array(e1),
+                e3=np.array(e3))
+
+
+def _se(a):
+    return a.std(ddof=1) / np.sqrt(a.size)
+
+
+@pytest.mark.parametrize("L", [10, 15, 25])
+def test_chain_properties_match_table1(lblib, L):
+    res = _production(lblib, L)
+    rg2, re2, rh, dcm, e1, e3 = (res[k] for k in ("rg2", "re2", "rh", "dcm", "e1", "e3"))
+    re2_p, dre2_p, rg2_p, drg2_p = _rows("table1_lb_statics.txt")[L]
+    se_rg, se_re = _se(rg2), _se(re2)
     rh_p, drh_p, d_p, dd_p, e1_p, de1_p, e3_p, de3_p = _rows("table1_lb_dynamics.txt")[L]
-    se = lambda a: a.std(ddof=1) / np.sqrt(R)
+    se = _se
     print(f"L={L}: Rg2 {rg2.mean():.2f} +- {se_rg:.2f} (paper {rg2_p} +- {drg2_p}); "
           f"Re2 {re2.mean():.2f} +- {se_re:.2f} (paper {re2_p} +- {dre2_p}); "
           f"1/RH {rh.mean():.4f} +- {se(rh):.4f} (paper {rh_p}); "
@@ -91,3 +102,17 @@ def test_chain_properties_match_table1(lblib, L):
     assert abs(dcm.mean() - d_p) <= 3 * np.hypot(se(dcm), dd_p)
     assert abs(e1.mean() - e1_p) <= 3 * np.hypot(se(e1), de1_p)
     assert abs(e3.mean() - e3_p) <= 3 * np.hypot(se(e3), de3_p)
+
+
+@pytest.mark.parametrize("L", [10, 15, 25])
+def test_stress_only_thermalization_matches_table1_note_b(lblib, L):
+    """The original thermalization, noise on the stress modes only (Table 1, note b; Sec. II B):
+    the same production runs give the note-b g1 exponents.  D_CM and <1/R_H> are printed for
+    the record (the paper compares the stress-only D_CM only through its L -> infinity
+    extrapolation, Sec. III B)."""
+    res = _production(lblib, L, stress_only=True)
+    rh, dcm, e1, e3 = (res[k] for k in ("rh", "dcm", "e1", "e3"))
+    e1_p, de1_p = _rows("table1_lb_stress_only.txt")[L]
+    print(f"L={L} stress-only: 1/RH {rh.mean():.4f} +- {_se(rh):.4f}; D_CM {dcm.mean():.3e} +- {_se(dcm):.1e}; "
+          f"g1 exp {e1.mean():.3f} +- {_se(e1):.3f} (paper {e1_p}); g3 exp {e3.mean():.3f} +- {_se(e3):.3f}")
+    assert abs(e1.mean() - e1_p) <= 3 * np.hypot(_se(e1), de1_p)
