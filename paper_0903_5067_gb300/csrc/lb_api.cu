@@ -415,9 +415,7 @@ int lb_get_beads_async(lb_ctx* ctx, double* x, double* v, size_t cap, int64_t* t
         cuda_check(cudaEventCreateWithFlags(&ctx->tev[j], cudaEventDisableTiming), "event");
     }
     const int slot = (int)(ctx->tickets % lb_ctx::kTickets);
-    ctx->eng->enqueue_beads(x, v, ctx->stream);
-    ctx->eng->enqueue_status(ctx->tstatus + slot, ctx->stream);
-    cuda_check(cudaEventRecord(ctx->tev[slot], ctx->stream), "record read-back");
+    ctx->eng->enqueue_beads_async(x, v, ctx->tstatus + slot, ctx->tev[slot], ctx->stream);
     *ticket = ctx->tickets++;
     return (int)LB_OK;
   });
@@ -573,7 +571,13 @@ void lb_destroy(lb_ctx* ctx) {
   } catch (...) {
   }
   if (ctx->tstatus) {  // asynchronous read-backs may still be in flight
-    if (ctx->live) cudaStreamSynchronize(ctx->stream);
+    if (ctx->live) {
+      cudaStreamSynchronize(ctx->stream);
+      try {
+        ctx->eng->drain();
+      } catch (...) {
+      }
+    }
     for (int j = 0; j < lb_ctx::kTickets; ++j)
       if (ctx->tev[j]) cudaEventDestroy(ctx->tev[j]);
     cudaFreeHost(ctx->tstatus);

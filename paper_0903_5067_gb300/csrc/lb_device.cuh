@@ -106,6 +106,10 @@ struct ChainK {
   int* p_count;
   int cap;     // 8N
   unsigned* status;
+  // FP64 snapshot of the state after each step, written by the bead kernel of step k into
+  // slot k mod 2 (3N unwrapped positions x + xl + img box, then 3N velocities), or null
+  double* snap;
+  double snap_box;  // L a in FP64
 };
 
 // Force corrections in flight between consecutive steps of a multi-step run.  The bead kernel
@@ -949,7 +953,14 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
       C.Fc[t] = fc;
       C.fc_hist[sub * 3 * N + t] = fc;
       C.F[t] = Ft;
-      C.v[t] = vh + h * Ft / (R(2) * C.m);
+      const R vn = vh + h * Ft / (R(2) * C.m);
+      C.v[t] = vn;
+      if (C.snap && sub == C.nsub - 1) {  // the step's end state, as the bead read-back forms it
+        double* sn = C.snap + (size_t)(step & 1u) * 6 * N;
+        const int im = G > 1 ? simg[t] : C.img[t];
+        sn[t] = __dadd_rn(__dadd_rn((double)sx[t], (double)sl[t]), __dmul_rn((double)im, C.snap_box));
+        sn[3 * N + t] = (double)vn;
+      }
     }
   }
   __syncthreads();

@@ -64,6 +64,12 @@ class Engine {
   virtual void enqueue_beads(double* x, double* v, cudaStream_t s) = 0;
   // enqueue a copy of the device status word to host memory
   virtual void enqueue_status(unsigned* host, cudaStream_t s) = 0;
+  // bead read-back and status copy after the work queued on s so far, completing `done`;
+  // off the stream s where the last step's snapshot holds the state (see EngineT)
+  virtual void enqueue_beads_async(double* x, double* v, unsigned* status_host, cudaEvent_t done,
+                                   cudaStream_t s) = 0;
+  // wait for read-backs in flight on the engine's own stream
+  virtual void drain() = 0;
   virtual void observables(double* out, int64_t step, int accumulate, cudaStream_t s) = 0;
   virtual void reset_reference(cudaStream_t s) = 0;
   // write the current unwrapped bead positions (3N doubles) to device memory

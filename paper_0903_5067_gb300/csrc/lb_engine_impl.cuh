@@ -35,6 +35,7 @@ class EngineT final : public Engine {
   void set_config(const Config& c) override { cfg_ = c; }
 
   void initialise(const double* x0, const double* v0, cudaStream_t s) override {
+    snap_valid_ = false;
     if ((size_t)Q * 256 * sizeof(R) > 48 * 1024) {  // FP64: staged corrections of a 256-node tile
       for (int v = 0; v < 4; ++v)
         cuda_check(cudaFuncSetAttribute(lb_kernel(v & 1, v >> 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -98,7 +99,11 @@ class EngineT final : public Engine {
     const S* A = pop_[cur_];
     S* Bo = pop_[cur_ ^ 1];
     const PendK<R> Pd = pend(false);
-    if (N_ > 0) launch_bead(A, P, Pd, k, s, ev0 == nullptr);
+    if (N_ > 0) {
+      launch_bead(A, P, Pd, k, s, ev0 == nullptr);
+      snap_valid_ = true;
+      snap_k_ = k;
+    }
     launch_lb(A, Bo, P, Pd, k, s, ev0, ev1);
     if (N_ > 0) apply(Bo, P, pslot_, s);
     cur_ ^= 1;
@@ -121,6 +126,8 @@ class EngineT final : public Engine {
     if (open_) pslot_ ^= 1;
     const PendK<R> Pd = pend(true);
     launch_bead(A, P, Pd, k, s, ev0 == nullptr);
+    snap_valid_ = true;
+    snap_k_ = k;
     launch_lb(A, Bo, P, Pd, k, s, ev0, ev1);
     open_ = true;
     cur_ ^= 1;
@@ -136,6 +143,7 @@ class EngineT final : public Engine {
   void adjoint_displacement(int64_t T, int K, uint32_t k0, double* O, double* gx, double* gz,
                             cudaStream_t s) override {
     flush(s);
+    snap_valid_ = false;
     if (N_ == 0) throw LbError(S_STATE, "adjoint needs a chain");
     if (nsub_ != 1) throw LbError(S_STATE, "adjoint needs one MD step per LB step");
     const FluidK<R> P = fluid();
@@ -368,6 +376,53 @@ class EngineT final : public Engine {
     cuda_check(cudaMemcpyAsync(host, status_, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "status");
   }
 
+  // Asynchronous read-back.  While the last step's snapshot holds the bead state, the copies
+  // run on the engine's own stream after an event on s, so that s goes on with the next steps
+  // (the bead kernel that next rewrites the slot waits for them); otherwise the read-back
+  // kernel and the copies are queued on s itself.  Either way `done` is recorded on the
+  // engine's stream, so read-backs complete in the order they were asked for.
+  void enqueue_beads_async(double* x, double* v, unsigned* status_host, cudaEvent_t done,
+                           cudaStream_t s) override {
+    if (!side_) {
+      cuda_check(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking), "read-back stream");
+      cuda_check(cudaEventCreateWithFlags(&step_ev_, cudaEventDisableTiming), "event");
+      for (int j = 0; j < 2; ++j) cuda_check(cudaEventCreateWithFlags(&copy_ev_[j], cudaEventDisableTiming), "event");
+    }
+    if (N_ == 0 || !snap_valid_) {
+      enqueue_beads(x, v, s);
+      enqueue_status(status_host, s);
+      cuda_check(cudaEventRecord(step_ev_, s), "record read-back");
+      cuda_check(cudaStreamWaitEvent(side_, step_ev_, 0), "wait read-back");
+      cuda_check(cudaEventRecord(done, side_), "record read-back");
+      return;
+    }
+    const int p = (int)(snap_k_ & 1u);
+    const size_t n3 = 3 * (size_t)N_;
+    const double* sn = snap_ + (size_t)p * 2 * n3;
+    cuda_check(cudaEventRecord(step_ev_, s), "record step");
+    cuda_check(cudaStreamWaitEvent(side_, step_ev_, 0), "wait step");
+    if (x) cuda_check(cudaMemcpyAsync(x, sn, n3 * sizeof(double), cudaMemcpyDeviceToHost, side_), "dl x");
+    if (v) cuda_check(cudaMemcpyAsync(v, sn + n3, n3 * sizeof(double), cudaMemcpyDeviceToHost, side_), "dl v");
+    enqueue_status(status_host, side_);
+    cuda_check(cudaEventRecord(copy_ev_[p], side_), "record copy");
+    snap_pending_[p] = true;
+    cuda_check(cudaEventRecord(done, side_), "record read-back");
+  }
+
+  void drain() override {
+    if (side_) cuda_check(cudaStreamSynchronize(side_), "drain read-backs");
+  }
+
+  ~EngineT() override {
+    if (side_) {
+      cudaStreamSynchronize(side_);
+      cudaStreamDestroy(side_);
+      cudaEventDestroy(step_ev_);
+      cudaEventDestroy(copy_ev_[0]);
+      cudaEventDestroy(copy_ev_[1]);
+    }
+  }
+
   void observables(double* out, int64_t step, int accumulate, cudaStream_t s) override {
     flush(s);
     ObsK<R> O = obs(step, accumulate);
@@ -427,6 +482,7 @@ class EngineT final : public Engine {
   }
   void load_state(const void* host, cudaStream_t s) override {
     flush(s);
+    snap_valid_ = false;
     unsigned char* p = const_cast<unsigned char*>(static_cast<const unsigned char*>(host));
     for (int i = 0; i < Q; ++i) {
       cuda_check(cudaMemcpyAsync(pop_[cur_] + (size_t)i * plane_, p, nnodes_ * sizeof(S), cudaMemcpyHostToDevice, s),
@@ -464,6 +520,10 @@ class EngineT final : public Engine {
   // programmatic stream serialization (it waits for the previous grid before reading, so only
   // its launch overlaps).
   void launch_bead(const S* A, const FluidK<R>& P, const PendK<R>& Pd, uint32_t k, cudaStream_t s, bool chained) {
+    if (snap_pending_[k & 1u]) {  // this kernel rewrites the snapshot slot being read back
+      cuda_check(cudaStreamWaitEvent(s, copy_ev_[k & 1u], 0), "wait read-back");
+      snap_pending_[k & 1u] = false;
+    }
     const int G = bead_cluster();
     cudaLaunchConfig_t lc;
     memset(&lc, 0, sizeof(lc));
@@ -682,6 +742,8 @@ class EngineT final : public Engine {
     C.p_count = p_count_[0];
     C.cap = cap_;
     C.status = status_;
+    C.snap = N_ > 0 ? snap_ : nullptr;
+    C.snap_box = cfg_.L * cfg_.a;
     return C;
   }
 
@@ -736,6 +798,7 @@ class EngineT final : public Engine {
     fch_ = reinterpret_cast<R*>(take(n3 * nsub_ * sizeof(R)));
     xref_ = reinterpret_cast<double*>(take(n3 * sizeof(double)));
     rb_ = reinterpret_cast<double*>(take(2 * n3 * sizeof(double)));
+    snap_ = reinterpret_cast<double*>(take(4 * n3 * sizeof(double)));
     e_node_ = reinterpret_cast<int*>(take(cap_ * sizeof(int)));
     e_w_ = reinterpret_cast<R*>(take(cap_ * sizeof(R)));
     e_mom_ = reinterpret_cast<R*>(take(4 * cap_ * sizeof(R)));
@@ -765,6 +828,14 @@ class EngineT final : public Engine {
   int* img_ = nullptr;
   double* xref_ = nullptr;
   double* rb_ = nullptr;  // bead read-back staging: 3N positions, 3N velocities (FP64)
+  double* snap_ = nullptr;  // two slots of the same, written by the bead kernel every step
+  // the snapshot of step snap_k_ holds the bead state (no state change since that step)
+  bool snap_valid_ = false;
+  uint32_t snap_k_ = 0;
+  // read-backs of snapshot slots on the engine's own stream, not yet known to be complete
+  bool snap_pending_[2] = {false, false};
+  cudaStream_t side_ = nullptr;
+  cudaEvent_t step_ev_ = nullptr, copy_ev_[2] = {nullptr, nullptr};
   int* e_node_ = nullptr;
   R *e_w_ = nullptr, *e_mom_ = nullptr;
   int4* p_pos_[2] = {nullptr, nullptr};

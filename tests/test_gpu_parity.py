@@ -319,21 +319,24 @@ def test_spreading_of_many_entries_matches_oracle(lblib):
     assert ex <= 1e-12 and ev <= 1e-11
 
 
-def test_asynchronous_bead_read_back(lblib):
+@pytest.mark.parametrize("N", [12, 48], ids=["one_block", "cluster"])
+def test_asynchronous_bead_read_back(lblib, N, tmp_path):
     """lb_get_beads_async + lb_wait return what lb_get_beads returns, step after step, with
-    reads queued behind later steps; a ticket not yet issued is an argument error."""
+    reads queued behind later steps (copied from the bead kernel's per-step snapshot, off the
+    context's stream); after a checkpoint load (the snapshot no longer holds the state) the
+    read-back of the loaded state; a ticket not yet issued is an argument error."""
     import torch
 
-    case = Case(L=10, N=12, steps=0, seed=12)
+    case = Case(L=10, N=N, steps=0, seed=12)
     a = gpu_sim(lblib, case, lblib.LB_FP32)
     b = gpu_sim(lblib, case, lblib.LB_FP32)
     a._bind()
-    bufs = [(torch.empty((12, 3), dtype=torch.float64, pin_memory=True).numpy(),
-             torch.empty((12, 3), dtype=torch.float64, pin_memory=True).numpy()) for _ in range(3)]
+    bufs = [(torch.empty((N, 3), dtype=torch.float64, pin_memory=True).numpy(),
+             torch.empty((N, 3), dtype=torch.float64, pin_memory=True).numpy()) for _ in range(3)]
     tickets, ref = [], {}
     for k in range(9):
         a.step(1)
-        tickets.append(lblib.lb_get_beads_async(a.ctx, bufs[k % 3][0], bufs[k % 3][1], 36))
+        tickets.append(lblib.lb_get_beads_async(a.ctx, bufs[k % 3][0], bufs[k % 3][1], 3 * N))
         b.step(1)
         xr, vr = b.beads()
         ref[k] = (xr.copy(), vr.copy())
@@ -341,8 +344,18 @@ def test_asynchronous_bead_read_back(lblib):
             lblib.lb_wait(a.ctx, tickets[k - 2])
             xo, vo = bufs[(k - 2) % 3]
             assert np.array_equal(xo, ref[k - 2][0]) and np.array_equal(vo, ref[k - 2][1])
+    for t in tickets[-2:]:
+        lblib.lb_wait(a.ctx, t)
+    path = str(tmp_path / "state.lb")
+    lblib.lb_save(a.ctx, path)
+    xs, vs = a.beads()
+    a.step(3)
+    lblib.lb_load(a.ctx, path)
+    t = lblib.lb_get_beads_async(a.ctx, bufs[0][0], bufs[0][1], 3 * N)
+    lblib.lb_wait(a.ctx, t)
+    assert np.array_equal(bufs[0][0], xs) and np.array_equal(bufs[0][1], vs)
     with pytest.raises(lblib.LBError) as ei:
-        lblib.lb_wait(a.ctx, len(tickets))
+        lblib.lb_wait(a.ctx, t + 1)
     assert ei.value.code == lblib.LB_ERR_ARG
     a.close()
     b.close()
