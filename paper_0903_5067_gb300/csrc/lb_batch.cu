@@ -85,20 +85,61 @@ struct BatchLB {
 
 // FP32: at most 42 registers (three 512-thread blocks per SM), as the single-box kernel; the
 // rare correction scatter would otherwise raise the whole kernel's register count
-// Tiles are taken from a per-group counter in chunks of kChunk (blocks that start late, e.g.
-// beside a bead block, simply take fewer); each block's tiles increase, so the replica search
-// only moves forward.  The counter of this step's parity was zeroed by the previous step's
-// bead kernel.
 constexpr unsigned kChunk = 2;
 
+// One tile (T = blockDim.x consecutive nodes of replica r): pull-stream + collide (Sec. II B).
 template <class S, class R, bool DEV, bool NOISE>
+__device__ __forceinline__ void batch_tile(const BatchLB<S, R>& B, const int r, const unsigned long long tile,
+                                           const int parity, const uint32_t step, unsigned char* dsm) {
+  const unsigned T = blockDim.x;
+  const int pslot = parity ^ 1;  // the previous step's corrections
+  const BatchRep<S, R>& rp = B.rep[r];
+  const unsigned long long n0 = (tile - rp.tile0) * T;
+  const unsigned long long node = n0 + threadIdx.x;
+  if (node >= rp.nnodes) return;
+  // a node marked by the previous step adds that step's corrections to what it pulls
+  // (replicas without a chain have no correction field and are never marked)
+  const bool stamped = rp.p_dense[pslot] != nullptr &&
+                       ((B.mask[pslot][rp.seg0 + ((unsigned)node >> kSegShift)] >> ((unsigned)node & 31u)) & 1u);
+  const unsigned L = rp.L;
+  unsigned x, y;
+  const unsigned t = div_small((unsigned)node, L, rp.invL, x);
+  const unsigned z = div_small(t, L, rp.invL, y);
+  if (stamped) {  // two inlined copies: the common one carries no correction code
+    R* col = reinterpret_cast<R*>(dsm) + threadIdx.x;
+    stage_corrections<R>(rp.p_dense[pslot], rp.plane, L, x, y, z, col, T);
+    lb_node_update<S, R, DEV, NOISE, unsigned>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r],
+                                               rp.nonpos, step, x, y, z, col, T);
+  } else {
+    lb_node_update<S, R, DEV, NOISE, unsigned>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r],
+                                               rp.nonpos, step, x, y, z);
+  }
+}
+
+// PERSIST: persistent blocks take tiles from a per-group counter in chunks of kChunk (blocks
+// that start late, e.g. beside a bead block, simply take fewer); each block's tiles increase,
+// so the replica search only moves forward.  The counter of this step's parity was zeroed by
+// the previous step's bead kernel.  Otherwise one block per tile: the tile is the block
+// index and the replica a binary search over the table, both uniform across the block, so the
+// replica's fields (its Philox round keys among them) stay in the constant bank and uniform
+// registers; the hardware block scheduler balances the load.
+template <class S, class R, bool DEV, bool NOISE, bool PERSIST>
 __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 3 : 1) k_batch_lb(const __grid_constant__ BatchLB<S, R> B, int parity,
                                                    const uint32_t* __restrict__ d_step, uint32_t j) {
   extern __shared__ __align__(16) unsigned char dsm[];  // staged corrections, 19 x T
-  __shared__ unsigned long long s_next;
   const uint32_t step = *d_step + j;
-  const unsigned T = blockDim.x;
-  const int pslot = parity ^ 1;  // the previous step's corrections
+  if (!PERSIST) {
+    const unsigned long long tile = blockIdx.x;
+    int lo = 0, hi = B.nrep - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (B.rep[mid].tile0 <= tile) lo = mid;
+      else hi = mid - 1;
+    }
+    batch_tile<S, R, DEV, NOISE>(B, lo, tile, parity, step, dsm);
+    return;
+  }
+  __shared__ unsigned long long s_next;
   unsigned long long* ctr = B.counter + parity;
   if (threadIdx.x == 0) s_next = atomicAdd(ctr, (unsigned long long)kChunk);
   __syncthreads();
@@ -110,28 +151,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 3 : 1) k_batch_lb(const 
     const unsigned long long t_end = cur + kChunk < B.total_tiles ? cur + kChunk : B.total_tiles;
     for (unsigned long long tile = cur; tile < t_end; ++tile) {
       while (r + 1 < B.nrep && B.rep[r + 1].tile0 <= tile) ++r;  // uniform
-      const BatchRep<S, R>& rp = B.rep[r];
-      const unsigned long long n0 = (tile - rp.tile0) * T;
-      const unsigned long long node = n0 + threadIdx.x;
-      if (node < rp.nnodes) {
-        // a node marked by the previous step adds that step's corrections to what it pulls
-        // (replicas without a chain have no correction field and are never marked)
-        const bool stamped = rp.p_dense[pslot] != nullptr &&
-                             ((B.mask[pslot][rp.seg0 + ((unsigned)node >> kSegShift)] >> ((unsigned)node & 31u)) & 1u);
-        const unsigned L = rp.L;
-        unsigned x, y;
-        const unsigned t = div_small((unsigned)node, L, rp.invL, x);
-        const unsigned z = div_small(t, L, rp.invL, y);
-        if (stamped) {  // two inlined copies: the common one carries no correction code
-          R* col = reinterpret_cast<R*>(dsm) + threadIdx.x;
-          stage_corrections<R>(rp.p_dense[pslot], rp.plane, L, x, y, z, col, T);
-          lb_node_update<S, R, DEV, NOISE, unsigned>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r],
-                                                     rp.nonpos, step, x, y, z, col, T);
-        } else {
-          lb_node_update<S, R, DEV, NOISE, unsigned>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r],
-                                                     rp.nonpos, step, x, y, z);
-        }
-      }
+      batch_tile<S, R, DEV, NOISE>(B, r, tile, parity, step, dsm);
     }
     __syncthreads();
     cur = s_next;
@@ -278,12 +298,10 @@ class BatchT final : public Batch {
     cuda_check(cudaMemsetAsync(flags_[0], 0, 2 * max_segs_ * sizeof(unsigned), s), "memset marks");
     const size_t lbsm = (size_t)Q * 512 * sizeof(R);
     if (lbsm > 48 * 1024) {  // FP64: staged corrections of a 512-node run
-      cuda_check(cudaFuncSetAttribute(k_batch_lb<S, R, DEV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)lbsm),
-                 "batch LB shared memory");
-      cuda_check(cudaFuncSetAttribute(k_batch_lb<S, R, DEV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)lbsm),
-                 "batch LB shared memory");
+      for (int v = 0; v < 4; ++v)
+        cuda_check(cudaFuncSetAttribute(lb_kernel(v & 1, v >> 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)lbsm),
+                   "batch LB shared memory");
     }
     cuda_check(cudaMemsetAsync(counters_, 0, 2 * (eng_.size() / kBatchGroup + 1) * sizeof(unsigned long long), s),
                "memset tile counters");
@@ -379,6 +397,13 @@ class BatchT final : public Batch {
     cuda_check(cudaGetLastError(), "batch apply");
     k_batch_clear<S, R><<<1, 256, 0, s>>>(d_reps_, R_, slot);
     cuda_check(cudaGetLastError(), "batch clear");
+  }
+
+  // the batched LB kernel for noise on/off, persistent blocks or one block per tile
+  using BatchLbKernel = void (*)(const BatchLB<S, R>, int, const uint32_t*, uint32_t);
+  static BatchLbKernel lb_kernel(bool noise, bool persist) {
+    if (noise) return persist ? k_batch_lb<S, R, DEV, true, true> : k_batch_lb<S, R, DEV, true, false>;
+    return persist ? k_batch_lb<S, R, DEV, false, true> : k_batch_lb<S, R, DEV, false, false>;
   }
 
   void drop_graph() {
@@ -480,12 +505,8 @@ class BatchT final : public Batch {
       at[0].val.programmaticStreamSerializationAllowed = 1;
       lc.attrs = at;
       lc.numAttrs = first ? 1 : 0;
-      if (noise_)
-        cuda_check(cudaLaunchKernelEx(&lc, k_batch_lb<S, R, DEV, true>, G, par, (const uint32_t*)d_step_, j),
-                   "batch LB");
-      else
-        cuda_check(cudaLaunchKernelEx(&lc, k_batch_lb<S, R, DEV, false>, G, par, (const uint32_t*)d_step_, j),
-                   "batch LB");
+      cuda_check(cudaLaunchKernelEx(&lc, lb_kernel(noise_, bps_ > 0), G, par, (const uint32_t*)d_step_, j),
+                 "batch LB");
       first = false;
     }
     if (advance) k_add_step<<<1, 1, 0, s>>>(d_step_, 1);
