@@ -98,22 +98,26 @@ __device__ __forceinline__ void batch_tile(const BatchLB<S, R>& B, const int r, 
   const unsigned long long node = n0 + threadIdx.x;
   if (node >= rp.nnodes) return;
   // a node marked by the previous step adds that step's corrections to what it pulls
-  // (replicas without a chain have no correction field and are never marked)
-  const bool stamped = rp.p_dense[pslot] != nullptr &&
-                       ((B.mask[pslot][rp.seg0 + ((unsigned)node >> kSegShift)] >> ((unsigned)node & 31u)) & 1u);
+  // (replicas without a chain have no correction field and are never marked); the pull is
+  // issued before the mark is known, and one copy of the collision follows, as in lb_tile.
+  // The node index handed on is formed again from (x, y, z) in 32 bits: the same value taken
+  // from the 64-bit tile arithmetic cost 17 us per step of the 64-replica batch.
+  const unsigned mw = rp.p_dense[pslot] != nullptr ? B.mask[pslot][rp.seg0 + ((unsigned)node >> kSegShift)] : 0u;
   const unsigned L = rp.L;
   unsigned x, y;
   const unsigned t = div_small((unsigned)node, L, rp.invL, x);
   const unsigned z = div_small(t, L, rp.invL, y);
-  if (stamped) {  // two inlined copies: the common one carries no correction code
+  const unsigned pl = (unsigned)rp.plane;
+  R n[Q];
+  lb_pull<S, R, unsigned>(rp.pop[parity], L, pl, x, y, z, n);
+  if ((mw >> ((unsigned)node & 31u)) & 1u) {
     R* col = reinterpret_cast<R*>(dsm) + threadIdx.x;
     stage_corrections<R>(rp.p_dense[pslot], rp.plane, L, x, y, z, col, T);
-    lb_node_update<S, R, DEV, NOISE, unsigned>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r],
-                                               rp.nonpos, step, x, y, z, col, T);
-  } else {
-    lb_node_update<S, R, DEV, NOISE, unsigned>(rp.pop[parity], rp.pop[parity ^ 1], B.P, L, rp.plane, B.rk[r],
-                                               rp.nonpos, step, x, y, z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) n[i] += col[i * T];
   }
+  lb_collide_store<S, R, DEV, NOISE, unsigned>(n, rp.pop[parity ^ 1], B.P, pl, B.rk[r], rp.nonpos, step,
+                                               x + L * (y + L * z));
 }
 
 // PERSIST: persistent blocks take tiles from a per-group counter in chunks of kChunk (blocks

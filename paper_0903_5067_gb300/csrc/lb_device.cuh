@@ -407,19 +407,11 @@ __device__ __forceinline__ void lb_collide_store(const R* n, S* __restrict__ dst
   for (int i = 0; i < Q; ++i) st<S, R>(dst + ((I)i * pl + (I)node), out[i]);
 }
 
-// One node of the LB step: pull the 19 populations from the neighbours in src (periodic),
-// collide, write the 19 post-collision populations of node (x, y, z) to dst.
-// (L, plane, rk, nonpos: the box's size, plane stride, noise keys and counter, which the
-// batched kernel takes per replica; P: the remaining, shared parameters)
-// I: the type of element offsets within the population array (unsigned when all 19 planes fit
-// in 32 bits, which makes each address one wide multiply-add)
-template <class S, class R, bool DEV, bool NOISE, class I = unsigned long long>
-__device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
-                                               const unsigned L, const unsigned long long plane,
-                                               const RoundKeys& rk, unsigned long long* nonpos,
-                                               const uint32_t step, const unsigned x, const unsigned y,
-                                               const unsigned z, const R* __restrict__ dcol = nullptr,
-                                               unsigned dstride = 0) {
+// The 19 populations node (x, y, z) pulls from its neighbours in src (periodic): n_i(r) =
+// src_i(r - c_i) (Sec. II B, Eq. 3, streaming).
+template <class S, class R, class I>
+__device__ __forceinline__ void lb_pull(const S* __restrict__ src, const unsigned L, const I pl, const unsigned x,
+                                        const unsigned y, const unsigned z, R n[Q]) {
   const unsigned xm = x ? x - 1 : L - 1, xp = (x + 1 < L) ? x + 1 : 0;
   const unsigned ym = y ? y - 1 : L - 1, yp = (y + 1 < L) ? y + 1 : 0;
   const unsigned zm = z ? z - 1 : L - 1, zp = (z + 1 < L) ? z + 1 : 0;
@@ -428,19 +420,11 @@ __device__ __forceinline__ void lb_node_update(const S* __restrict__ src, S* __r
   const unsigned ry[3] = {yp * L, y * L, ym * L};
   const unsigned rz[3] = {zp * LL, z * LL, zm * LL};
   const unsigned sxs[3] = {xp, x, xm};
-
-  const I pl = (I)plane;
-  R n[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const unsigned idx = sxs[cx(i) + 1] + ry[cy(i) + 1] + rz[cz(i) + 1];
     n[i] = ld<S, R>(src + ((I)i * pl + (I)idx));
   }
-  if (dcol) {  // the previous step's corrections at the pulled nodes, staged by the caller
-#pragma unroll
-    for (int i = 0; i < Q; ++i) n[i] += dcol[i * dstride];
-  }
-  lb_collide_store<S, R, DEV, NOISE, I>(n, dst, P, pl, rk, nonpos, step, x + y * L + z * LL);
 }
 
 // Stage the previous step's corrections at the 19 pull sources of node (x, y, z) into
@@ -471,11 +455,17 @@ __device__ __forceinline__ void stage_corrections(const R* __restrict__ corr, un
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// One LB tile: pull-stream + collide for the (blockDim.x x blockDim.y) nodes at
-// (tx, ty, z) (Sec. II B, Eq. 3).  A node marked by the previous deferred step adds that
-// step's corrections to the populations it pulls (staged per thread in shared memory,
-// 19 x blockDim.x x blockDim.y values).
-template <class S, class R, bool DEV, bool NOISE, class I>
+// One LB tile: pull-stream + collide for the (blockDim.x x blockDim.y) nodes at (tx, ty, z)
+// (Sec. II B, Eq. 3).  Every thread loads its 19 populations and its mark word together; a
+// node marked by the previous deferred step then stages that step's corrections at its pull
+// sources (in shared memory, 19 x blockDim.x x blockDim.y values) and adds them to what it
+// pulled, and one copy of the collision follows.  (Branching on the mark before the loads put
+// an L2 round trip in front of every warp's loads, 1.4 us per launch at L = 128 with no node
+// marked; with two inlined copies of the update, a warp holding marked and unmarked nodes
+// ran both: 67.8 against 64.0 us with 1.5 % of the nodes marked.)
+// CORR = false (a box without a chain): no correction code at all (the dead correction path
+// alone cost 0.5 us per chained launch at L = 128).
+template <class S, class R, bool DEV, bool NOISE, class I, bool CORR>
 __device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
                                         const PendK<R>& Pd, const uint32_t step, unsigned tx, unsigned ty,
                                         unsigned z, R* stage) {
@@ -484,15 +474,17 @@ __device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict
   const unsigned y = ty * blockDim.y + threadIdx.y;
   if (x >= L || y >= L) return;
   const unsigned node = x + L * (y + L * z);
-  // two inlined copies of the update: the common one carries no correction code (one shared
-  // copy with a runtime branch measured 6 % slower)
-  if (Pd.have_prev && ((Pd.prev_mask[Pd.seg0 + (node >> kSegShift)] >> (node & 31u)) & 1u)) {
+  const unsigned mw = CORR && Pd.have_prev ? Pd.prev_mask[Pd.seg0 + (node >> kSegShift)] : 0u;
+  const I pl = (I)P.plane;
+  R n[Q];
+  lb_pull<S, R, I>(src, L, pl, x, y, z, n);
+  if (CORR && ((mw >> (node & 31u)) & 1u)) {
     const unsigned T = blockDim.x * blockDim.y, tid = threadIdx.x + blockDim.x * threadIdx.y;
     stage_corrections<R>(Pd.prev_dense, Pd.plane, L, x, y, z, stage + tid, T);
-    lb_node_update<S, R, DEV, NOISE, I>(src, dst, P, P.L, P.plane, P.rk, P.nonpos, step, x, y, z, stage + tid, T);
-  } else {
-    lb_node_update<S, R, DEV, NOISE, I>(src, dst, P, P.L, P.plane, P.rk, P.nonpos, step, x, y, z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) n[i] += stage[tid + i * T];
   }
+  lb_collide_store<S, R, DEV, NOISE, I>(n, dst, P, pl, P.rk, P.nonpos, step, node);
 }
 
 // Programmatic dependent launch (a grid launched with programmatic stream serialization may
@@ -509,7 +501,7 @@ __device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddep
 // runs beside it; the blocks of plane z = L, scheduled last, wait for it (bit 1), so that the
 // grid completes only after the bead kernel and whatever comes next may take this grid's
 // completion for both.  (A wait at the end of every block raised the register count.)
-template <class S, class R, bool DEV, bool NOISE, class I>
+template <class S, class R, bool DEV, bool NOISE, class I, bool CORR>
 __global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* __restrict__ dst,
                                                   const FluidK<R> P, const PendK<R> Pd, const uint32_t step) {
   extern __shared__ __align__(16) unsigned char lsm[];
@@ -520,7 +512,8 @@ __global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* _
   }
   if (P.pdl & 1) grid_dependency_wait();
   allow_dependent_launch();
-  lb_tile<S, R, DEV, NOISE, I>(src, dst, P, Pd, step, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<R*>(lsm));
+  lb_tile<S, R, DEV, NOISE, I, CORR>(src, dst, P, Pd, step, blockIdx.x, blockIdx.y, blockIdx.z,
+                                     reinterpret_cast<R*>(lsm));
 }
 
 // ---------------------------------------------------------------------------------------

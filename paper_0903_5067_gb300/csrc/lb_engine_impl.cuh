@@ -37,9 +37,9 @@ class EngineT final : public Engine {
   void initialise(const double* x0, const double* v0, cudaStream_t s) override {
     snap_valid_ = false;
     if ((size_t)Q * 256 * sizeof(R) > 48 * 1024) {  // FP64: staged corrections of a 256-node tile
-      for (int v = 0; v < 4; ++v)
-        cuda_check(cudaFuncSetAttribute(lb_kernel(v & 1, v >> 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(Q * 256 * sizeof(R))),
+      for (int v = 0; v < 8; ++v)
+        cuda_check(cudaFuncSetAttribute(lb_kernel(v & 1, (v >> 1) & 1, v >> 2),
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(Q * 256 * sizeof(R))),
                    "LB kernel shared memory");
     }
     if (bead_smem() > 48 * 1024)
@@ -574,7 +574,7 @@ class EngineT final : public Engine {
     lc.attrs = at;
     lc.numAttrs = chained ? 1 : 0;
     if (ev0) cudaEventRecord(ev0, s);
-    cuda_check(cudaLaunchKernelEx(&lc, lb_kernel(P.ncalls > 0, narrow_offsets()), A, Bo, P, Pd, k), "LB kernel");
+    cuda_check(cudaLaunchKernelEx(&lc, lb_kernel(P.ncalls > 0, narrow_offsets(), N_ > 0), A, Bo, P, Pd, k), "LB kernel");
     if (ev1) cudaEventRecord(ev1, s);
     cuda_check(cudaGetLastError(), "LB kernel");
   }
@@ -609,12 +609,18 @@ class EngineT final : public Engine {
 
   size_t nsegs() const { return (size_t)((nnodes_ + 31) >> kSegShift); }
 
-  // the LB kernel for noise on/off and 32-bit (all 19 planes below 2^32 elements) or 64-bit
-  // element offsets
+  // the LB kernel for noise on/off, 32-bit (all 19 planes below 2^32 elements) or 64-bit
+  // element offsets, and with or without the deferred force corrections (a chain)
   using LbKernel = void (*)(const S*, S*, const FluidK<R>, const PendK<R>, const uint32_t);
-  static LbKernel lb_kernel(bool noise, bool narrow) {
-    if (noise) return narrow ? k_lb_step<S, R, DEV, true, unsigned> : k_lb_step<S, R, DEV, true, unsigned long long>;
-    return narrow ? k_lb_step<S, R, DEV, false, unsigned> : k_lb_step<S, R, DEV, false, unsigned long long>;
+  static LbKernel lb_kernel(bool noise, bool narrow, bool corr) {
+    using U = unsigned;
+    using W = unsigned long long;
+    if (corr) {
+      if (noise) return narrow ? k_lb_step<S, R, DEV, true, U, true> : k_lb_step<S, R, DEV, true, W, true>;
+      return narrow ? k_lb_step<S, R, DEV, false, U, true> : k_lb_step<S, R, DEV, false, W, true>;
+    }
+    if (noise) return narrow ? k_lb_step<S, R, DEV, true, U, false> : k_lb_step<S, R, DEV, true, W, false>;
+    return narrow ? k_lb_step<S, R, DEV, false, U, false> : k_lb_step<S, R, DEV, false, W, false>;
   }
   bool narrow_offsets() const { return (unsigned long long)Q * plane_ <= 0xFFFFFFFFull; }
 
