@@ -32,7 +32,7 @@ METRIC = "MLUPS and % of HBM roofline: fused FP32 LB+chain vs plain FP64, same G
 L_BENCH, N_BENCH, SEED = 128, 128, 3
 PARAMS = dict(rho=1.0, eta=3.0, eta_b=3.0, kT=1.0, h=0.01, a=1.0)
 CHAIN = dict(m=1.0, zeta=20.8, k_fene=30.0, R0=1.5, eps=1.0, sigma=1.0)
-BYTES_PER_NODE = {"f32": 19 * 4 * 2, "f64": 19 * 8 * 2}  # algorithmic: 19 reads + 19 writes
+BYTES_PER_NODE = {"f32": 19 * 4 * 2, "f64": 19 * 8 * 2, "bf16": 19 * 2 * 2}  # algorithmic: 19 reads + 19 writes
 KERNEL_SOURCES = ["paper_0903_5067_gb300/csrc/lb_device.cuh", "paper_0903_5067_gb300/csrc/d3q19.cuh",
                   "paper_0903_5067_gb300/csrc/philox.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "lb_step_f32_L128_traffic.json")
@@ -338,12 +338,19 @@ def run_ours(args):
         k256 = max(10, args.steps // 40)
         t256 = timed_steps(s256, k256)
         s256.close()
+        sb = make(lb.LB_BF16)  # BF16 storage of the deviations, FP32 arithmetic
+        kb16 = max(20, args.steps // 5)
+        tb16 = timed_steps(sb, kb16)
+        sb.close()
         peak_q = measured_peaks()[0]
         variants = {
             "noise_off_L128": {"value": L ** 3 / tq / 1e6, "unit": "MLUPS", "ms_per_step": tq * 1e3, "steps": kq,
                                "hbm_frac": BYTES_PER_NODE["f32"] * L ** 3 / tq / 1e9 / peak_q},
             "L256": {"value": 256 ** 3 / t256 / 1e6, "unit": "MLUPS", "ms_per_step": t256 * 1e3, "steps": k256,
                      "hbm_frac": BYTES_PER_NODE["f32"] * 256 ** 3 / t256 / 1e9 / peak_q},
+            "bf16_storage_L128": {"value": L ** 3 / tb16 / 1e6, "unit": "MLUPS", "ms_per_step": tb16 * 1e3,
+                                  "steps": kb16,
+                                  "hbm_frac": BYTES_PER_NODE["bf16"] * L ** 3 / tb16 / 1e9 / peak_q},
         }
 
     # chain observables (Sec. III A/B) on a recorded trajectory: 1000 frames of the N=128

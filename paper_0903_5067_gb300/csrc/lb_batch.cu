@@ -65,7 +65,7 @@ template <class S, class R>
 struct BatchRep {
   S* pop[2];
   unsigned long long nnodes, tile0, plane;
-  unsigned seg0;  // first stamp segment of the replica
+  unsigned seg0;  // first mask word of the replica
   unsigned long long* nonpos;
   const R* p_dense[2];  // dense correction fields by slot
   unsigned L;
@@ -298,7 +298,7 @@ class BatchT final : public Batch {
                  "batch bead shared memory");
     cap_max_ = 8;
     for (auto& e : eng_) cap_max_ = e->pending_capacity() > cap_max_ ? e->pending_capacity() : cap_max_;
-    // the engines zeroed their pending counts; no tile carries a stamp a step can match
+    // the engines zeroed their pending counts; no node is marked
     cuda_check(cudaMemsetAsync(flags_[0], 0, 2 * max_segs_ * sizeof(unsigned), s), "memset marks");
     const size_t lbsm = (size_t)Q * 512 * sizeof(R);
     if (lbsm > 48 * 1024) {  // FP64: staged corrections of a 512-node run

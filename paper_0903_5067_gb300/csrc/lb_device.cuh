@@ -5,12 +5,13 @@
 // n_i - w_i rho0 (DEV = true), the FP64 context the full n_i.  A step reads buffer A
 // (post-collision populations of the previous step, "pull" storage) and writes B.
 //
-// One step = k_bead_step (one CTA: velocity Verlet, FENE/WCA, interpolation, friction +
-// noise, spreading -> sparse list of per-node population corrections), k_lb_step (every
-// node: pull-stream, moments, relaxation + noise, back-transform) and k_apply_pending (adds
-// the force corrections to B).  The bead kernel and the LB kernel read only A, so they are
-// independent; the correction is additive on the post-collision populations because the
-// collision conserves the density and momentum it depends on.
+// One step = k_bead_step (one thread block, or a cluster of up to 8: velocity Verlet,
+// FENE/WCA, interpolation, friction + noise, spreading -> sparse list of per-node population
+// corrections), k_lb_step (every node: pull-stream, moments, relaxation + noise,
+// back-transform) and the force corrections, added to B by k_apply_pending or, kept pending,
+// by the next step's kernels where they read.  The bead kernel and the LB kernel read only A,
+// so they are independent; the correction is additive on the post-collision populations
+// because the collision conserves the density and momentum it depends on.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -517,7 +518,7 @@ __global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* _
 }
 
 // ---------------------------------------------------------------------------------------
-// bead / coupling kernel (one CTA)
+// bead / coupling kernel (one thread block or one cluster)
 // ---------------------------------------------------------------------------------------
 // cell of a coordinate: floor(x/a) mod L into [0, L); frac = x/a - floor(x/a)
 template <class R>

@@ -90,9 +90,9 @@ class EngineT final : public Engine {
       cuda_check(cudaMemsetAsync(masks_[j], 0, nsegs() * sizeof(unsigned), s), "memset marks");
   }
 
-  // One coupled step, complete on return: the bead kernel (one CTA), then the LB kernel,
-  // released as soon as the bead CTA is resident (both read only buffer A), then the force
-  // correction adds the bead reaction to buffer B.  One stream.
+  // One coupled step, complete on return: the bead kernel, then the LB kernel, released as
+  // soon as the bead kernel is resident (both read only buffer A), then the force correction
+  // adds the bead reaction to buffer B.  One stream.
   void step(uint32_t k, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) override {
     flush(s);
     const FluidK<R> P = fluid();
@@ -110,8 +110,8 @@ class EngineT final : public Engine {
   }
 
   // One coupled step whose force correction stays pending: the next deferred step adds it
-  // where it reads the populations (the LB tiles stamped by this step, the bead kernel in
-  // its gather), and flush() applies it.  Stream order gives every dependency: the bead
+  // where it reads the populations (the LB kernel at the nodes this step marks, the bead
+  // kernel in its gather), and flush() applies it.  Stream order gives every dependency: the bead
   // kernel of step k starts after the LB and bead kernels of step k-1 have completed, and
   // the LB kernel of step k, released early, touches nothing the bead kernel of step k
   // reads or writes.
@@ -587,7 +587,7 @@ class EngineT final : public Engine {
   }
 
   // pending-correction block: deferred steps read slot pslot_^1 (when open) and write
-  // pslot_ with stamps; complete steps write slot pslot_ only, without stamps
+  // pslot_ with node marks; complete steps write slot pslot_ only, without marks
   PendK<R> pend(bool deferred) const {
     PendK<R> Pd;
     memset(&Pd, 0, sizeof(Pd));
