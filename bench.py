@@ -386,6 +386,27 @@ def run_ours(args):
                   "work": "g1/g2/g3 to lag 500; Rouse modes p=1..127 and correlation to lag 500; S(k) at 16 k; "
                           "S(k,t) at 4 k, lags 0..100, origins every 20 frames; FP64, host-timed with sync"}
 
+    # Brownian dynamics with hydrodynamic interaction (Sec. II C): 64 chains of the paper's
+    # production model (N = 32), one thread block per chain, RPY mobility and Fixman's
+    # Chebyshev square root (degree 20, 20 power iterations for the bounds) every step
+    bd = None
+    if not args.no_bd:
+        Xb = np.stack([inputs.chain_walk(32, L=1000, bond=0.97, seed=100 + r, self_avoiding=True) for r in range(64)])
+        sbd = lb.BD(Xb, precision=lb.LB_FP32, seed=2)
+        sbd.step(20)
+        sbd.sync()
+        kbd = max(200, args.steps // 5)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        sbd.step(kbd)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        tbd = b0.elapsed_time(b1) / 1e3 / kbd
+        sbd.close()
+        bd = {"chains": 64, "N": 32, "steps": kbd, "us_per_step": tbd * 1e6, "chain_steps_per_s": 64 / tbd,
+              "work": "per chain and step: RPY mobility (96 x 96), 40 power-iteration and 20 Chebyshev "
+                      "mat-vecs, FENE + WCA, Ito-Euler update; FP32, HI on"}
+
     value, tmax = aggregate_throughput(L ** 3 * args.steps / 1e6, t32, ws, dev)
     v64, _ = aggregate_throughput(L ** 3 * k64 / 1e6, t64, ws, dev)
 
@@ -447,6 +468,7 @@ def run_ours(args):
         "bead_steps_per_s": N * args.steps * ws / tmax,
         "batch_c4": batch,
         "observables_f3": observ,
+        "bd_f4": bd,
         "variants": variants,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "C ABI, pinned host buffers: set_populations, K x (step + asynchronous bead read-back, each waited for one step later), get_populations"},
@@ -473,6 +495,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-observables", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-bd", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
