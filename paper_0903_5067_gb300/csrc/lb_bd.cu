@@ -60,13 +60,22 @@ __device__ R block_sum(R v, R* red) {
 }
 
 // out = a * (M v) + b * v + c * u (M symmetric, n x n, leading dimension n; u may be null);
-// one thread per output row, reading M by columns
+// one thread per output row, reading M by columns, with four partial sums (columns mod 4) so
+// that the dependent chain of multiply-adds is a quarter as long
 template <class R>
 __device__ __forceinline__ void matvec(const R* __restrict__ M, int n, const R* __restrict__ v, R a, R b, R c,
                                        const R* __restrict__ u, R* __restrict__ out) {
   for (int row = threadIdx.x; row < n; row += blockDim.x) {
-    R s = R(0);
-    for (int col = 0; col < n; ++col) s += M[col * n + row] * v[col];
+    R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
+    int col = 0;
+    for (; col + 3 < n; col += 4) {
+      s0 += M[col * n + row] * v[col];
+      s1 += M[(col + 1) * n + row] * v[col + 1];
+      s2 += M[(col + 2) * n + row] * v[col + 2];
+      s3 += M[(col + 3) * n + row] * v[col + 3];
+    }
+    for (; col < n; ++col) s0 += M[col * n + row] * v[col];
+    const R s = (s0 + s1) + (s2 + s3);
     R o = a * s + b * v[row];
     if (u) o += c * u[row];
     out[row] = o;
@@ -122,8 +131,8 @@ __global__ void __launch_bounds__(kBDThreads) k_bd_steps(const BDK<R> P, uint32_
     }
     // mobility D/kT: zeta^-1 on the diagonal blocks, regularised RPY elsewhere
     const R self = rcp(P.zeta);
-    for (int pr = tid; pr < N * N; pr += nt) {
-      const int i = pr / N, j = pr - (pr / N) * N;
+    for (int pr = tid; pr < N * N; pr += nt) {  // consecutive threads: consecutive i (store stride 3)
+      const int j = pr / N, i = pr - (pr / N) * N;
       R blk[3][3];
       if (i == j || !P.hi) {
 #pragma unroll
@@ -170,13 +179,20 @@ __global__ void __launch_bounds__(kBDThreads) k_bd_steps(const BDK<R> P, uint32_
       const R inv = rcp(sqrt(R(n)));
       for (int t = tid; t < n; t += nt) t0[t] = inv;
       __syncthreads();
+      // the iterate is normalised every fourth iteration and after the last (the direction,
+      // and so the Rayleigh quotient below, does not depend on it; four unnormalised
+      // iterations change the norm by at most lam_max^4)
       for (int k = 0; k < P.piters; ++k) {
         matvec<R>(M, n, t0, P.kT, R(0), R(0), nullptr, t1);
         __syncthreads();
-        R part = R(0);
-        for (int t = tid; t < n; t += nt) part += t1[t] * t1[t];
-        const R nrm = rcp(sqrt(block_sum<R>(part, red)));
-        for (int t = tid; t < n; t += nt) t0[t] = t1[t] * nrm;
+        if ((k & 3) == 3 || k == P.piters - 1) {
+          R part = R(0);
+          for (int t = tid; t < n; t += nt) part += t1[t] * t1[t];
+          const R nrm = rcp(sqrt(block_sum<R>(part, red)));
+          for (int t = tid; t < n; t += nt) t0[t] = t1[t] * nrm;
+        } else {
+          for (int t = tid; t < n; t += nt) t0[t] = t1[t];
+        }
         __syncthreads();
       }
       matvec<R>(M, n, t0, P.kT, R(0), R(0), nullptr, t1);
@@ -189,10 +205,14 @@ __global__ void __launch_bounds__(kBDThreads) k_bd_steps(const BDK<R> P, uint32_
       for (int k = 0; k < P.piters; ++k) {
         matvec<R>(M, n, t0, -P.kT, lam_max, R(0), nullptr, t1);  // (lam_max I - D) v
         __syncthreads();
-        R pp = R(0);
-        for (int t = tid; t < n; t += nt) pp += t1[t] * t1[t];
-        const R nrm = rcp(sqrt(block_sum<R>(pp, red)));
-        for (int t = tid; t < n; t += nt) t0[t] = t1[t] * nrm;
+        if ((k & 3) == 3 || k == P.piters - 1) {
+          R pp = R(0);
+          for (int t = tid; t < n; t += nt) pp += t1[t] * t1[t];
+          const R nrm = rcp(sqrt(block_sum<R>(pp, red)));
+          for (int t = tid; t < n; t += nt) t0[t] = t1[t] * nrm;
+        } else {
+          for (int t = tid; t < n; t += nt) t0[t] = t1[t];
+        }
         __syncthreads();
       }
       matvec<R>(M, n, t0, -P.kT, lam_max, R(0), nullptr, t1);
