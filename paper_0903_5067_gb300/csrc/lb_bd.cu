@@ -59,26 +59,31 @@ __device__ R block_sum(R v, R* red) {
   return s;
 }
 
-// out = a * (M v) + b * v + c * u (M symmetric, n x n, leading dimension n; u may be null);
-// one thread per output row, reading M by columns, with four partial sums (columns mod 4) so
-// that the dependent chain of multiply-adds is a quarter as long
+// out = a * (M v) + b * v + c * u (M symmetric, n x n, leading dimension n; u may be null),
+// and, with y, also y += cy * out.  Two neighbouring threads per output row, each over half
+// the columns with two partial sums (M read by columns: consecutive rows are consecutive
+// words), combined by a shuffle; the pair's even thread writes.
 template <class R>
 __device__ __forceinline__ void matvec(const R* __restrict__ M, int n, const R* __restrict__ v, R a, R b, R c,
-                                       const R* __restrict__ u, R* __restrict__ out) {
-  for (int row = threadIdx.x; row < n; row += blockDim.x) {
-    R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
-    int col = 0;
-    for (; col + 3 < n; col += 4) {
+                                       const R* __restrict__ u, R* __restrict__ out, R* __restrict__ y = nullptr,
+                                       R cy = R(0)) {
+  const int half = threadIdx.x & 1, h0 = half ? n / 2 : 0, h1 = half ? n : n / 2;
+  for (int row = threadIdx.x >> 1; row < n; row += blockDim.x >> 1) {
+    R s0 = R(0), s1 = R(0);
+    int col = h0;
+    for (; col + 1 < h1; col += 2) {
       s0 += M[col * n + row] * v[col];
       s1 += M[(col + 1) * n + row] * v[col + 1];
-      s2 += M[(col + 2) * n + row] * v[col + 2];
-      s3 += M[(col + 3) * n + row] * v[col + 3];
     }
-    for (; col < n; ++col) s0 += M[col * n + row] * v[col];
-    const R s = (s0 + s1) + (s2 + s3);
-    R o = a * s + b * v[row];
-    if (u) o += c * u[row];
-    out[row] = o;
+    if (col < h1) s0 += M[col * n + row] * v[col];
+    R sum = s0 + s1;
+    sum += __shfl_xor_sync(__activemask(), sum, 1);  // the pair (2k, 2k+1) is active together
+    if (!half) {
+      R o = a * sum + b * v[row];
+      if (u) o += c * u[row];
+      out[row] = o;
+      if (y) y[row] += cy * o;
+    }
   }
 }
 
@@ -182,17 +187,24 @@ __global__ void __launch_bounds__(kBDThreads) k_bd_steps(const BDK<R> P, uint32_
       // the iterate is normalised every fourth iteration and after the last (the direction,
       // and so the Rayleigh quotient below, does not depend on it; four unnormalised
       // iterations change the norm by at most lam_max^4)
+      R* pa = t0;  // the iterate
+      R* pb = t1;
       for (int k = 0; k < P.piters; ++k) {
-        matvec<R>(M, n, t0, P.kT, R(0), R(0), nullptr, t1);
+        matvec<R>(M, n, pa, P.kT, R(0), R(0), nullptr, pb);
         __syncthreads();
         if ((k & 3) == 3 || k == P.piters - 1) {
           R part = R(0);
-          for (int t = tid; t < n; t += nt) part += t1[t] * t1[t];
+          for (int t = tid; t < n; t += nt) part += pb[t] * pb[t];
           const R nrm = rcp(sqrt(block_sum<R>(part, red)));
-          for (int t = tid; t < n; t += nt) t0[t] = t1[t] * nrm;
-        } else {
-          for (int t = tid; t < n; t += nt) t0[t] = t1[t];
+          for (int t = tid; t < n; t += nt) pb[t] *= nrm;
+          __syncthreads();
         }
+        R* sw = pa;
+        pa = pb;
+        pb = sw;
+      }
+      if (pa != t0) {  // the iterate back into t0
+        for (int t = tid; t < n; t += nt) t0[t] = pa[t];
         __syncthreads();
       }
       matvec<R>(M, n, t0, P.kT, R(0), R(0), nullptr, t1);
@@ -202,17 +214,24 @@ __global__ void __launch_bounds__(kBDThreads) k_bd_steps(const BDK<R> P, uint32_
       const R lam_max = R(1.05) * block_sum<R>(part, red);
       for (int t = tid; t < n; t += nt) t0[t] = inv;
       __syncthreads();
+      pa = t0;
+      pb = t1;
       for (int k = 0; k < P.piters; ++k) {
-        matvec<R>(M, n, t0, -P.kT, lam_max, R(0), nullptr, t1);  // (lam_max I - D) v
+        matvec<R>(M, n, pa, -P.kT, lam_max, R(0), nullptr, pb);  // (lam_max I - D) v
         __syncthreads();
         if ((k & 3) == 3 || k == P.piters - 1) {
           R pp = R(0);
-          for (int t = tid; t < n; t += nt) pp += t1[t] * t1[t];
+          for (int t = tid; t < n; t += nt) pp += pb[t] * pb[t];
           const R nrm = rcp(sqrt(block_sum<R>(pp, red)));
-          for (int t = tid; t < n; t += nt) t0[t] = t1[t] * nrm;
-        } else {
-          for (int t = tid; t < n; t += nt) t0[t] = t1[t];
+          for (int t = tid; t < n; t += nt) pb[t] *= nrm;
+          __syncthreads();
         }
+        R* sw = pa;
+        pa = pb;
+        pb = sw;
+      }
+      if (pa != t0) {
+        for (int t = tid; t < n; t += nt) t0[t] = pa[t];
         __syncthreads();
       }
       matvec<R>(M, n, t0, -P.kT, lam_max, R(0), nullptr, t1);
@@ -239,18 +258,18 @@ __global__ void __launch_bounds__(kBDThreads) k_bd_steps(const BDK<R> P, uint32_
       matvec<R>(M, n, W, sc * P.kT, -tc, R(0), nullptr, t1);  // T_1 W
       __syncthreads();
       for (int t = tid; t < n; t += nt) y[t] = coef[0] * W[t] + coef[1] * t1[t];
+      __syncthreads();  // y and t1 are next touched by other threads (the mat-vecs' rows)
       R* tp = W;   // T_{k-1}
       R* tcur = t1;  // T_k
       R* tn = t2;
       for (int k = 2; k < K; ++k) {
-        matvec<R>(M, n, tcur, R(2) * sc * P.kT, R(-2) * tc, R(-1), tp, tn);  // 2 Dt T_k - T_{k-1}
+        // 2 Dt T_k - T_{k-1}, added to y times c_k by the thread that forms each row
+        matvec<R>(M, n, tcur, R(2) * sc * P.kT, R(-2) * tc, R(-1), tp, tn, y, coef[k]);
         __syncthreads();
-        for (int t = tid; t < n; t += nt) y[t] += coef[k] * tn[t];
         R* sw = tp;
         tp = tcur;
         tcur = tn;
         tn = (sw == W) ? t0 : sw;  // never overwrite W before the recurrence is done
-        __syncthreads();
       }
     } else {
       const R amp = sqrt(P.kT / P.zeta);
