@@ -121,14 +121,17 @@ int lb_set_populations(lb_ctx* ctx, const double* in, size_t count);
  * NULL.  Synchronising.  Before the first device call it returns the staged initial chain
  * (given or generated by lb_add_chain) without touching the device. */
 int lb_get_beads(lb_ctx* ctx, double* x, double* v, size_t cap);
-/* The same read-back enqueued on the context stream without waiting, so that the caller can
- * keep steps queued while earlier results travel: x, v (3N doubles each, v may be NULL) must
- * stay valid until the read-back completes and should be pinned (page-locked) host memory for
- * the copies to be asynchronous.  *ticket identifies the read-back; lb_wait(ctx, ticket)
- * blocks until it (and everything enqueued before it) has completed and returns the device
- * status latched at that point.  Tickets older than the last 8 remain valid (a later
- * read-back completes after them).  Needs a chain and a live context (LB_ERR_ARG otherwise:
- * a bad pointer, size or ticket). */
+/* The same read-back without waiting, so that the caller can keep steps queued while earlier
+ * results travel: it follows everything enqueued on the context stream before the call, and
+ * its copies (from a snapshot the bead kernel writes at the end of every step) run on the
+ * library's own stream, so that steps enqueued afterwards proceed meanwhile.  x, v (3N
+ * doubles each, v may be NULL) must stay valid until the read-back completes and should be
+ * pinned (page-locked) host memory for the copies to be asynchronous.  *ticket identifies the
+ * read-back; lb_wait(ctx, ticket) blocks until it (and everything enqueued on the context
+ * stream before it) has completed and returns the device status latched at that point.
+ * Read-backs complete in the order they were asked for; tickets older than the last 8 remain
+ * valid.  Needs a chain and a live context (LB_ERR_ARG otherwise: a bad pointer, size or
+ * ticket). */
 int lb_get_beads_async(lb_ctx* ctx, double* x, double* v, size_t cap, int64_t* ticket);
 int lb_wait(lb_ctx* ctx, int64_t ticket);
 
