@@ -386,6 +386,31 @@ def run_ours(args):
                   "work": "g1/g2/g3 to lag 500; Rouse modes p=1..127 and correlation to lag 500; S(k) at 16 k; "
                           "S(k,t) at 4 k, lags 0..100, origins every 20 frames; FP64, host-timed with sync"}
 
+    # the adjoint of the coupled step (gradient of sum_b |x_b(T) - x_b(0)|^2 with respect to the
+    # initial positions and zeta, noise held fixed): L = 32, N = 16, T = 100, checkpoints every
+    # 10 steps, FP32; one call runs the forward pass, the checkpointed recomputation and the
+    # reverse sweep
+    adj = None
+    if not args.no_adjoint:
+        Xa = inputs.chain_walk(16, L=32, bond=0.97, seed=7, self_avoiding=True)
+        calls = []
+        for rep in range(3):
+            sa = lb.Simulation(L=32, seed=7, precision=lb.LB_FP32, **PARAMS)
+            sa.add_chain(16, x0=Xa, **CHAIN)
+            sa._bind()
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            lb.lb_adjoint_displacement(sa.ctx, 100, 10, 16)
+            torch.cuda.synchronize()
+            calls.append(time.perf_counter() - ta)
+            sa.close()
+        ta = min(calls[1:])
+        adj = {"L": 32, "N": 16, "steps": 100, "checkpoint_every": 10, "ms_per_call": ta * 1e3,
+               "us_per_step_forward_and_reverse": ta / 100 * 1e6,
+               "work": "forward 100 steps with checkpoints, recomputation of each 10-step segment and the "
+                       "reverse sweep (adjoint LB and bead kernels); FP32; host-timed, best of 2 after one "
+                       "warm-up call"}
+
     # Brownian dynamics with hydrodynamic interaction (Sec. II C): 64 chains of the paper's
     # production model (N = 32), one thread block per chain, RPY mobility and Fixman's
     # Chebyshev square root (degree 20, 20 power iterations for the bounds) every step
@@ -469,6 +494,7 @@ def run_ours(args):
         "batch_c4": batch,
         "observables_f3": observ,
         "bd_f4": bd,
+        "adjoint_c5": adj,
         "variants": variants,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "C ABI, pinned host buffers: set_populations, K x (step + asynchronous bead read-back, each waited for one step later), get_populations"},
@@ -496,6 +522,7 @@ def main():
     ap.add_argument("--no-observables", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-bd", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
