@@ -405,11 +405,24 @@ def run_ours(args):
             calls.append(time.perf_counter() - ta)
             sa.close()
         ta = min(calls[1:])
+        fwd = []
+        for rep in range(3):
+            sf = lb.Simulation(L=32, seed=7, precision=lb.LB_FP32, **PARAMS)
+            sf.add_chain(16, x0=Xa, **CHAIN)
+            sf._bind()
+            torch.cuda.synchronize()
+            tf = time.perf_counter()
+            sf.step(100)
+            sf.sync()
+            fwd.append(time.perf_counter() - tf)
+            sf.close()
+        tf = min(fwd[1:])
         adj = {"L": 32, "N": 16, "steps": 100, "checkpoint_every": 10, "ms_per_call": ta * 1e3,
-               "us_per_step_forward_and_reverse": ta / 100 * 1e6,
+               "us_per_step_forward_and_reverse": ta / 100 * 1e6, "forward_ms": tf * 1e3,
+               "adjoint_over_forward": ta / tf,
                "work": "forward 100 steps with checkpoints, recomputation of each 10-step segment and the "
                        "reverse sweep (adjoint LB and bead kernels); FP32; host-timed, best of 2 after one "
-                       "warm-up call"}
+                       "warm-up call; forward_ms: the same 100 steps through lb_step alone"}
 
     # Brownian dynamics with hydrodynamic interaction (Sec. II C): 64 chains of the paper's
     # production model (N = 32), one thread block per chain, RPY mobility and Fixman's
