@@ -149,3 +149,133 @@ def test_uniformly_forced_fluid_stress_follows_the_forcing_recurrence():
         x_pred = Gamma(x_pred) - 0.5 * (D - Gamma(D))
         n = o.collide(nps, fp, step=t)
     assert np.abs(x_pred).max() > 1e-8  # the recurrence was exercised
+
+
+def _linear_operator(fp, kvec):
+    """One step of the LB linearised about the fluid at rest, for a Fourier mode exp(i k.r):
+    pull streaming multiplies population i by exp(-i k.e_i); the collision keeps the
+    conserved moments 0..3 and multiplies moment k >= 4 by gamma_k (the equilibrium moments
+    beyond momentum are quadratic in U and drop out at linear order).  Step = collide after
+    stream: n_{t+1} = M^-1 diag(lambda) M S(k) n_t."""
+    lam = o.relaxation(fp).copy()
+    lam[:4] = 1.0
+    C = o.MINV @ np.diag(lam) @ o.M
+    S = np.diag(np.exp(-1j * (o.E.astype(float) @ kvec)))
+    return C @ S
+
+
+def test_small_perturbation_follows_the_linearised_operator_exactly():
+    """A small plane-wave perturbation with an arbitrary population profile, along a wave
+    vector that is not a lattice axis, evolves under the oracle's nonlinear stream + collide
+    as powers of the 19 x 19 linear operator.  The odd part in the amplitude (runs at +eps and
+    -eps) removes the quadratic terms of the equilibrium; what is left is O(eps^2) relative
+    (checked: a tenfold smaller amplitude shrinks it a hundredfold) down to round-off."""
+    L = 8
+    fp = o.FluidParams(L=L, rho=1.0, eta=3.0, eta_b=1.5, kT=0.0, h=0.01, noise_fluid=False)
+    kvec = 2 * np.pi / L * np.array([1.0, 1.0, 2.0])
+    rng = np.random.default_rng(9)
+    v = rng.standard_normal(o.Q) + 1j * rng.standard_normal(o.Q)
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    phase = np.exp(1j * (kvec[0] * x + kvec[1] * y + kvec[2] * z))  # (z, y, x)
+    base = o.fluid_at_rest(fp)
+    T = 12
+    vT = np.linalg.matrix_power(_linear_operator(fp, kvec), T) @ v
+
+    def misfit(eps):
+        runs = []
+        for sgn in (1.0, -1.0):
+            n = base + sgn * eps * np.real(v[:, None, None, None] * phase[None])
+            for k in range(T):
+                n = o.collide(o.stream(n), fp, step=k)
+            runs.append(n)
+        odd = 0.5 * (runs[0] - runs[1])
+        want = eps * np.real(vT[:, None, None, None] * phase[None])
+        assert np.abs(want).max() > 1e-3 * eps  # the mode has not decayed away
+        return np.abs(odd - want).max() / np.abs(want).max(), odd, want
+
+    r4, _, _ = misfit(1e-4)
+    r5, _, _ = misfit(1e-5)
+    assert 60.0 < r4 / r5 < 160.0  # the misfit is the cubic term of the equilibrium
+    r6, odd, want = misfit(1e-6)
+    assert r6 < 3e-9
+    eps = 1e-6
+    # streaming the other way (push instead of pull) would not match
+    wrong = np.linalg.matrix_power(_linear_operator(fp, -kvec), T) @ v
+    wrong = eps * np.real(wrong[:, None, None, None] * phase[None])
+    assert np.abs(odd - wrong).max() > 1e-3 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("L,tol", [(16, 0.009), (32, 0.0022)])
+def test_shear_eigenvalue_of_the_linear_operator_approaches_hydrodynamics(L, tol):
+    """For k along z the two transverse-momentum eigenvalues of the linear operator are the
+    shear modes; their magnitude approaches exp(-nu k^2 h) as k -> 0 (lattice corrections of
+    relative order k^2), and the oracle's shear wave decays at exactly that eigenvalue."""
+    fp = o.FluidParams(L=L, rho=1.0, eta=3.0, eta_b=3.0, kT=0.0, h=0.01, noise_fluid=False)
+    kz = 2 * np.pi / L
+    Lk = _linear_operator(fp, np.array([0.0, 0.0, kz]))
+    w, V = np.linalg.eig(Lk)
+    # eigenvectors carrying x-momentum
+    jx = np.abs(o.E[:, 0].astype(float) @ V)
+    i = int(np.argmax(jx))
+    lam = w[i]
+    assert abs(lam.imag) < 1e-12
+    want = math.exp(-fp.eta / fp.rho * kz * kz * fp.h)
+    assert abs(lam.real) == pytest.approx(want, rel=tol)
+    # the oracle's shear wave: amplitude ratio over 100 steps once the non-hydrodynamic
+    # transients (|gamma_s|^t) have died out
+    z = np.arange(L)
+    U = np.zeros((3, L, L, L))
+    U[0] = (1e-6 * np.sin(kz * z))[:, None, None]
+    n = o.n_eq(np.ones((L, L, L)), U)
+    sinz = np.sin(kz * z)
+    amps = []
+    for k in range(160):
+        n = o.collide(o.stream(n), fp, step=k)
+        jx_z = np.einsum("i,izyx->z", o.E[:, 0].astype(float), n)
+        amps.append(2.0 / L * (jx_z * sinz).sum())
+    assert (amps[159] / amps[59]) ** 0.01 == pytest.approx(lam.real, rel=1e-11)
+
+
+@pytest.mark.parametrize("L,tol_damp,tol_freq", [(16, 5e-4, 5e-3), (32, 1.5e-4, 1.25e-3)])
+def test_sound_eigenvalues_of_the_linear_operator(L, tol_damp, tol_freq):
+    """For k along z the two density-carrying eigenvalues of largest magnitude are the sound
+    pair exp(-Gamma h +- i c_s k h), Gamma = (4 eta/3 + eta_b) k^2 / (2 rho), c_s = a/(h sqrt 3):
+    the damping pins the bulk relaxation rate (eta_b != eta here), the frequency the speed of
+    sound; both approach the closed forms as k^2."""
+    fp = o.FluidParams(L=L, rho=1.0, eta=3.0, eta_b=1.5, kT=0.0, h=0.01, noise_fluid=False)
+    kz = 2 * np.pi / L
+    w, V = np.linalg.eig(_linear_operator(fp, np.array([0.0, 0.0, kz])))
+    carries_rho = np.abs(np.ones(o.Q) @ V)
+    pair = np.argsort(-carries_rho * np.abs(w))[:2]
+    gamma = (4.0 / 3.0 * fp.eta + fp.eta_b) * kz * kz / (2.0 * fp.rho) * fp.h
+    for j in pair:
+        assert -math.log(abs(w[j])) == pytest.approx(gamma, rel=tol_damp)
+        assert abs(np.angle(w[j])) == pytest.approx(kz / math.sqrt(3.0), rel=tol_freq)
+    assert np.angle(w[pair[0]]) == pytest.approx(-np.angle(w[pair[1]]), rel=1e-12)
+
+
+def test_collision_projects_out_the_kinetic_modes():
+    """Reading of the kinetic-mode rate (gamma = 0 for modes 10..18, the paper being silent):
+    with the noise off, one collision of an arbitrary non-equilibrium state leaves every
+    kinetic moment at zero, keeps rho and J, and relaxes the stress modes by gamma_b, gamma_s
+    about their equilibrium values."""
+    L = 3
+    fp = o.FluidParams(L=L, rho=1.0, eta=3.0, eta_b=1.5, kT=0.0, h=0.01, noise_fluid=False)
+    rng = np.random.default_rng(4)
+    n = o.fluid_at_rest(fp) * (1.0 + 0.2 * rng.random((o.Q, L, L, L)))
+    out = o.collide(n, fp, step=0)
+    m_in = o.M @ n.reshape(o.Q, -1)
+    m_out = o.M @ out.reshape(o.Q, -1)
+    assert np.abs(m_out[10:]).max() < 1e-15
+    assert np.allclose(m_out[:4], m_in[:4], rtol=0, atol=1e-15)
+    rho, J = m_in[0], m_in[1:4]
+    meq = o.M @ o.n_eq(rho, J / rho[None])
+    # eta = rho c_s^2 h (1 + g) / (2 (1 - g)) and eta_b = rho c_s^2 h (1 + g_b) / (3 (1 - g_b))
+    # with c_s^2 = a^2 / (3 h^2): solve for the stress eigenvalues
+    x = 6.0 * fp.eta * fp.h / (fp.rho * fp.a ** 2)
+    gs = (x - 1.0) / (x + 1.0)
+    xb = 9.0 * fp.eta_b * fp.h / (fp.rho * fp.a ** 2)
+    gb = (xb - 1.0) / (xb + 1.0)
+    assert np.allclose(m_out[4], meq[4] + gb * (m_in[4] - meq[4]), rtol=0, atol=1e-15)
+    for k in range(5, 10):
+        assert np.allclose(m_out[k], meq[k] + gs * (m_in[k] - meq[k]), rtol=0, atol=1e-15)
