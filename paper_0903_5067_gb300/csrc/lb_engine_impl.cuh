@@ -151,8 +151,19 @@ class EngineT final : public Engine {
     if (T < 1 || K < 1) throw LbError(S_ARG, "T and K must be >= 1");
     const size_t popb = (size_t)Q * plane_ * sizeof(S);
     const size_t n3 = 3 * (size_t)N_;
-    const size_t beadb = n3 * (5 * sizeof(R) + sizeof(int));
+    // layout() places the six bead arrays x_, xl_, img_, v_, F_, Fc_ one after the other, so
+    // a saved state is the population field plus one copy of that span
+    unsigned char* const bead0 = reinterpret_cast<unsigned char*>(x_);
+    const size_t beadb = (size_t)(reinterpret_cast<unsigned char*>(Fc_ + n3) - bead0);
+    {
+      const unsigned char* arr[6] = {bead0, reinterpret_cast<unsigned char*>(xl_),
+                                     reinterpret_cast<unsigned char*>(img_), reinterpret_cast<unsigned char*>(v_),
+                                     reinterpret_cast<unsigned char*>(F_), reinterpret_cast<unsigned char*>(Fc_)};
+      for (int i = 1; i < 6; ++i)
+        if (arr[i] <= arr[i - 1]) throw LbError(S_STATE, "bead arrays are not laid out in order");
+    }
     const int nck = (int)((T + K - 1) / K);
+    const size_t stb = align_up(popb + beadb, 256);  // one saved state, 256-byte aligned
     const size_t lamb = (size_t)Q * plane_ * sizeof(R);
     // scratch layout
     size_t off = 0;
@@ -162,9 +173,9 @@ class EngineT final : public Engine {
       off += b;
       return o;
     };
-    const size_t o_ck = take((size_t)nck * (popb + beadb));
-    const size_t o_seg = take((size_t)K * (popb + beadb));
-    const size_t o_fin = take(popb + beadb);
+    const size_t o_ck = take((size_t)nck * stb);
+    const size_t o_seg = take((size_t)K * stb);
+    const size_t o_fin = take(stb);
     const size_t o_lam0 = take(lamb), o_lam1 = take(lamb);
     const size_t o_bar = take(3 * n3 * sizeof(R));
     const size_t o_adj = take(10 * n3 * sizeof(R) + (size_t)cap_ * (3 + 1 + 4) * sizeof(R) + cap_ * sizeof(int) +
@@ -180,26 +191,14 @@ class EngineT final : public Engine {
     } guard{base};
     auto save_state = [&](unsigned char* dst) {
       cuda_check(cudaMemcpyAsync(dst, pop_[cur_], popb, cudaMemcpyDeviceToDevice, s), "save pops");
-      unsigned char* q = dst + popb;
-      for (auto pr : {std::make_pair((void*)x_, n3 * sizeof(R)), std::make_pair((void*)xl_, n3 * sizeof(R)),
-                      std::make_pair((void*)v_, n3 * sizeof(R)), std::make_pair((void*)F_, n3 * sizeof(R)),
-                      std::make_pair((void*)Fc_, n3 * sizeof(R)), std::make_pair((void*)img_, n3 * sizeof(int))}) {
-        cuda_check(cudaMemcpyAsync(q, pr.first, pr.second, cudaMemcpyDeviceToDevice, s), "save beads");
-        q += pr.second;
-      }
+      cuda_check(cudaMemcpyAsync(dst + popb, bead0, beadb, cudaMemcpyDeviceToDevice, s), "save beads");
     };
     auto load_state = [&](const unsigned char* src, bool pops) {
       if (pops) cuda_check(cudaMemcpyAsync(pop_[cur_], src, popb, cudaMemcpyDeviceToDevice, s), "load pops");
-      const unsigned char* q = src + popb;
-      for (auto pr : {std::make_pair((void*)x_, n3 * sizeof(R)), std::make_pair((void*)xl_, n3 * sizeof(R)),
-                      std::make_pair((void*)v_, n3 * sizeof(R)), std::make_pair((void*)F_, n3 * sizeof(R)),
-                      std::make_pair((void*)Fc_, n3 * sizeof(R)), std::make_pair((void*)img_, n3 * sizeof(int))}) {
-        cuda_check(cudaMemcpyAsync(pr.first, q, pr.second, cudaMemcpyDeviceToDevice, s), "load beads");
-        q += pr.second;
-      }
+      cuda_check(cudaMemcpyAsync(bead0, src + popb, beadb, cudaMemcpyDeviceToDevice, s), "load beads");
     };
-    auto ck = [&](int i) { return base + o_ck + (size_t)i * (popb + beadb); };
-    auto seg = [&](int i) { return base + o_seg + (size_t)i * (popb + beadb); };
+    auto ck = [&](int i) { return base + o_ck + (size_t)i * stb; };
+    auto seg = [&](int i) { return base + o_seg + (size_t)i * stb; };
     // 1. forward pass with checkpoints
     std::vector<double> x0h(n3), xTh(n3);
     get_beads(x0h.data(), nullptr, s);
