@@ -118,6 +118,19 @@ def _dbuf(a):
     return a.ctypes.data_as(_dp) if a is not None else None
 
 
+def _out64(a, need: int, where: str):
+    """Pointer to a caller's output array after checking that the library may write `need`
+    doubles into it (None passes through): the C side only knows the capacity it is told."""
+    if a is None:
+        return None
+    if (not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous
+            or not a.flags.writeable):
+        raise ValueError(f"{where}: output must be a writable C-contiguous float64 numpy array")
+    if a.size < need:
+        raise ValueError(f"{where}: output holds {a.size} values, {need} are written")
+    return a.ctypes.data_as(_dp)
+
+
 # --- C functions, same names -----------------------------------------------------------
 def lb_strerror(code: int) -> str:
     return _lib.lb_strerror(code).decode()
@@ -132,12 +145,17 @@ def lb_create(L, rho, eta, eta_b, kT, h, a, seed, precision):
 def lb_add_chain(ctx, N, m, zeta, k_fene, R0, eps, sigma, x0=None, v0=None, bond=0.97, saw=1):
     x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).reshape(-1)
     v0 = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float64).reshape(-1)
+    for name, arr in (("x0", x0), ("v0", v0)):
+        if arr is not None and arr.size != 3 * int(N):
+            raise ValueError(f"lb_add_chain: {name} must hold 3 N = {3 * int(N)} values, got {arr.size}")
     _check(_lib.lb_add_chain(ctx, int(N), m, zeta, k_fene, R0, eps, sigma, _dbuf(x0), _dbuf(v0), bond, int(saw)),
            "lb_add_chain")
 
 
 def lb_set_options(ctx, noise_fluid=1, noise_beads=1, stress_only=0, ext_bead_force=None, counter_force_fluid=0):
-    ext = None if ext_bead_force is None else np.ascontiguousarray(ext_bead_force, dtype=np.float64)
+    ext = None if ext_bead_force is None else np.ascontiguousarray(ext_bead_force, dtype=np.float64).reshape(-1)
+    if ext is not None and ext.size != 3:
+        raise ValueError("lb_set_options: ext_bead_force must hold 3 values")
     _check(_lib.lb_set_options(ctx, int(noise_fluid), int(noise_beads), int(stress_only), _dbuf(ext),
                                int(counter_force_fluid)), "lb_set_options")
 
@@ -173,8 +191,7 @@ def lb_sync(ctx):
 
 
 def lb_get_populations(ctx, out: np.ndarray):
-    assert out.dtype == np.float64 and out.flags.c_contiguous
-    _check(_lib.lb_get_populations(ctx, _dbuf(out), out.size), "lb_get_populations")
+    _check(_lib.lb_get_populations(ctx, _out64(out, 0, "lb_get_populations"), out.size), "lb_get_populations")
 
 
 def lb_set_populations(ctx, arr: np.ndarray):
@@ -183,14 +200,16 @@ def lb_set_populations(ctx, arr: np.ndarray):
 
 
 def lb_get_beads(ctx, x: np.ndarray | None, v: np.ndarray | None, cap: int):
-    _check(_lib.lb_get_beads(ctx, _dbuf(x), _dbuf(v), cap), "lb_get_beads")
+    _check(_lib.lb_get_beads(ctx, _out64(x, cap, "lb_get_beads"), _out64(v, cap, "lb_get_beads"), cap),
+           "lb_get_beads")
 
 
 def lb_get_beads_async(ctx, x: np.ndarray, v, cap: int) -> int:
     """Enqueue a bead read-back into x (and v) without waiting; returns the ticket for
     lb_wait.  The arrays must stay alive (and should be pinned) until then."""
     t = C.c_int64()
-    _check(_lib.lb_get_beads_async(ctx, _dbuf(x), _dbuf(v), cap, C.byref(t)),
+    _check(_lib.lb_get_beads_async(ctx, _out64(x, cap, "lb_get_beads_async"),
+                                   _out64(v, cap, "lb_get_beads_async"), cap, C.byref(t)),
            "lb_get_beads_async")
     return t.value
 
@@ -311,6 +330,8 @@ def lb_batch_create(L, N, seeds, rho, eta, eta_b, kT, h, a, m, zeta, k_fene, R0,
     Ns = (C.c_int * R)(*[int(v) for v in N])
     Ss = (C.c_uint64 * R)(*[int(v) for v in seeds])
     xa = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).reshape(-1)
+    if xa is not None and xa.size != 3 * sum(int(v) for v in N):
+        raise ValueError(f"lb_batch_create: x0 must hold 3 sum(N) = {3 * sum(int(v) for v in N)} values")
     b = _vp()
     _check(_lib.lb_batch_create(C.byref(b), R, Ls, Ns, Ss, rho, eta, eta_b, kT, h, a, m, zeta, k_fene, R0, eps,
                                 sigma, _dbuf(xa), int(precision), int(md_substeps)), "lb_batch_create")
@@ -354,11 +375,13 @@ def lb_batch_sync(b):
 
 
 def lb_batch_get_populations(b, r: int, out: np.ndarray):
-    _check(_lib.lb_batch_get_populations(b, int(r), _dbuf(out), out.size), "lb_batch_get_populations")
+    _check(_lib.lb_batch_get_populations(b, int(r), _out64(out, 0, "lb_batch_get_populations"), out.size),
+           "lb_batch_get_populations")
 
 
 def lb_batch_get_beads(b, r: int, x, v, cap: int):
-    _check(_lib.lb_batch_get_beads(b, int(r), _dbuf(x), _dbuf(v), cap), "lb_batch_get_beads")
+    _check(_lib.lb_batch_get_beads(b, int(r), _out64(x, cap, "lb_batch_get_beads"),
+                                   _out64(v, cap, "lb_batch_get_beads"), cap), "lb_batch_get_beads")
 
 
 def lb_batch_get_observables(b, r: int) -> np.ndarray:
@@ -565,7 +588,7 @@ def lb_bd_sync(b):
 
 
 def lb_bd_get_beads(b, out: np.ndarray):
-    _check(_lib.lb_bd_get_beads(b, _dbuf(out), out.size), "lb_bd_get_beads")
+    _check(_lib.lb_bd_get_beads(b, _out64(out, 0, "lb_bd_get_beads"), out.size), "lb_bd_get_beads")
 
 
 def lb_bd_get_step(b) -> int:

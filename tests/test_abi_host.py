@@ -158,3 +158,37 @@ def test_batch_options_before_first_use(lblib):
     finally:
         lblib.lb_batch_destroy(b)
     assert lblib._lib.lb_batch_set_options(None, 1, 1, 1) == lblib.LB_ERR_ARG
+
+
+def test_binding_refuses_buffers_the_library_would_overrun(lblib):
+    """The C calls write as many doubles as the capacity they are given; the binding checks
+    every caller-owned array against that before the call (dtype, layout, size)."""
+    ctx = lblib.lb_create(8, 1.0, 3.0, 3.0, 1.0, 0.01, 1.0, 3, lblib.LB_FP32)
+    try:
+        with pytest.raises(ValueError):
+            lblib.lb_add_chain(ctx, 4, 1.0, 20.8, 30.0, 1.5, 1.0, 1.0, x0=np.zeros((3, 3)))
+        with pytest.raises(ValueError):
+            lblib.lb_set_options(ctx, ext_bead_force=[1.0, 2.0])
+        lblib.lb_add_chain(ctx, 4, 1.0, 20.8, 30.0, 1.5, 1.0, 1.0)
+        good = np.empty((4, 3))
+        for bad in (np.empty((4, 3), dtype=np.float32), np.empty((3, 4)).T, np.empty((3, 3))):
+            with pytest.raises(ValueError):
+                lblib.lb_get_beads(ctx, bad, good, 12)
+            with pytest.raises(ValueError):
+                lblib.lb_get_beads(ctx, good, bad, 12)
+        ro = np.empty((4, 3))
+        ro.flags.writeable = False
+        with pytest.raises(ValueError):
+            lblib.lb_get_beads(ctx, ro, None, 12)
+        with pytest.raises(ValueError):
+            lblib.lb_get_populations(ctx, np.empty((19, 8, 8, 8), dtype=np.float32))
+        lblib.lb_get_beads(ctx, good, None, 12)  # the well-formed call still goes through
+    finally:
+        lblib.lb_destroy(ctx)
+    with pytest.raises(ValueError):
+        lblib.lb_batch_create([8], [4], [1], 1.0, 3.0, 3.0, 1.0, 0.01, 1.0, 1.0, 20.8, 30.0, 1.5, 1.0, 1.0,
+                              np.zeros(9), lblib.LB_FP32)
+    with pytest.raises(ValueError):
+        lblib.lb_batch_get_populations(None, 0, np.empty(10, dtype=np.float32))
+    with pytest.raises(ValueError):
+        lblib.lb_bd_get_beads(None, np.empty(10, dtype=np.float32))
