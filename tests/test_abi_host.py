@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol(lblib):
 
 def test_create_validates_arguments(lblib):
     bad = [dict(L=3), dict(rho=0.0), dict(eta=-1.0), dict(eta_b=0.0), dict(kT=-1.0), dict(h=0.0),
-           dict(a=0.0), dict(precision=7)]
+           dict(a=0.0), dict(precision=7), dict(precision=100)]
     base = dict(L=8, rho=1.0, eta=3.0, eta_b=3.0, kT=1.0, h=0.01, a=1.0, seed=1, precision=lblib.LB_FP32)
     for b in bad:
         kw = dict(base, **b)
