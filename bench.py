@@ -445,6 +445,8 @@ def run_ours(args):
               "work": "per chain and step: RPY mobility (96 x 96), 40 power-iteration and 20 Chebyshev "
                       "mat-vecs, FENE + WCA, Ito-Euler update; FP32, HI on"}
 
+    cost = cost_scaling(stream) if args.cost_scaling else None
+
     value, tmax = aggregate_throughput(L ** 3 * args.steps / 1e6, t32, ws, dev)
     v64, _ = aggregate_throughput(L ** 3 * k64 / 1e6, t64, ws, dev)
 
@@ -507,6 +509,7 @@ def run_ours(args):
         "batch_c4": batch,
         "observables_f3": observ,
         "bd_f4": bd,
+        "cost_scaling": cost,
         "adjoint_c5": adj,
         "variants": variants,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -524,6 +527,64 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# the paper's production model in MD/LB units (Sec. II E): dt_MD = 0.01, dtau_LB = 0.02
+PAPER = dict(rho=0.864, eta=0.864 * 2.8, eta_b=0.864 * 2.8, kT=1.2, h=0.02, a=1.0, m=1.0, zeta=20.8, k_fene=7.0,
+             R0=2.0, eps=1.0, sigma=1.0)
+
+
+def cost_scaling(stream):
+    """Cost of each method per chain and time unit as the chain grows (Sec. IV): the LB side
+    runs, like the paper, three boxes per N with sqrt<R_e^2>/L = 0.5, 0.4, 0.3 (R_e from the
+    Table 1 BD value at N = 32 scaled by N^0.588), each as a batch of 64 replicas with two MD
+    steps per LB step; the BD side runs 64 chains of the same N with RPY and the Chebyshev
+    square root at its production time step.  Device time with CUDA events."""
+    import math
+
+    import numpy as np
+    import torch
+    from paper_0903_5067_gb300 import inputs, lb
+
+    out = []
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for N in (16, 32, 64):
+        re = math.sqrt(99.22) * (N / 32.0) ** 0.588
+        Ls = [max(8, int(round(re / f))) for f in (0.5, 0.4, 0.3)]
+        lb_cost = 0.0
+        for Lb in Ls:
+            seeds = [7000 + 97 * Lb + r for r in range(64)]
+            X = [inputs.chain_walk(N, L=Lb, bond=0.97, seed=sd, self_avoiding=True) for sd in seeds]
+            b = lb.Batch([Lb] * 64, [N] * 64, seeds, X, precision=lb.LB_FP32, md_substeps=2, **PAPER)
+            b.step(5)
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            b.step(100)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lb_cost += e0.elapsed_time(e1) / 1e3 / (64 * 100 * PAPER["h"])
+            b.close()
+        Xb = np.stack([inputs.chain_walk(N, L=1000, bond=0.97, seed=300 + r, self_avoiding=True) for r in range(64)])
+        zeta = lb.zeta_eff(20.8, PAPER["eta"])
+        dt = 0.005 * zeta / (4.0 * PAPER["k_fene"])
+        sb = lb.BD(Xb, kT=PAPER["kT"], zeta=zeta, eta_s=PAPER["eta"], dt=dt, k_fene=PAPER["k_fene"],
+                   R0=PAPER["R0"], precision=lb.LB_FP32, seed=5)
+        sb.step(20)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        sb.step(400)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bd_cost = e0.elapsed_time(e1) / 1e3 / (64 * 400 * dt)
+        sb.close()
+        out.append({"N": N, "L": Ls, "lb_s_per_chain_time_unit": lb_cost, "bd_s_per_chain_time_unit": bd_cost,
+                    "lb_over_bd": lb_cost / bd_cost})
+    lg = np.log([r["N"] for r in out])
+    return {"points": out,
+            "lb_exponent": float(np.polyfit(lg, np.log([r["lb_s_per_chain_time_unit"] for r in out]), 1)[0]),
+            "bd_exponent": float(np.polyfit(lg, np.log([r["bd_s_per_chain_time_unit"] for r in out]), 1)[0]),
+            "work": "FP32; LB: 64 replicas per box, 100 LB steps (200 MD steps) timed after 5; BD: 64 chains, "
+                    "400 steps timed after 20, dt = 0.005 zeta_eff / (4 k)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -536,6 +597,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-bd", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--cost-scaling", action="store_true",
+                    help="also time LB against BD per chain and time unit for N = 16, 32, 64 (Sec. IV)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
