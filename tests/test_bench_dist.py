@@ -53,3 +53,43 @@ def test_single_rank_is_identity():
     assert bench.max_over_ranks(1.5, 1) == 1.5
     v, t = bench.aggregate_throughput(10.0, 2.0, 1)
     assert (v, t) == (5.0, 2.0)
+
+
+def test_oracle_sample_times_only_the_steps_after_warmup():
+    import bench
+
+    t = bench.cpu_oracle_sample(6, 4, 2, 3, timeout=300, warmup=1)
+    assert 0.0 < t < 30.0
+
+
+def test_reference_line_keeps_the_contract(monkeypatch, capsys):
+    """The reference arm (the FP64 oracle on the host) prints one JSON line with the main
+    arm's metric, unit and config, impl = reference, its CPU baseline and an end-to-end object
+    with no host-device traffic; a box too slow for the time budget is replaced by the largest
+    sub-box that fits, and the line says so."""
+    import argparse
+    import json
+
+    import bench
+
+    calls = []
+
+    def fake(L, N, steps, seed, timeout=900.0, warmup=0):
+        calls.append((L, N, steps, warmup))
+        return 1e-6 * L ** 3  # seconds per step: 2.1 s at L = 128, 0.26 s at L = 64
+    monkeypatch.setattr(bench, "cpu_oracle_sample", fake)
+    bench.run_reference(argparse.Namespace(steps=20, warmup=5))
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "MLUPS"
+    assert line["steps"] == 20 and line["warmup"] == 5 and line["higher_is_better"] is True
+    assert line["config"]["workload"] == bench.workload_name()
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    # budget 150 s / 25 steps = 6 s per step: L = 128 (2.1 s) fits
+    assert calls[-1] == (bench.L_BENCH, bench.N_BENCH, 20, 5)
+    assert line["value"] == pytest.approx(1.0)  # L^3 / (1e-6 L^3) / 1e6
+    calls.clear()
+    bench.run_reference(argparse.Namespace(steps=200, warmup=50))  # 0.6 s per step: L = 64
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert calls[-1] == (64, bench.N_BENCH, 200, 50)
+    assert "L=64 sub-box" in line["cpu_baseline"]["sample"]
