@@ -79,10 +79,12 @@ class ClockSampler:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, directory: str | None = None):
+        import tempfile
+
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(directory or tempfile.gettempdir(), f"clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
@@ -255,7 +257,7 @@ def run_ours(args):
     sim.step(args.warmup)
     sim.sync()
 
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_dir)
     with clocks:
         # timed region: K fused steps, inputs resident in HBM
         barrier()
@@ -593,6 +595,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="where the nvidia-smi clock samples of the timed region are written (default: temp dir)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-observables", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
