@@ -167,8 +167,8 @@ int lb_trajectory_frames(lb_ctx* ctx, int64_t* frames);
  * initial bead positions x_b(0) (grad_x0, 3N, bead-major) and to zeta_bare (grad_zeta).
  * The forward run keeps full-state checkpoints every K steps and recomputes each segment
  * during the reverse sweep (memory ~ (T/K + K) states).  Must be called on a context that
- * has not stepped yet (the initial force is F_cons(x_0)); requires a chain and no fluid body
- * force; leaves the context at step T.  Allocates its checkpoint and adjoint memory with
+ * has not stepped yet (the initial force is F_cons(x_0)); requires a chain, one MD step per
+ * LB step and no fluid body force (LB_ERR_STATE otherwise); leaves the context at step T.  Allocates its checkpoint and adjoint memory with
  * cudaMalloc for the duration of the call. */
 int lb_adjoint_displacement(lb_ctx* ctx, int64_t T, int K, double* objective, double* grad_x0,
                             size_t cap, double* grad_zeta);
