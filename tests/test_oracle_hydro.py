@@ -279,3 +279,43 @@ def test_collision_projects_out_the_kinetic_modes():
     assert np.allclose(m_out[4], meq[4] + gb * (m_in[4] - meq[4]), rtol=0, atol=1e-15)
     for k in range(5, 10):
         assert np.allclose(m_out[k], meq[k] + gs * (m_in[k] - meq[k]), rtol=0, atol=1e-15)
+
+
+def test_plane_wave_force_response_follows_the_linearised_operator():
+    """From the fluid at rest, a force density f = F0 Re(v e^{i k.r}) (arbitrary direction,
+    k not along an axis) adds the lattice momentum f h^2 / a to modes 1..3 of every node after
+    each relaxation.  To linear order in F0 the populations after T steps are therefore
+    sum_{t<T} (C S)^t M^-1 e_J (f h^2/a): the odd part in F0 of the oracle's run matches it
+    (the forcing's stress terms, U'.dJ, are even in F0 and drop out)."""
+    L, T = 8, 15
+    fp = o.FluidParams(L=L, rho=1.0, eta=3.0, eta_b=1.5, kT=0.0, h=0.01, noise_fluid=False)
+    kvec = 2 * np.pi / L * np.array([1.0, -1.0, 2.0])
+    rng = np.random.default_rng(13)
+    vf = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    phase = np.exp(1j * (kvec[0] * x + kvec[1] * y + kvec[2] * z))
+    F0 = 1e-3
+    base = o.fluid_at_rest(fp)
+    runs = []
+    for sgn in (1.0, -1.0):
+        force = sgn * F0 * np.real(vf[:, None, None, None] * phase[None])
+        n = base.copy()
+        for k in range(T):
+            n = o.collide(o.stream(n), fp, step=k, force_density=force)
+        runs.append(n - base)
+    odd = 0.5 * (runs[0] - runs[1])
+    A = _linear_operator(fp, kvec)
+    dm = np.zeros(o.Q, dtype=complex)
+    dm[1:4] = F0 * vf * fp.h * fp.h / fp.a
+    g = o.MINV @ dm
+    acc = np.zeros(o.Q, dtype=complex)
+    P = np.eye(o.Q, dtype=complex)
+    for _ in range(T):
+        acc += P @ g
+        P = A @ P
+    want = np.real(acc[:, None, None, None] * phase[None])
+    assert np.abs(want).max() > 0.0
+    assert np.abs(odd - want).max() < 1e-8 * np.abs(want).max()
+    # the momentum entering before streaming instead of after the collision would not match
+    wrong = np.real((A @ acc)[:, None, None, None] * phase[None])
+    assert np.abs(odd - wrong).max() > 1e-3 * np.abs(want).max()
