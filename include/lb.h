@@ -186,6 +186,12 @@ int lb_get_timing(lb_ctx* ctx, double* total_ms, int64_t* launches);
 
 void lb_destroy(lb_ctx* ctx);
 const char* lb_strerror(int status);
+/* The message of the calling thread's last failing single-context call (lb_create ..
+ * lb_adjoint_displacement, the status a synchronising call reports included), copied
+ * NUL-terminated into buf (truncated to cap - 1 bytes; buf may be NULL) and then cleared;
+ * returns its full length, 0 when there is none.  Batch and Brownian-dynamics calls return
+ * their status without a message. */
+size_t lb_last_error(char* buf, size_t cap);
 
 /* --- test hooks on raw device buffers (enqueued on `stream`, no context) --------------- */
 

@@ -70,7 +70,11 @@ namespace {
 int fail(int code, const char* msg);
 void record_frame(lb_ctx* ctx);
 
+// the message of this thread's last failing call, until lb_last_error takes it
+thread_local std::string t_last_error;
+
 int fail(int code, const char* msg) {
+  t_last_error = msg ? msg : "";
   if (getenv("GBLB_VERBOSE")) fprintf(stderr, "libgblb: %s\n", msg);
   return code;
 }
@@ -173,9 +177,9 @@ void materialise(lb_ctx* ctx) {
 }
 
 int status_from_device(unsigned st) {
-  if (st & ST_FENE) return LB_ERR_FENE;
-  if (st & ST_NONFINITE) return LB_ERR_NONFINITE;
-  if (st & ST_TIMEOUT) return LB_ERR_TIMEOUT;
+  if (st & ST_FENE) return fail(LB_ERR_FENE, "a FENE bond reached R0");
+  if (st & ST_NONFINITE) return fail(LB_ERR_NONFINITE, "a non-finite value appeared in the state");
+  if (st & ST_TIMEOUT) return fail(LB_ERR_TIMEOUT, "a device wait ran out of iterations");
   return LB_OK;
 }
 
@@ -201,7 +205,7 @@ extern "C" {
 
 int lb_create(lb_ctx** out, int L, double rho, double eta, double eta_b, double kT, double h, double a,
               uint64_t seed, int precision) {
-  if (!out) return LB_ERR_ARG;
+  if (!out) return fail(LB_ERR_ARG, "invalid argument: !out");
   *out = nullptr;
   if (L < 4 || L > 1290) return fail(LB_ERR_ARG, "L out of range [4, 1290]");
   if (!(rho > 0) || !(eta > 0) || !(eta_b > 0) || !(h > 0) || !(a > 0) || !(kT >= 0))
@@ -225,7 +229,7 @@ int lb_create(lb_ctx** out, int L, double rho, double eta, double eta_b, double 
 
 int lb_add_chain(lb_ctx* ctx, int N, double m, double zeta, double k_fene, double R0, double eps, double sigma,
                  const double* x0, const double* v0, double bond, int saw) {
-  if (!ctx) return LB_ERR_ARG;
+  if (!ctx) return fail(LB_ERR_ARG, "invalid argument: !ctx");
   if (ctx->live || ctx->cfg.N > 0) return fail(LB_ERR_STATE, "chain must be added once, before the first step");
   if (N < 1 || N > 1024) return fail(LB_ERR_ARG, "N out of range [1, 1024]");
   if (8ll * N * ctx->cfg.substeps > 16384) return fail(LB_ERR_ARG, "8 N substeps exceeds 16384");
@@ -281,7 +285,7 @@ int lb_add_chain(lb_ctx* ctx, int N, double m, double zeta, double k_fene, doubl
 
 int lb_set_options(lb_ctx* ctx, int noise_fluid, int noise_beads, int stress_only, const double ext_bead_force[3],
                    int counter_force_fluid) {
-  if (!ctx) return LB_ERR_ARG;
+  if (!ctx) return fail(LB_ERR_ARG, "invalid argument: !ctx");
   Config& c = ctx->cfg;
   c.noise_fluid = noise_fluid ? 1 : 0;
   c.noise_beads = noise_beads ? 1 : 0;
@@ -293,7 +297,7 @@ int lb_set_options(lb_ctx* ctx, int noise_fluid, int noise_beads, int stress_onl
 }
 
 int lb_set_md_substeps(lb_ctx* ctx, int n) {
-  if (!ctx || n < 1 || n > 16) return LB_ERR_ARG;
+  if (!ctx || n < 1 || n > 16) return fail(LB_ERR_ARG, "invalid argument: !ctx || n < 1 || n > 16");
   if (ctx->live) return fail(LB_ERR_STATE, "substeps must be set before the first device call");
   if (8ll * ctx->cfg.N * n > 16384) return fail(LB_ERR_ARG, "8 N substeps exceeds 16384");
   ctx->cfg.substeps = n;
@@ -302,13 +306,13 @@ int lb_set_md_substeps(lb_ctx* ctx, int n) {
 }
 
 int lb_set_stream(lb_ctx* ctx, void* stream) {
-  if (!ctx) return LB_ERR_ARG;
+  if (!ctx) return fail(LB_ERR_ARG, "invalid argument: !ctx");
   ctx->stream = static_cast<cudaStream_t>(stream);
   return LB_OK;
 }
 
 int lb_workspace_size(lb_ctx* ctx, size_t* bytes) {
-  if (!ctx || !bytes) return LB_ERR_ARG;
+  if (!ctx || !bytes) return fail(LB_ERR_ARG, "invalid argument: !ctx || !bytes");
   return guarded([&] {
     if (!ctx->eng) ctx->eng.reset(make_engine(ctx->cfg));
     *bytes = ctx->eng->workspace_bytes();
@@ -317,7 +321,7 @@ int lb_workspace_size(lb_ctx* ctx, size_t* bytes) {
 }
 
 int lb_bind_workspace(lb_ctx* ctx, void* device_ptr, size_t bytes) {
-  if (!ctx || !device_ptr) return LB_ERR_ARG;
+  if (!ctx || !device_ptr) return fail(LB_ERR_ARG, "invalid argument: !ctx || !device_ptr");
   if (ctx->live) return fail(LB_ERR_STATE, "workspace must be bound before the first device call");
   if (reinterpret_cast<uintptr_t>(device_ptr) % 256 != 0) return fail(LB_ERR_ARG, "workspace not 256-byte aligned");
   return guarded([&] {
@@ -332,7 +336,7 @@ int lb_bind_workspace(lb_ctx* ctx, void* device_ptr, size_t bytes) {
 }
 
 int lb_step(lb_ctx* ctx, int64_t n) {
-  if (!ctx || n < 0) return LB_ERR_ARG;
+  if (!ctx || n < 0) return fail(LB_ERR_ARG, "invalid argument: !ctx || n < 0");
   return guarded([&] {
     materialise(ctx);
     for (int64_t t = 0; t < n; ++t) {
@@ -355,7 +359,7 @@ int lb_step(lb_ctx* ctx, int64_t n) {
 }
 
 int lb_sync(lb_ctx* ctx) {
-  if (!ctx) return LB_ERR_ARG;
+  if (!ctx) return fail(LB_ERR_ARG, "invalid argument: !ctx");
   return guarded([&] {
     if (!ctx->live) return (int)LB_OK;
     cuda_check(cudaStreamSynchronize(ctx->stream), "stream sync");
@@ -364,7 +368,7 @@ int lb_sync(lb_ctx* ctx) {
 }
 
 int lb_get_populations(lb_ctx* ctx, double* out, size_t cap) {
-  if (!ctx || !out) return LB_ERR_ARG;
+  if (!ctx || !out) return fail(LB_ERR_ARG, "invalid argument: !ctx || !out");
   const size_t need = 19 * (size_t)ctx->cfg.L * ctx->cfg.L * ctx->cfg.L;
   if (cap < need) return fail(LB_ERR_ARG, "population buffer too small");
   return guarded([&] {
@@ -375,7 +379,7 @@ int lb_get_populations(lb_ctx* ctx, double* out, size_t cap) {
 }
 
 int lb_set_populations(lb_ctx* ctx, const double* in, size_t count) {
-  if (!ctx || !in) return LB_ERR_ARG;
+  if (!ctx || !in) return fail(LB_ERR_ARG, "invalid argument: !ctx || !in");
   const size_t need = 19 * (size_t)ctx->cfg.L * ctx->cfg.L * ctx->cfg.L;
   if (count != need) return fail(LB_ERR_ARG, "population count must be 19 L^3");
   return guarded([&] {
@@ -386,7 +390,7 @@ int lb_set_populations(lb_ctx* ctx, const double* in, size_t count) {
 }
 
 int lb_get_beads(lb_ctx* ctx, double* x, double* v, size_t cap) {
-  if (!ctx) return LB_ERR_ARG;
+  if (!ctx) return fail(LB_ERR_ARG, "invalid argument: !ctx");
   if (cap < 3 * (size_t)ctx->cfg.N) return fail(LB_ERR_ARG, "bead buffer too small");
   if (!ctx->live) {
     // before the first device call the chain is the host-staged initial state
@@ -405,7 +409,7 @@ int lb_get_beads(lb_ctx* ctx, double* x, double* v, size_t cap) {
 }
 
 int lb_get_beads_async(lb_ctx* ctx, double* x, double* v, size_t cap, int64_t* ticket) {
-  if (!ctx || !ticket) return LB_ERR_ARG;
+  if (!ctx || !ticket) return fail(LB_ERR_ARG, "invalid argument: !ctx || !ticket");
   if (cap < 3 * (size_t)ctx->cfg.N) return fail(LB_ERR_ARG, "bead buffer too small");
   return guarded([&] {
     materialise(ctx);
@@ -422,7 +426,7 @@ int lb_get_beads_async(lb_ctx* ctx, double* x, double* v, size_t cap, int64_t* t
 }
 
 int lb_wait(lb_ctx* ctx, int64_t ticket) {
-  if (!ctx || ticket < 0 || ticket >= ctx->tickets) return LB_ERR_ARG;
+  if (!ctx || ticket < 0 || ticket >= ctx->tickets) return fail(LB_ERR_ARG, "invalid argument: !ctx || ticket < 0 || ticket >= ctx->tickets");
   return guarded([&] {
     const int slot = (int)(ticket % lb_ctx::kTickets);
     // a later read-back in the same slot completes after this one: waiting on it suffices
@@ -432,7 +436,7 @@ int lb_wait(lb_ctx* ctx, int64_t ticket) {
 }
 
 int lb_get_observables(lb_ctx* ctx, double* out, size_t cap) {
-  if (!ctx || !out) return LB_ERR_ARG;
+  if (!ctx || !out) return fail(LB_ERR_ARG, "invalid argument: !ctx || !out");
   if (cap < LB_NOBS) return fail(LB_ERR_ARG, "observable buffer too small");
   return guarded([&] {
     materialise(ctx);
@@ -442,7 +446,7 @@ int lb_get_observables(lb_ctx* ctx, double* out, size_t cap) {
 }
 
 int lb_record_trajectory(lb_ctx* ctx, double* traj_dev, int capacity, int stride) {
-  if (!ctx) return LB_ERR_ARG;
+  if (!ctx) return fail(LB_ERR_ARG, "invalid argument: !ctx");
   if (!traj_dev || capacity <= 0 || stride <= 0) {
     ctx->traj = nullptr;
     ctx->traj_cap = ctx->traj_stride = 0;
@@ -462,19 +466,19 @@ int lb_record_trajectory(lb_ctx* ctx, double* traj_dev, int capacity, int stride
 }
 
 int lb_trajectory_frames(lb_ctx* ctx, int64_t* frames) {
-  if (!ctx || !frames) return LB_ERR_ARG;
+  if (!ctx || !frames) return fail(LB_ERR_ARG, "invalid argument: !ctx || !frames");
   *frames = ctx->traj ? ctx->traj_frames : 0;
   return LB_OK;
 }
 
 int lb_set_obs_stride(lb_ctx* ctx, int stride) {
-  if (!ctx || stride < 0) return LB_ERR_ARG;
+  if (!ctx || stride < 0) return fail(LB_ERR_ARG, "invalid argument: !ctx || stride < 0");
   ctx->obs_stride = stride;
   return LB_OK;
 }
 
 int lb_reset_reference(lb_ctx* ctx) {
-  if (!ctx) return LB_ERR_ARG;
+  if (!ctx) return fail(LB_ERR_ARG, "invalid argument: !ctx");
   return guarded([&] {
     materialise(ctx);
     ctx->eng->reset_reference(ctx->stream);
@@ -483,7 +487,7 @@ int lb_reset_reference(lb_ctx* ctx) {
 }
 
 int lb_save(lb_ctx* ctx, const char* path) {
-  if (!ctx || !path) return LB_ERR_ARG;
+  if (!ctx || !path) return fail(LB_ERR_ARG, "invalid argument: !ctx || !path");
   return guarded([&] {
     materialise(ctx);
     std::vector<unsigned char> buf(ctx->eng->state_bytes());
@@ -500,7 +504,7 @@ int lb_save(lb_ctx* ctx, const char* path) {
 }
 
 int lb_load(lb_ctx* ctx, const char* path) {
-  if (!ctx || !path) return LB_ERR_ARG;
+  if (!ctx || !path) return fail(LB_ERR_ARG, "invalid argument: !ctx || !path");
   return guarded([&] {
     FILE* f = fopen(path, "rb");
     if (!f) return fail(LB_ERR_ARG, "cannot open checkpoint");
@@ -529,7 +533,7 @@ int lb_load(lb_ctx* ctx, const char* path) {
 
 int lb_adjoint_displacement(lb_ctx* ctx, int64_t T, int K, double* objective, double* grad_x0, size_t cap,
                             double* grad_zeta) {
-  if (!ctx || !objective || !grad_x0 || !grad_zeta || T < 1 || K < 1) return LB_ERR_ARG;
+  if (!ctx || !objective || !grad_x0 || !grad_zeta || T < 1 || K < 1) return fail(LB_ERR_ARG, "invalid argument: !ctx || !objective || !grad_x0 || !grad_zeta || T < 1 || K < 1");
   if (ctx->cfg.N == 0) return fail(LB_ERR_STATE, "adjoint needs a chain");
   if (cap < 3 * (size_t)ctx->cfg.N) return fail(LB_ERR_ARG, "gradient buffer too small");
   if (ctx->step != 0) return fail(LB_ERR_STATE, "adjoint must start from the initial state");
@@ -544,7 +548,7 @@ int lb_adjoint_displacement(lb_ctx* ctx, int64_t T, int K, double* objective, do
 int64_t lb_get_step(lb_ctx* ctx) { return ctx ? ctx->step : -1; }
 
 int lb_set_timing(lb_ctx* ctx, int enable) {
-  if (!ctx) return LB_ERR_ARG;
+  if (!ctx) return fail(LB_ERR_ARG, "invalid argument: !ctx");
   return guarded([&] {
     drain_timing(ctx);
     ctx->timing = enable != 0;
@@ -555,7 +559,7 @@ int lb_set_timing(lb_ctx* ctx, int enable) {
 }
 
 int lb_get_timing(lb_ctx* ctx, double* total_ms, int64_t* launches) {
-  if (!ctx) return LB_ERR_ARG;
+  if (!ctx) return fail(LB_ERR_ARG, "invalid argument: !ctx");
   return guarded([&] {
     drain_timing(ctx);
     if (total_ms) *total_ms = ctx->timed_ms;
@@ -586,6 +590,17 @@ void lb_destroy(lb_ctx* ctx) {
   delete ctx;
 }
 
+size_t lb_last_error(char* buf, size_t cap) {
+  const size_t n = t_last_error.size();
+  if (buf && cap > 0) {
+    const size_t m = n < cap - 1 ? n : cap - 1;
+    memcpy(buf, t_last_error.data(), m);
+    buf[m] = '\0';
+  }
+  t_last_error.clear();
+  return n;
+}
+
 const char* lb_strerror(int status) {
   switch (status) {
     case LB_OK: return "ok";
@@ -602,14 +617,14 @@ const char* lb_strerror(int status) {
 
 int lb_philox4x32_10(const uint32_t* ctr_dev, int64_t n, uint32_t k0, uint32_t k1, uint32_t* out_dev,
                      void* stream) {
-  if (n < 0 || (n > 0 && (!ctr_dev || !out_dev))) return LB_ERR_ARG;
+  if (n < 0 || (n > 0 && (!ctr_dev || !out_dev))) return fail(LB_ERR_ARG, "invalid argument: n < 0 || (n > 0 && (!ctr_dev || !out_dev))");
   if (n == 0) return LB_OK;
   k_philox<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(ctr_dev, n, k0, k1, out_dev);
   return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ERR_CUDA;
 }
 
 int lb_cell_index_f32(const float* x_dev, int64_t n, float a, int L, int32_t* out_dev, void* stream) {
-  if (n < 0 || L < 1 || !(a > 0) || (n > 0 && (!x_dev || !out_dev))) return LB_ERR_ARG;
+  if (n < 0 || L < 1 || !(a > 0) || (n > 0 && (!x_dev || !out_dev))) return fail(LB_ERR_ARG, "invalid argument: n < 0 || L < 1 || !(a > 0) || (n > 0 && (!x_dev || !out_dev))");
   if (n == 0) return LB_OK;
   k_cell_index_f32<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x_dev, n, a, L,
                                                                                                out_dev);

@@ -71,6 +71,7 @@ _SIGS = {
     "lb_get_timing": (C.c_int, [_vp, _dp, C.POINTER(C.c_int64)]),
     "lb_destroy": (None, [_vp]),
     "lb_strerror": (C.c_char_p, [C.c_int]),
+    "lb_last_error": (C.c_size_t, [C.c_char_p, C.c_size_t]),
     "lb_philox4x32_10": (C.c_int, [_vp, C.c_int64, C.c_uint32, C.c_uint32, _vp, _vp]),
     "lb_cell_index_f32": (C.c_int, [_vp, C.c_int64, C.c_float, C.c_int, _vp, _vp]),
     "lb_fluid_sums_noalloc": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double, _dp, _vp]),
@@ -105,8 +106,10 @@ def library_path() -> str:
 
 class LBError(RuntimeError):
     def __init__(self, code: int, where: str):
-        super().__init__(f"{where}: {lb_strerror(code)} (status {code})")
+        detail = lb_last_error()
+        super().__init__(f"{where}: {lb_strerror(code)} (status {code})" + (f": {detail}" if detail else ""))
         self.code = code
+        self.detail = detail
 
 
 def _check(code: int, where: str) -> None:
@@ -134,6 +137,13 @@ def _out64(a, need: int, where: str):
 # --- C functions, same names -----------------------------------------------------------
 def lb_strerror(code: int) -> str:
     return _lib.lb_strerror(code).decode()
+
+
+def lb_last_error() -> str:
+    """The message of this thread's last failing call (and clears it); '' when none."""
+    buf = C.create_string_buffer(512)
+    _lib.lb_last_error(buf, len(buf))
+    return buf.value.decode(errors="replace")
 
 
 def lb_create(L, rho, eta, eta_b, kT, h, a, seed, precision):

@@ -192,3 +192,31 @@ def test_binding_refuses_buffers_the_library_would_overrun(lblib):
         lblib.lb_batch_get_populations(None, 0, np.empty(10, dtype=np.float32))
     with pytest.raises(ValueError):
         lblib.lb_bd_get_beads(None, np.empty(10, dtype=np.float32))
+
+
+def test_failing_calls_leave_a_message_for_their_thread(lblib):
+    """lb_last_error hands over the reason of the calling thread's last failure once; the
+    binding's LBError carries it."""
+    import threading
+
+    assert lblib.lb_last_error() == ""
+    with pytest.raises(lblib.LBError) as ei:
+        lblib.lb_create(3, 1.0, 3.0, 3.0, 1.0, 0.01, 1.0, 1, lblib.LB_FP32)
+    assert "L out of range" in ei.value.detail and "L out of range" in str(ei.value)
+    assert lblib.lb_last_error() == ""  # taken by the exception
+    import ctypes
+
+    out = ctypes.c_void_p()
+    assert lblib._lib.lb_create(ctypes.byref(out), 8, -1.0, 3.0, 3.0, 1.0, 0.01, 1.0, 1, lblib.LB_FP32) != lblib.LB_OK
+    seen = []
+    t = threading.Thread(target=lambda: seen.append(lblib.lb_last_error()))
+    t.start()
+    t.join()
+    assert seen == [""]  # another thread's failure is not visible here
+    msg = lblib.lb_last_error()
+    assert "must be > 0" in msg
+    n = lblib._lib.lb_last_error(None, 0)
+    assert n == 0
+    with pytest.raises(lblib.LBError) as ei:  # a null handle
+        lblib.lb_step(None, 1)
+    assert "invalid argument" in ei.value.detail
