@@ -184,7 +184,10 @@ int64_t lb_get_step(lb_ctx* ctx);
 int lb_set_timing(lb_ctx* ctx, int enable);
 int lb_get_timing(lb_ctx* ctx, double* total_ms, int64_t* launches);
 
+/* Wait for the context's outstanding work and read-backs, then free its device memory
+ * (a caller-bound workspace stays the caller's) and the handle.  NULL is ignored. */
 void lb_destroy(lb_ctx* ctx);
+/* A static, NUL-terminated name for a status code ("unknown status" for others). */
 const char* lb_strerror(int status);
 /* The message of the calling thread's last failing single-context call (lb_create ..
  * lb_adjoint_displacement, the status a synchronising call reports included), copied
