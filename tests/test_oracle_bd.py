@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import bd
+from oracle import lbchain as o
 from paper_0903_5067_gb300 import inputs
 
 
@@ -91,3 +92,118 @@ def test_single_bead_limits():
     n = 20000
     disp = np.array([bd.step(X, q, r, 0)[0] for r in range(n)])
     assert np.mean(np.sum(disp ** 2, axis=1)) == pytest.approx(6 * q.kT / q.zeta * q.dt, rel=0.03)
+
+
+# ---------------------------------------------------------------------------------------
+# The BD chain's conservative forces (Sec. II A, Eqs. 1-2, in an infinite medium)
+# ---------------------------------------------------------------------------------------
+def _folded_chain():
+    """Six beads, bonds between 0.9 and 1.9 (the production model's R0 = 2), and two
+    non-bonded pairs, (0, 5) and (2, 4), inside the WCA range 2^(1/6) sigma."""
+    return np.array([[0.0, 0.0, 0.0], [0.95, 0.1, 0.0], [1.6, 0.9, 0.3], [1.3, 1.8, 0.9],
+                     [0.55, 1.0, 0.55], [-0.4, 0.6, 0.5]])
+
+
+def _wca_energy(r, eps, sigma):
+    """Eq. 2 restated: 4 eps ((sigma/r)^12 - (sigma/r)^6 + 1/4) below 2^(1/6) sigma, else 0."""
+    return 4.0 * eps * ((sigma / r) ** 12 - (sigma / r) ** 6 + 0.25) if r < 2.0 ** (1.0 / 6.0) * sigma else 0.0
+
+
+def _chain_energy(X, p):
+    """FENE (Eq. 1) on the bonds plus WCA on all pairs, infinite medium: a second, independent
+    statement of the potential whose negative gradient the BD forces are."""
+    N = X.shape[0]
+    e = 0.0
+    for i in range(N - 1):
+        r2 = float(((X[i] - X[i + 1]) ** 2).sum())
+        e += -0.5 * p.k_fene * p.R0 ** 2 * math.log(1.0 - r2 / p.R0 ** 2)
+    for i in range(N):
+        for j in range(i + 1, N):
+            e += _wca_energy(math.sqrt(float(((X[i] - X[j]) ** 2).sum())), p.eps, p.sigma)
+    return e
+
+
+def _force_pin_failures(forces):
+    """Names of the properties a BD force routine misses (empty when all hold):
+    - F = -grad V by central differences of the restated energy above (folded chain);
+    - two beads: |F| = k r / (1 - r^2/R0^2) attractive for a bond beyond the WCA range, and
+      the FENE pull minus the WCA push 24 eps (2 (sigma/r)^12 - (sigma/r)^6) / r inside it;
+    - Newton's third law (zero net force) and zero net torque (central pair forces);
+    - equal to the LB oracle's chain forces in a box far larger than the chain."""
+    fails = []
+    p = bd.BDParams(N=6)
+    X = _folded_chain()
+    F = forces(X, p)
+    h = 1e-6
+    for b in range(6):
+        for al in range(3):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[b, al] += h
+            Xm[b, al] -= h
+            fd = -(_chain_energy(Xp, p) - _chain_energy(Xm, p)) / (2 * h)
+            if abs(F[b, al] - fd) > 1e-6 * max(1.0, abs(fd)):
+                fails.append(f"-grad V bead {b} axis {al}")
+    if np.abs(F.sum(axis=0)).max() > 1e-10:
+        fails.append("net force")
+    if np.abs(np.cross(X, F).sum(axis=0)).max() > 1e-10:
+        fails.append("net torque")
+    q = bd.BDParams(N=2)
+    for r in (0.95, 1.5):
+        X2 = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+        F2 = forces(X2, q)
+        fene = q.k_fene * r / (1.0 - r * r / q.R0 ** 2)
+        wca = 24.0 * q.eps * (2.0 * (q.sigma / r) ** 12 - (q.sigma / r) ** 6) / r if r < 2 ** (1 / 6) else 0.0
+        want = -fene + wca  # x component on bead 1 (positive: pushed away from bead 0)
+        if abs(F2[1, 0] - want) > 1e-12 * abs(want) or abs(F2[0, 0] + want) > 1e-12 * abs(want):
+            fails.append(f"two beads r={r}")
+    cp = o.ChainParams(N=6, k_fene=p.k_fene, R0=p.R0, eps=p.eps, sigma=p.sigma)
+    if not np.allclose(forces(X + 50.0, p), o.chain_forces(X + 50.0, cp, 1.0e6), rtol=1e-13, atol=1e-13):
+        fails.append("LB oracle chain forces")
+    return fails
+
+
+def test_bd_forces_are_minus_the_gradient_of_fene_plus_wca():
+    assert _force_pin_failures(bd.forces) == []
+
+
+def _forces_wca_sign(X, p):  # planted: the WCA pair force with the wrong sign
+    F = bd.forces(X, bd.BDParams(N=p.N, k_fene=0.0, R0=p.R0, eps=p.eps, sigma=p.sigma))
+    G = bd.forces(X, bd.BDParams(N=p.N, k_fene=p.k_fene, R0=p.R0, eps=0.0, sigma=p.sigma))
+    return G - F
+
+
+def _forces_fene_linear(X, p):  # planted: a harmonic bond k r in place of FENE
+    F = bd.forces(X, bd.BDParams(N=p.N, k_fene=0.0, R0=p.R0, eps=p.eps, sigma=p.sigma))
+    for i in range(X.shape[0] - 1):
+        d = X[i] - X[i + 1]
+        F[i] -= p.k_fene * d
+        F[i + 1] += p.k_fene * d
+    return F
+
+
+def _forces_bonded_wca_only(X, p):  # planted: WCA between chain neighbours only
+    F = bd.forces(X, bd.BDParams(N=p.N, k_fene=p.k_fene, R0=p.R0, eps=0.0, sigma=p.sigma))
+    rc2 = 2.0 ** (1.0 / 3.0) * p.sigma ** 2
+    for i in range(X.shape[0] - 1):
+        d = X[i] - X[i + 1]
+        r2 = d @ d
+        if r2 < rc2:
+            sr6 = (p.sigma ** 2 / r2) ** 3
+            f = 24.0 * p.eps / r2 * (2.0 * sr6 * sr6 - sr6) * d
+            F[i] += f
+            F[i + 1] -= f
+    return F
+
+
+def _forces_one_sided(X, p):  # planted: the reaction on the second bead of each pair dropped
+    F = np.zeros_like(X)
+    full = bd.forces(X, p)
+    F[: X.shape[0] // 2] = full[: X.shape[0] // 2]
+    F[X.shape[0] // 2:] = 0.5 * full[X.shape[0] // 2:]
+    return F
+
+
+@pytest.mark.parametrize("fn", [_forces_wca_sign, _forces_fene_linear, _forces_bonded_wca_only, _forces_one_sided],
+                         ids=["wca_sign", "fene_linear", "wca_bonded_only", "reaction_halved"])
+def test_planted_bd_force_mistakes_are_caught(fn):
+    assert _force_pin_failures(fn)

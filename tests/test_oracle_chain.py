@@ -226,3 +226,86 @@ def test_single_substep_is_the_plain_step():
     a = o.run(st, fp, cp, 5)
     b = o.run(st, fp, cp1, 5)
     assert np.array_equal(a.n, b.n) and np.array_equal(a.X, b.X)
+
+
+# ---------------------------------------------------------------------------------------
+# Chain size observables (Sec. III A: R_g^2 = (1/2N^2) sum_ij r_ij^2, R_e^2 = (r_N - r_1)^2)
+# ---------------------------------------------------------------------------------------
+def _rotation(seed):
+    q, r = np.linalg.qr(np.random.default_rng(seed).standard_normal((3, 3)))
+    q = q * np.sign(np.diag(r))[None]
+    return q if np.linalg.det(q) > 0 else -q
+
+
+def _size_pin_failures(rg2, re2):
+    """Names of the closed forms that rg2 / re2 miss (empty when all hold):
+    - a straight rod of N beads at spacing b: R_g^2 = b^2 (N^2 - 1) / 12, R_e^2 = (N - 1)^2 b^2;
+    - N beads equally spaced on a circle of radius R: R_g^2 = R^2, R_e^2 = (2 R sin(pi/N))^2;
+    - a single bead: both zero;
+    - any chain: R_g^2 equals the mean squared distance from the centre of mass (the identity
+      (1/2N^2) sum_ij |r_i - r_j|^2 = (1/N) sum_i |r_i - r_cm|^2), and neither changes under a
+      rotation plus a translation."""
+    fails = []
+    close = lambda a, b: abs(a - b) <= 1e-12 * max(abs(b), 1e-300)
+    for N, b in ((2, 0.97), (3, 1.3), (8, 0.97), (33, 0.5)):
+        d = np.array([0.36, -0.48, 0.8])
+        X = np.array([2.0, -1.0, 0.5])[None] + b * np.arange(N)[:, None] * d[None]
+        if not close(rg2(X), b * b * (N * N - 1) / 12.0):
+            fails.append(f"rod R_g^2 N={N}")
+        if not close(re2(X), ((N - 1) * b) ** 2):
+            fails.append(f"rod R_e^2 N={N}")
+    for N, R in ((5, 1.7), (12, 0.8)):
+        ph = 2.0 * np.pi * np.arange(N) / N
+        X = R * np.stack([np.cos(ph), np.sin(ph), np.zeros(N)], axis=1) @ _rotation(N).T + 3.0
+        if not close(rg2(X), R * R):
+            fails.append(f"ring R_g^2 N={N}")
+        if not close(re2(X), (2.0 * R * np.sin(np.pi / N)) ** 2):
+            fails.append(f"ring R_e^2 N={N}")
+    one = np.array([[0.3, 0.2, -0.7]])
+    if rg2(one) != 0.0 or re2(one) != 0.0:
+        fails.append("single bead")
+    X = inputs.chain_walk(24, L=12, bond=0.97, seed=11, self_avoiding=True)
+    cm = X.mean(axis=0)
+    if not close(rg2(X), float(((X - cm) ** 2).sum(axis=1).mean())):
+        fails.append("centre-of-mass form")
+    Y = X @ _rotation(5).T + np.array([40.0, -7.0, 3.0])
+    if not (close(rg2(Y), rg2(X)) and close(re2(Y), re2(X))):
+        fails.append("rigid motion")
+    return fails
+
+
+def test_chain_size_observables_match_closed_forms():
+    assert _size_pin_failures(o.radius_of_gyration2, o.end_to_end2) == []
+
+
+def _rg2_over_n2(X):  # planted: 1/N^2 instead of 1/(2N^2)
+    d = X[:, None, :] - X[None, :, :]
+    return float((d * d).sum() / (X.shape[0] ** 2))
+
+
+def _rg2_over_pairs(X):  # planted: normalised by the number of distinct ordered pairs
+    N = X.shape[0]
+    d = X[:, None, :] - X[None, :, :]
+    return float((d * d).sum() / (2.0 * N * max(N - 1, 1)))
+
+
+def _rg2_about_first_bead(X):  # planted: distances from bead 1 instead of the centre of mass
+    return float(((X - X[0]) ** 2).sum(axis=1).mean())
+
+
+def _re2_second_bead(X):  # planted: r_N - r_2
+    d = X[-1] - X[min(1, X.shape[0] - 1)]
+    return float(d @ d)
+
+
+def _re2_not_squared(X):  # planted: |r_N - r_1| instead of its square
+    return float(np.linalg.norm(X[-1] - X[0]))
+
+
+@pytest.mark.parametrize("rg2,re2", [
+    (_rg2_over_n2, o.end_to_end2), (_rg2_over_pairs, o.end_to_end2), (_rg2_about_first_bead, o.end_to_end2),
+    (o.radius_of_gyration2, _re2_second_bead), (o.radius_of_gyration2, _re2_not_squared),
+], ids=["rg2_1/N^2", "rg2_pairs", "rg2_about_bead1", "re2_second_bead", "re2_not_squared"])
+def test_planted_size_observable_mistakes_are_caught(rg2, re2):
+    """Each planted normalisation, centre or index mistake fails at least one closed form."""
+    assert _size_pin_failures(rg2, re2)
