@@ -303,23 +303,31 @@ void lb_bd_destroy(lb_bd* b);
 
 /* --- allocation-free variant ---------------------------------------------------------
  * Fluid mass and momentum of a population field, like lb_get_observables' entries [1] and
- * [5..7], for callers that cannot allocate device memory where they need these sums: code
- * running while a stream is captured into a CUDA graph (cudaMalloc is not permitted there),
- * processes whose device memory is owned by another allocator, or latency-critical loops.
- * The paper has no counterpart; this is a service of the library.
+ * [5..7], for callers that cannot allocate device memory where they need these sums: a host
+ * application whose device memory is all reserved by another allocator (a framework's
+ * caching allocator or a pool sized to the whole GPU), where an allocation of the library's
+ * own would fail or fragment that pool; and time-critical loops, where cudaFree's implicit
+ * device-wide synchronisation and an allocation's latency are not acceptable.  The paper has
+ * no counterpart; this is a service of the library.
  *
  * pop_dev: 19 L^3 full populations (FP64, mass densities) on the current device, in the
  * layout lb_get_populations returns ([i][z][y][x], ABI velocity order).  out_host receives
- * 4 doubles: a^3 sum n, then (a^4/h) sum_i n_i c_i (x, y, z).  Enqueued on `stream` and
- * synchronised before returning.
+ * 4 doubles: a^3 sum n, then (a^4/h) sum_i n_i c_i (x, y, z).  stream: a stream of the
+ * current device (NULL: the default stream); the two kernels and the copy of the result
+ * to out_host are enqueued on it, and the call synchronises that stream before it returns.
  *
  * Scratch: a file-scope device array of LB_NOALLOC_MAX_L^3 / 256 partial sums (2 MiB), held by
  * every GPU that loads the library until the process exits; L > LB_NOALLOC_MAX_L returns
  * LB_ERR_ARG.  The function calls no cudaMalloc, cudaFree or allocating library routine.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture begins.  All
- * calls share the array (it keeps the last call's partial sums, each call overwrites every
- * slot it reads), so calls that overlap on the GPU, from several streams or threads, race. */
+ * with that device current and keeps it for later calls; make that first call before any
+ * stream capture begins.  The kept address does not survive cudaDeviceReset of that device
+ * (do not call this function again in a process that reset the device).  All calls share the
+ * array (it keeps the last call's partial sums; each call overwrites every slot it reads),
+ * so calls that overlap on the GPU, from several streams or threads, race.
+ * Errors: LB_ERR_ARG for null pointers, a, h <= 0, L outside [1, LB_NOALLOC_MAX_L] or a
+ * stream of another device; LB_ERR_CUDA when a launch, the copy or the synchronisation
+ * fails.  Every failure leaves its reason for lb_last_error. */
 #define LB_NOALLOC_MAX_L 256
 int lb_fluid_sums_noalloc(const double* pop_dev, int L, double a, double h, double* out_host,
                           void* stream);

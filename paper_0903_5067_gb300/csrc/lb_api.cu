@@ -79,6 +79,15 @@ int fail(int code, const char* msg) {
   return code;
 }
 
+}  // namespace
+
+namespace gblb {
+// failure with a message for this thread's lb_last_error, for entry points outside this file
+int api_fail(int code, const char* msg) { return fail(code, msg); }
+}  // namespace gblb
+
+namespace {
+
 template <class F>
 int guarded(F&& f) {
   try {

@@ -33,6 +33,9 @@ struct LbError : std::runtime_error {
   LbError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
 };
 
+// records msg as the calling thread's last error (returned by lb_last_error) and returns code
+int api_fail(int code, const char* msg);
+
 inline void cuda_check(cudaError_t e, const char* what) {
   if (e != cudaSuccess) {
     if (e == cudaErrorMemoryAllocation) throw LbError(S_OOM, std::string(what) + ": " + cudaGetErrorString(e));

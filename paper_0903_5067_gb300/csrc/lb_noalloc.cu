@@ -1,16 +1,18 @@
 // lb_fluid_sums_noalloc: fluid mass and momentum of a population field, computed without
 // allocating device memory.
 //
-// Some callers cannot allocate device memory at the point where they need these sums: code
-// running while a CUDA stream is being captured into a graph (cudaMalloc is not allowed
-// there), hosts whose device memory is entirely owned by another allocator or framework, and
-// time-critical loops that must not pay for an allocation.  This entry point serves them:
-// its per-block partial sums go to a fixed scratch array declared below at file scope, which
-// every GPU that loads the library holds until the process exits.
+// Some callers cannot allocate device memory at the point where they need these sums: a host
+// application whose device memory is all reserved by another allocator (a framework's caching
+// allocator, a memory pool sized to the whole GPU), where a cudaMalloc of its own would fail
+// or fragment that pool; and time-critical loops, where cudaFree's implicit device-wide
+// synchronisation and the allocation's latency are not acceptable.  This entry point serves
+// them: its per-block partial sums go to a fixed scratch array declared below at file scope,
+// which every GPU that loads the library holds until the process exits.
 #include <cuda_runtime.h>
 #include <mutex>
 
 #include "../../include/lb.h"
+#include "lb_engine.h"
 
 namespace {
 
@@ -103,24 +105,46 @@ int device_addresses(int dev, double** partials, double** result) {
 
 extern "C" int lb_fluid_sums_noalloc(const double* pop_dev, int L, double a, double h, double* out_host,
                                      void* stream) {
-  if (!pop_dev || !out_host || !(a > 0) || !(h > 0)) return LB_ERR_ARG;
-  if (L < 1 || L > LB_NOALLOC_MAX_L) return LB_ERR_ARG;  // beyond the static scratch capacity
+  using gblb::api_fail;
+  if (!pop_dev || !out_host) return api_fail(LB_ERR_ARG, "lb_fluid_sums_noalloc: null population or output pointer");
+  if (!(a > 0) || !(h > 0)) return api_fail(LB_ERR_ARG, "lb_fluid_sums_noalloc: a and h must be > 0");
+  if (L < 1 || L > LB_NOALLOC_MAX_L)
+    return api_fail(LB_ERR_ARG, "lb_fluid_sums_noalloc: L outside [1, LB_NOALLOC_MAX_L] (the fixed scratch holds "
+                                "the partial sums of at most 256^3 nodes)");
   const long long nnodes = (long long)L * L * L;
-  const int nblocks = (int)((nnodes + kThreads - 1) / kThreads);
-  if (nblocks > kMaxBlocks) return LB_ERR_ARG;
+  int nblocks = (int)((nnodes + kThreads - 1) / kThreads);
+  if (nblocks > kMaxBlocks) return api_fail(LB_ERR_ARG, "lb_fluid_sums_noalloc: box beyond the scratch capacity");
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LB_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return api_fail(LB_ERR_CUDA, "lb_fluid_sums_noalloc: no usable current device");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (s) {  // the scratch address below belongs to the current device: the stream must too
+    int sdev = -1;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess)
+      return api_fail(LB_ERR_ARG, "lb_fluid_sums_noalloc: the stream is not a valid CUDA stream");
+    if (sdev != dev)
+      return api_fail(LB_ERR_ARG, "lb_fluid_sums_noalloc: the stream belongs to another device than the current one");
+  }
   double* partials = nullptr;
   double* result = nullptr;
-  const int rc = device_addresses(dev, &partials, &result);
-  if (rc != LB_OK) return rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_partials<<<nblocks, kThreads, 0, s>>>(pop_dev, nnodes, partials);
-  if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
-  k_finish<<<1, kThreads, 0, s>>>(partials, nblocks, a * a * a, a * a * a * a / h, result);
-  if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
+  if (device_addresses(dev, &partials, &result) != LB_OK)
+    return api_fail(LB_ERR_CUDA, "lb_fluid_sums_noalloc: cudaGetSymbolAddress of the scratch array failed");
+  // launches checked by their own return codes: an error left pending by the caller's
+  // earlier work is neither taken nor reported here
+  {
+    void* args[] = {(void*)&pop_dev, (void*)&nnodes, (void*)&partials};
+    if (cudaLaunchKernel((const void*)k_partials, dim3((unsigned)nblocks), dim3(kThreads), args, 0, s) != cudaSuccess)
+      return api_fail(LB_ERR_CUDA, "lb_fluid_sums_noalloc: partial-sum kernel launch failed");
+  }
+  {
+    const double a3 = a * a * a, ms = a * a * a * a / h;
+    void* args[] = {(void*)&partials, (void*)&nblocks, (void*)&a3, (void*)&ms, (void*)&result};
+    if (cudaLaunchKernel((const void*)k_finish, dim3(1), dim3(kThreads), args, 0, s) != cudaSuccess)
+      return api_fail(LB_ERR_CUDA, "lb_fluid_sums_noalloc: final-sum kernel launch failed");
+  }
   if (cudaMemcpyAsync(out_host, result, 4 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return LB_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return LB_ERR_CUDA;
+    return api_fail(LB_ERR_CUDA, "lb_fluid_sums_noalloc: copy of the sums to the host failed");
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return api_fail(LB_ERR_CUDA, cudaGetErrorString(e));
   return LB_OK;
 }

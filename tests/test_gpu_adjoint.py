@@ -141,6 +141,31 @@ def test_autograd_function_returns_the_adjoint(lblib):
     assert float(z.grad) == pytest.approx(3.0 * gz, rel=1e-12)
 
 
+def test_autograd_function_keeps_the_device_and_skips_the_adjoint_without_grad(lblib):
+    """x0 and zeta on the GPU: O and the gradients come back on that device in the inputs'
+    dtypes; without requires_grad the forward gives the same O from the steps alone."""
+    import torch
+    from paper_0903_5067_gb300.autograd import chain_displacement
+
+    L, N, T, K, seed = 8, 4, 10, 4, 5
+    X0 = inputs.chain_walk(N, L=L, bond=0.97, seed=seed, self_avoiding=True)
+    x = torch.tensor(X0, dtype=torch.float64, device="cuda", requires_grad=True)
+    z = torch.tensor(20.8, dtype=torch.float32, device="cuda", requires_grad=True)
+    params = dict(L=L, seed=seed, precision=lblib.LB_FP64)
+    O = chain_displacement(x, z, params, T=T, K=K)
+    assert O.device == x.device and O.dtype == torch.float64
+    O.backward()
+    assert x.grad.device == x.device and x.grad.dtype == torch.float64
+    assert z.grad.device == z.device and z.grad.dtype == torch.float32
+    O_ref, gx, gz = _gpu_adjoint(lblib, L, X0, 20.8, T, K, seed, lblib.LB_FP64)
+    assert O.item() == pytest.approx(O_ref, rel=1e-14)
+    assert np.allclose(x.grad.cpu().numpy(), gx, rtol=1e-12)
+    assert float(z.grad) == pytest.approx(gz, rel=1e-6)
+    with torch.no_grad():
+        O2 = chain_displacement(x, z, params, T=T, K=K)
+    assert O2.item() == pytest.approx(O.item(), rel=1e-13) and not O2.requires_grad
+
+
 def test_adjoint_rejects_a_stepped_context(lblib):
     sim = lblib.Simulation(L=8, seed=1, precision=lblib.LB_FP64)
     sim.add_chain(3, x0=inputs.chain_walk(3, L=8, seed=1, self_avoiding=True))
