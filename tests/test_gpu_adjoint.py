@@ -70,7 +70,10 @@ def test_adjoint_fp64_matches_finite_differences_of_the_gpu_path(lblib):
 
 def test_adjoint_c5_workload_matches_oracle_finite_differences(lblib):
     """L=32, N=16, 100 steps, checkpoints every 10, noise fixed by seed 7: FP32 adjoint
-    within 1e-3 and FP64 adjoint within 1e-6 of central differences of the FP64 oracle."""
+    within 1e-3 and FP64 adjoint within 1e-6 of central differences of the FP64 oracle with
+    the step 1e-5.  The configured step 1e-4 is checked beside it: its truncation error
+    (O(eps^2) times the third derivative of the 100-step objective) is larger, so the FP64
+    bar there is 1e-4; both differences are printed."""
     L, N, T, K, seed, zeta = 32, 16, 100, 10, 7, 20.8
     X0 = inputs.chain_walk(N, L=L, bond=0.97, seed=seed, self_avoiding=True)
     O64, gx64, gz64 = _gpu_adjoint(lblib, L, X0, zeta, T, K, seed, lblib.LB_FP64)
@@ -78,28 +81,39 @@ def test_adjoint_c5_workload_matches_oracle_finite_differences(lblib):
     O_or, _ = _oracle_objective(L, X0, zeta, T, seed)
     assert O64 == pytest.approx(O_or, rel=1e-10)
     assert O32 == pytest.approx(O_or, rel=1e-5)
-    eps = 1e-5
+    bars = {1e-5: (1e-6, 1e-3), 1e-4: (1e-4, 1e-3)}  # step: (FP64, FP32) relative bars
+
+    def fd(eps, d=None, dz=0.0):
+        """central difference along (d, dz), or None when a bead changes cell between the two
+        perturbed trajectories (a kink of the trilinear weights)"""
+        dX = np.zeros((N, 3)) if d is None else d
+        op, cp_ = _oracle_objective(L, X0 + eps * dX, zeta + eps * dz, T, seed)
+        om, cm_ = _oracle_objective(L, X0 - eps * dX, zeta - eps * dz, T, seed)
+        return None if not np.array_equal(cp_, cm_) else (op - om) / (2 * eps)
+
     rng = np.random.default_rng(11)
-    checked = 0
+    checked = {1e-5: 0, 1e-4: 0}
     for _ in range(4):
         d = rng.standard_normal((N, 3))
-        op, cp_ = _oracle_objective(L, X0 + eps * d, zeta, T, seed)
-        om, cm_ = _oracle_objective(L, X0 - eps * d, zeta, T, seed)
-        if not np.array_equal(cp_, cm_):
-            continue  # a bead crossed a cell face between the two runs: derivative kink
-        fd = (op - om) / (2 * eps)
-        assert (gx64 * d).sum() == pytest.approx(fd, rel=1e-6, abs=1e-8)
-        assert (gx32 * d).sum() == pytest.approx(fd, rel=1e-3, abs=1e-6)
-        checked += 1
-        if checked == 2:
+        for eps, (b64, b32) in bars.items():
+            q = fd(eps, d)
+            if q is None:
+                continue
+            print(f"direction {checked[eps]}: step {eps:.0e}: FD {q:.10e}, FP64 adjoint rel. diff "
+                  f"{(gx64 * d).sum() / q - 1:+.2e}, FP32 {(gx32 * d).sum() / q - 1:+.2e}")
+            assert (gx64 * d).sum() == pytest.approx(q, rel=b64, abs=1e-8)
+            assert (gx32 * d).sum() == pytest.approx(q, rel=b32, abs=1e-6)
+            checked[eps] += 1
+        if min(checked.values()) >= 2:
             break
-    assert checked >= 1
-    op, cp_ = _oracle_objective(L, X0, zeta + eps, T, seed)
-    om, cm_ = _oracle_objective(L, X0, zeta - eps, T, seed)
-    if np.array_equal(cp_, cm_):
-        fdz = (op - om) / (2 * eps)
-        assert gz64 == pytest.approx(fdz, rel=1e-6, abs=1e-8)
-        assert gz32 == pytest.approx(fdz, rel=1e-3, abs=1e-6)
+    assert min(checked.values()) >= 1
+    for eps, (b64, b32) in bars.items():
+        q = fd(eps, dz=1.0)
+        if q is not None:
+            print(f"zeta: step {eps:.0e}: FD {q:.10e}, FP64 adjoint rel. diff {gz64 / q - 1:+.2e}, "
+                  f"FP32 {gz32 / q - 1:+.2e}")
+            assert gz64 == pytest.approx(q, rel=b64, abs=1e-8)
+            assert gz32 == pytest.approx(q, rel=b32, abs=1e-6)
 
 
 def test_adjoint_c5_workload_matches_the_oracle_tangent(lblib):

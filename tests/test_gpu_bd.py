@@ -106,3 +106,10 @@ def test_bd_chain_properties_match_table1_bd_column(lblib):
     for k, (ref, err) in dict(rg2=(rg2_p, drg2_p), re2=(re2_p, dre2_p), rh=(rh_p, drh_p), dcm=(d_p, dd_p),
                               e1=(e1_p, de1_p), e3=(e3_p, de3_p)).items():
         assert abs(m[k] - ref) <= 3 * np.hypot(se[k], err), k
+    # tau_tr = <R_g^2> / (6 D_CM) against Table 1's last row (BD column)
+    tau_rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "table1_tau_tr.txt"))
+    tau_p, dtau_p = tau_rows[tau_rows[:, 0] == 0][0, 1:]
+    tau = m["rg2"] / (6.0 * m["dcm"])
+    se_tau = tau * np.hypot(se["rg2"] / m["rg2"], se["dcm"] / m["dcm"])
+    print(f"BD: tau_tr {tau:.1f} +- {se_tau:.1f} (paper {tau_p} +- {dtau_p})")
+    assert abs(tau - tau_p) <= 3 * np.hypot(se_tau, dtau_p)

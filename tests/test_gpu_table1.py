@@ -102,6 +102,13 @@ def test_chain_properties_match_table1(lblib, L):
     assert abs(dcm.mean() - d_p) <= 3 * np.hypot(se(dcm), dd_p)
     assert abs(e1.mean() - e1_p) <= 3 * np.hypot(se(e1), de1_p)
     assert abs(e3.mean() - e3_p) <= 3 * np.hypot(se(e3), de3_p)
+    # tau_tr = <R_g^2> / (6 D_CM), the paper's estimate (Table 1, last row), with the error of
+    # the two measured means propagated
+    tau = rg2.mean() / (6.0 * dcm.mean())
+    se_tau = tau * np.hypot(se_rg / rg2.mean(), se(dcm) / dcm.mean())
+    tau_p, dtau_p = _rows("table1_tau_tr.txt")[L]
+    print(f"L={L}: tau_tr {tau:.1f} +- {se_tau:.1f} (paper {tau_p} +- {dtau_p})")
+    assert abs(tau - tau_p) <= 3 * np.hypot(se_tau, dtau_p)
 
 
 @pytest.mark.parametrize("L", [10, 15, 25])

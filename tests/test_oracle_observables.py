@@ -147,3 +147,19 @@ def test_inverse_hydrodynamic_radius_closed_forms():
     rod = np.array([[[0.0, 0, 0], [1.0, 0, 0], [2.0, 0, 0]], [[0.0, 0, 0], [2.0, 0, 0], [4.0, 0, 0]]])
     one = 2 * (1 + 1 + 0.5) / 9
     assert ob.inverse_hydrodynamic_radius(rod) == pytest.approx((one + one / 2) / 2, rel=1e-14)
+
+
+def test_table1_tau_tr_row_is_rg2_over_six_d_cm():
+    """The golden Table 1 rows are read consistently: the printed tau_tr estimate equals
+    <R_g^2> / (6 D_CM) with D_CM = (printed value) x 1e-3 (reading of the row label
+    'D_CM x 10^-3') within 0.5 %, for the three LB boxes and the BD column."""
+    import os
+
+    g = os.path.join(os.path.dirname(__file__), "golden")
+    tau = {int(r[0]): r[1] for r in np.loadtxt(os.path.join(g, "table1_tau_tr.txt"), ndmin=2)}
+    stat = {int(r[0]): r for r in np.loadtxt(os.path.join(g, "table1_lb_statics.txt"), ndmin=2)}
+    dyn = {int(r[0]): r for r in np.loadtxt(os.path.join(g, "table1_lb_dynamics.txt"), ndmin=2)}
+    bd = np.loadtxt(os.path.join(g, "table1_bd.txt"))
+    for L in (10, 15, 25):
+        assert stat[L][3] / (6.0 * dyn[L][3]) == pytest.approx(tau[L], rel=5e-3)
+    assert bd[2] / (6.0 * bd[6]) == pytest.approx(tau[0], rel=5e-3)
