@@ -197,35 +197,36 @@ def box_muller(u0: np.ndarray, u1: np.ndarray):
     return r * np.cos(theta), r * np.sin(theta)
 
 
-FLUID_CALLS = 3
+FLUID_CALLS = 2
 
 
 def fluid_uniforms(seed, tag, replica, step, index, ncalls=FLUID_CALLS):
-    """(6 ncalls, ...) uniforms per index.  Call c (counter (step, index, c, 0)) gives four
-    words, read as a 128-bit string (word j holds bits 32j .. 32j+31, least significant
-    first); uniform 6c + i takes its bits 21i .. 21i+20 as the integer k: u = (k + 1/2) 2^-21."""
+    """Uniform pairs of the fluid noise, shape (2, 4 ncalls, ...): call c (counter
+    (step, index, c, 0)) gives four 32-bit words; word j is Box-Muller pair p = 4c + j.  Its 21
+    high bits k_r = w >> 11 give the radius uniform u0 = (k_r + 1/2) 2^-21 (row 0), its 11 low
+    bits k_a = w mod 2^11 the angle uniform u1 = (k_a + 1/2) 2^-11 (row 1): 2048 equally
+    spaced angles, offset by half a step (reading of the noise layout; the paper asks only for
+    Gaussian fluctuations of unit variance on the non-conserved modes, Sec. II B)."""
     k0, k1 = philox_key(seed, tag, replica)
     index = np.asarray(index, dtype=np.uint64)
-    out = []
+    u0, u1 = [], []
     for call in range(ncalls):
-        w = [v.astype(np.uint64) for v in
-             philox4x32_10(np.uint64(step) & _MASK, index, np.uint64(call), np.uint64(0), k0, k1)]
-        for i in range(6):
-            q, s = divmod(21 * i, 32)
-            two = w[q] | ((w[q + 1] << np.uint64(32)) if q < 3 else np.uint64(0))
-            k = (two >> np.uint64(s)) & np.uint64(0x1FFFFF)
-            out.append((k.astype(np.float64) + 0.5) * 2.0 ** -21)
-    return np.array(out)
+        w = philox4x32_10(np.uint64(step) & _MASK, index, np.uint64(call), np.uint64(0), k0, k1)
+        for j in range(4):
+            wj = w[j].astype(np.uint64)
+            u0.append(((wj >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -21)
+            u1.append(((wj & np.uint64(0x7FF)).astype(np.float64) + 0.5) * 2.0 ** -11)
+    return np.array([u0, u1])
 
 
 def fluid_gaussians(seed, tag, replica, step, index):
-    """18 standard normals per index: pair p = 0..8 is Box-Muller on the uniforms (2p, 2p+1)
-    of fluid_uniforms.  Mode k = 4..18 takes g[k - 4]; the stress modes 4..9 thus depend on
-    the first call only."""
+    """16 standard normals per index: pair p = 0..7 is Box-Muller on (u0[p], u1[p]) of
+    fluid_uniforms, giving g[2p], g[2p+1].  Mode k = 4..18 takes g[k - 4] (g[15] is unused);
+    the stress modes 4..9 thus depend on words 0..2 of the first call only."""
     u = fluid_uniforms(seed, tag, replica, step, index)
     out = []
-    for p in range(9):
-        g0, g1 = box_muller(u[2 * p], u[2 * p + 1])
+    for p in range(8):
+        g0, g1 = box_muller(u[0, p], u[1, p])
         out += [g0, g1]
     return np.array(out)
 

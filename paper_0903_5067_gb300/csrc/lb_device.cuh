@@ -42,6 +42,53 @@ __device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat16* p, float
 template <>
 __device__ __forceinline__ void st<__half, float>(__half* p, float v) { *p = __float2half_rn(v); }
 
+// two consecutive elements (the first at an even element offset, so 2 sizeof(S)-aligned) in
+// one access: 8 bytes for FP32, 16 for FP64, 4 for the 16-bit formats
+template <class S, class R>
+__device__ __forceinline__ void ld2(const S* p, R& a, R& b);
+template <>
+__device__ __forceinline__ void ld2<float, float>(const float* p, float& a, float& b) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  a = v.x;
+  b = v.y;
+}
+template <>
+__device__ __forceinline__ void ld2<double, double>(const double* p, double& a, double& b) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  a = v.x;
+  b = v.y;
+}
+template <>
+__device__ __forceinline__ void ld2<__nv_bfloat16, float>(const __nv_bfloat16* p, float& a, float& b) {
+  const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(p);
+  a = __low2float(v);
+  b = __high2float(v);
+}
+template <>
+__device__ __forceinline__ void ld2<__half, float>(const __half* p, float& a, float& b) {
+  const __half2 v = *reinterpret_cast<const __half2*>(p);
+  a = __low2float(v);
+  b = __high2float(v);
+}
+template <class S, class R>
+__device__ __forceinline__ void st2(S* p, R a, R b);
+template <>
+__device__ __forceinline__ void st2<float, float>(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+template <>
+__device__ __forceinline__ void st2<double, double>(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+template <>
+__device__ __forceinline__ void st2<__nv_bfloat16, float>(__nv_bfloat16* p, float a, float b) {
+  *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+}
+template <>
+__device__ __forceinline__ void st2<__half, float>(__half* p, float a, float b) {
+  *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+}
+
 // 1/rho for the LB kernel: the hardware reciprocal in single precision (1 ulp; the density is
 // a normal number), correctly rounded division in double
 template <class R>
@@ -67,7 +114,7 @@ struct FluidK {
   R wam[Q], wae[Q], wag[Q];
   uint32_t k0, k1; // Philox key of the fluid stream
   RoundKeys rk;    // its ten round keys
-  int ncalls;      // Philox calls per node: 0 (noise off), 1 (stress modes only), 3 (all)
+  int ncalls;      // Philox calls per node: 0 (noise off), 1 (stress modes only), 2 (all)
   int body_on;     // uniform body force
   R body_dJ[3];    // lattice momentum it adds per step and node: f h^2 / a
   unsigned long long* nonpos;  // counter of non-positive densities met by the noise
@@ -348,12 +395,12 @@ __host__ __device__ __forceinline__ void pops_from_w2scaled(const R a[Q], R n[Q]
 // ---------------------------------------------------------------------------------------
 // LB kernel: pull-stream + collide for every node (Sec. II B, Eq. 3)
 // ---------------------------------------------------------------------------------------
-// Collide the 19 pulled populations n of one node (Sec. II B, Eq. 3) and write its 19
-// post-collision populations to dst (element offset i * pl + node for population i).
-template <class S, class R, bool DEV, bool NOISE, class I>
-__device__ __forceinline__ void lb_collide_store(const R* n, S* __restrict__ dst, const FluidK<R>& P, const I pl,
-                                                 const RoundKeys& rk, unsigned long long* nonpos,
-                                                 const uint32_t step, const unsigned node) {
+// Collide the 19 pulled populations n of one node (Sec. II B, Eq. 3) into its 19
+// post-collision populations out (lb_collide_store: written to dst at element offset
+// i * pl + node for population i).
+template <class R, bool DEV, bool NOISE>
+__device__ __forceinline__ void lb_collide(const R* n, R out[Q], const FluidK<R>& P, const RoundKeys& rk,
+                                           unsigned long long* nonpos, const uint32_t step, const unsigned node) {
   // moments 0..9 (the kinetic modes relax to zero and are not needed)
   R m[10];
   moments_0_9<R>(n, m);
@@ -402,8 +449,15 @@ __device__ __forceinline__ void lb_collide_store(const R* n, S* __restrict__ dst
     a[9] += dm[9] * R(InvB<9>::v / 36.0);
   }
 
-  R out[Q];
   pops_from_w2scaled<R>(a, out);
+}
+
+template <class S, class R, bool DEV, bool NOISE, class I>
+__device__ __forceinline__ void lb_collide_store(const R* n, S* __restrict__ dst, const FluidK<R>& P, const I pl,
+                                                 const RoundKeys& rk, unsigned long long* nonpos,
+                                                 const uint32_t step, const unsigned node) {
+  R out[Q];
+  lb_collide<R, DEV, NOISE>(n, out, P, rk, nonpos, step, node);
 #pragma unroll
   for (int i = 0; i < Q; ++i) st<S, R>(dst + ((I)i * pl + (I)node), out[i]);
 }
@@ -488,6 +542,73 @@ __device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict
   lb_collide_store<S, R, DEV, NOISE, I>(n, dst, P, pl, P.rk, P.nonpos, step, node);
 }
 
+// The populations the two nodes (x0, y, z) and (x0 + 1, y, z), x0 even, pull from their
+// neighbours (periodic; Sec. II B, Eq. 3): n0 for x0, n1 for x0 + 1.  The planes with c_x = 0
+// read both nodes' sources with one two-element access (x0 even and L even keep it aligned);
+// the planes with c_x = +-1 read their two sources x0 - c_x, x0 + 1 - c_x one by one.
+template <class S, class R, class I>
+__device__ __forceinline__ void lb_pull2(const S* __restrict__ src, const unsigned L, const I pl, const unsigned x0,
+                                         const unsigned y, const unsigned z, R n0[Q], R n1[Q]) {
+  const unsigned xm = x0 ? x0 - 1 : L - 1, xp = x0 + 1, xpp = (x0 + 2 < L) ? x0 + 2 : 0;
+  const unsigned ym = y ? y - 1 : L - 1, yp = (y + 1 < L) ? y + 1 : 0;
+  const unsigned zm = z ? z - 1 : L - 1, zp = (z + 1 < L) ? z + 1 : 0;
+  const unsigned LL = L * L;
+  const unsigned ry[3] = {yp * L, y * L, ym * L};
+  const unsigned rz[3] = {zp * LL, z * LL, zm * LL};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const I row = (I)i * pl + (I)(ry[cy(i) + 1] + rz[cz(i) + 1]);
+    if (cx(i) == 0) {
+      ld2<S, R>(src + (row + (I)x0), n0[i], n1[i]);
+    } else if (cx(i) == 1) {  // sources x0 - 1, x0
+      n0[i] = ld<S, R>(src + (row + (I)xm));
+      n1[i] = ld<S, R>(src + (row + (I)x0));
+    } else {  // sources x0 + 1, x0 + 2
+      n0[i] = ld<S, R>(src + (row + (I)xp));
+      n1[i] = ld<S, R>(src + (row + (I)xpp));
+    }
+  }
+}
+
+// One LB tile with two nodes per thread along x (L even): the 2 blockDim.x x blockDim.y nodes
+// at x = 2 (tx blockDim.x + threadIdx.x) + {0, 1}, y = ty blockDim.y + threadIdx.y, z.  The
+// same update as lb_tile, node by node, with the 19 post-collision pairs written by
+// two-element stores.  Marked nodes stage their corrections into
+// stage[(2 tid + j) + i * 2T] (j: the node of the pair).
+template <class S, class R, bool DEV, bool NOISE, class I, bool CORR>
+__device__ __forceinline__ void lb_tile2(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
+                                         const PendK<R>& Pd, const uint32_t step, unsigned tx, unsigned ty,
+                                         unsigned z, R* stage) {
+  const unsigned L = P.L;
+  const unsigned x0 = 2 * (tx * blockDim.x + threadIdx.x);
+  const unsigned y = ty * blockDim.y + threadIdx.y;
+  if (x0 >= L || y >= L) return;
+  const unsigned node = x0 + L * (y + L * z);
+  const unsigned mw = CORR && Pd.have_prev ? Pd.prev_mask[Pd.seg0 + (node >> kSegShift)] >> (node & 31u) : 0u;
+  const I pl = (I)P.plane;
+  R n0[Q], n1[Q];
+  lb_pull2<S, R, I>(src, L, pl, x0, y, z, n0, n1);
+  if (CORR && (mw & 3u)) {
+    const unsigned T2 = 2 * blockDim.x * blockDim.y, t2 = 2 * (threadIdx.x + blockDim.x * threadIdx.y);
+#pragma unroll 1
+    for (unsigned j = 0; j < 2; ++j)
+      if ((mw >> j) & 1u) stage_corrections<R>(Pd.prev_dense, Pd.plane, L, x0 + j, y, z, stage + t2 + j, T2);
+    if (mw & 1u) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) n0[i] += stage[t2 + i * T2];
+    }
+    if (mw & 2u) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) n1[i] += stage[t2 + 1 + i * T2];
+    }
+  }
+  R o0[Q], o1[Q];
+  lb_collide<R, DEV, NOISE>(n0, o0, P, P.rk, P.nonpos, step, node);
+  lb_collide<R, DEV, NOISE>(n1, o1, P, P.rk, P.nonpos, step, node + 1);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) st2<S, R>(dst + ((I)i * pl + (I)node), o0[i], o1[i]);
+}
+
 // Programmatic dependent launch (a grid launched with programmatic stream serialization may
 // start before the previous grid in the stream has completed): `wait` blocks until that
 // previous grid has completed and its writes are visible; `release` lets the next grid start.
@@ -502,8 +623,18 @@ __device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddep
 // runs beside it; the blocks of plane z = L, scheduled last, wait for it (bit 1), so that the
 // grid completes only after the bead kernel and whatever comes next may take this grid's
 // completion for both.  (A wait at the end of every block raised the register count.)
-template <class S, class R, bool DEV, bool NOISE, class I, bool CORR>
-__global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* __restrict__ dst,
+// Resident blocks of 256 threads per SM that the single-precision LB kernels are compiled
+// for: 6 (40 registers) with one node per thread, 4 (64 registers) with two, so that 48 and 32
+// warps keep 48 and 64 node updates' loads in flight per SM quarter; the FP64 kernel is
+// bound by FP64 arithmetic and compiled without a bound.
+template <class R, bool PAIR>
+struct LbMinBlocks {
+  static constexpr int value = sizeof(R) == 4 ? (PAIR ? 4 : 6) : 1;
+};
+
+// PAIR: two nodes per thread along x (lb_tile2, L even), else one (lb_tile).
+template <class S, class R, bool DEV, bool NOISE, class I, bool CORR, bool PAIR>
+__global__ void __launch_bounds__(256, LbMinBlocks<R, PAIR>::value) k_lb_step(const S* __restrict__ src, S* __restrict__ dst,
                                                   const FluidK<R> P, const PendK<R> Pd, const uint32_t step) {
   extern __shared__ __align__(16) unsigned char lsm[];
   if (blockIdx.z >= P.L) {  // a waiting block
@@ -513,8 +644,12 @@ __global__ void __launch_bounds__(256) k_lb_step(const S* __restrict__ src, S* _
   }
   if (P.pdl & 1) grid_dependency_wait();
   allow_dependent_launch();
-  lb_tile<S, R, DEV, NOISE, I, CORR>(src, dst, P, Pd, step, blockIdx.x, blockIdx.y, blockIdx.z,
-                                     reinterpret_cast<R*>(lsm));
+  if constexpr (PAIR)
+    lb_tile2<S, R, DEV, NOISE, I, CORR>(src, dst, P, Pd, step, blockIdx.x, blockIdx.y, blockIdx.z,
+                                        reinterpret_cast<R*>(lsm));
+  else
+    lb_tile<S, R, DEV, NOISE, I, CORR>(src, dst, P, Pd, step, blockIdx.x, blockIdx.y, blockIdx.z,
+                                       reinterpret_cast<R*>(lsm));
 }
 
 // ---------------------------------------------------------------------------------------

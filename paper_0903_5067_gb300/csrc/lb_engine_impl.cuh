@@ -36,11 +36,15 @@ class EngineT final : public Engine {
 
   void initialise(const double* x0, const double* v0, cudaStream_t s) override {
     snap_valid_ = false;
-    if ((size_t)Q * 256 * sizeof(R) > 48 * 1024) {  // FP64: staged corrections of a 256-node tile
-      for (int v = 0; v < 8; ++v)
-        cuda_check(cudaFuncSetAttribute(lb_kernel(v & 1, (v >> 1) & 1, v >> 2),
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(Q * 256 * sizeof(R))),
-                   "LB kernel shared memory");
+    {
+      dim3 blk, grd;
+      lb_launch_shape(blk, grd, pair_nodes());
+      const size_t sb = lb_stage_bytes(blk);
+      if (sb > 48 * 1024)  // FP64: staged corrections of a 256-thread tile
+        for (int v = 0; v < 8; ++v)
+          cuda_check(cudaFuncSetAttribute(lb_kernel(v & 1, (v >> 1) & 1, v >> 2, pair_nodes()),
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb),
+                     "LB kernel shared memory");
     }
     if (bead_smem() > 48 * 1024)
       cuda_check(cudaFuncSetAttribute(k_bead_step<S, R, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -262,7 +266,7 @@ class EngineT final : public Engine {
       cuda_check(cudaFuncSetAttribute(k_adj_bead<S, R, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                  "adjoint smem");
     dim3 blk, grd;
-    lb_launch_shape(blk, grd);
+    lb_launch_shape(blk, grd, false);  // the adjoint LB kernel: one node per thread
     int cur_lam = 0;
     // 3. reverse sweep over the segments
     for (int sgi = nck - 1; sgi >= 0; --sgi) {
@@ -559,13 +563,13 @@ class EngineT final : public Engine {
     const bool chained = ev0 == nullptr;
     P.pdl = chained ? (N_ > 0 ? 2 : 1) : 0;
     dim3 blk, grd;
-    lb_launch_shape(blk, grd);
+    lb_launch_shape(blk, grd, pair_nodes());
     cudaLaunchConfig_t lc;
     memset(&lc, 0, sizeof(lc));
     if (P.pdl & 2) grd.z += 1;  // the plane of waiting blocks
     lc.gridDim = grd;
     lc.blockDim = blk;
-    lc.dynamicSmemBytes = Pd.have_prev ? (size_t)Q * blk.x * blk.y * sizeof(R) : 0;  // staged corrections
+    lc.dynamicSmemBytes = Pd.have_prev ? lb_stage_bytes(blk) : 0;  // staged corrections
     lc.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -573,7 +577,8 @@ class EngineT final : public Engine {
     lc.attrs = at;
     lc.numAttrs = chained ? 1 : 0;
     if (ev0) cudaEventRecord(ev0, s);
-    cuda_check(cudaLaunchKernelEx(&lc, lb_kernel(P.ncalls > 0, narrow_offsets(), N_ > 0), A, Bo, P, Pd, k), "LB kernel");
+    cuda_check(cudaLaunchKernelEx(&lc, lb_kernel(P.ncalls > 0, narrow_offsets(), N_ > 0, pair_nodes()), A, Bo, P, Pd, k),
+               "LB kernel");
     if (ev1) cudaEventRecord(ev1, s);
     cuda_check(cudaGetLastError(), "LB kernel");
   }
@@ -609,26 +614,42 @@ class EngineT final : public Engine {
   size_t nsegs() const { return (size_t)((nnodes_ + 31) >> kSegShift); }
 
   // the LB kernel for noise on/off, 32-bit (all 19 planes below 2^32 elements) or 64-bit
-  // element offsets, and with or without the deferred force corrections (a chain)
+  // element offsets, with or without the deferred force corrections (a chain), and with two
+  // nodes per thread along x (even L) or one
   using LbKernel = void (*)(const S*, S*, const FluidK<R>, const PendK<R>, const uint32_t);
-  static LbKernel lb_kernel(bool noise, bool narrow, bool corr) {
+  template <bool NOISE, class I, bool CORR>
+  static LbKernel lb_kernel_p(bool pair) {
+    return pair ? k_lb_step<S, R, DEV, NOISE, I, CORR, true> : k_lb_step<S, R, DEV, NOISE, I, CORR, false>;
+  }
+  static LbKernel lb_kernel(bool noise, bool narrow, bool corr, bool pair) {
     using U = unsigned;
     using W = unsigned long long;
     if (corr) {
-      if (noise) return narrow ? k_lb_step<S, R, DEV, true, U, true> : k_lb_step<S, R, DEV, true, W, true>;
-      return narrow ? k_lb_step<S, R, DEV, false, U, true> : k_lb_step<S, R, DEV, false, W, true>;
+      if (noise) return narrow ? lb_kernel_p<true, U, true>(pair) : lb_kernel_p<true, W, true>(pair);
+      return narrow ? lb_kernel_p<false, U, true>(pair) : lb_kernel_p<false, W, true>(pair);
     }
-    if (noise) return narrow ? k_lb_step<S, R, DEV, true, U, false> : k_lb_step<S, R, DEV, true, W, false>;
-    return narrow ? k_lb_step<S, R, DEV, false, U, false> : k_lb_step<S, R, DEV, false, W, false>;
+    if (noise) return narrow ? lb_kernel_p<true, U, false>(pair) : lb_kernel_p<true, W, false>(pair);
+    return narrow ? lb_kernel_p<false, U, false>(pair) : lb_kernel_p<false, W, false>(pair);
   }
   bool narrow_offsets() const { return (unsigned long long)Q * plane_ <= 0xFFFFFFFFull; }
+  // two nodes per thread along x: every row starts at an even element offset (even L); in
+  // single-precision arithmetic only (the FP64 kernel is bound by FP64 arithmetic, which two
+  // nodes per thread do not reduce)
+  bool pair_nodes() const { return (L_ & 1) == 0 && sizeof(R) == 4; }
 
-  void lb_launch_shape(dim3& blk, dim3& grd) const {
-    unsigned bx = ((unsigned)L_ + 31) / 32 * 32;
+  // threads along x cover a row of L nodes (L/2 threads with two nodes each), up to 256 per
+  // block; the rest of the 256 threads take further rows
+  void lb_launch_shape(dim3& blk, dim3& grd, bool pair) const {
+    const unsigned row = pair ? (unsigned)L_ / 2 : (unsigned)L_;
+    unsigned bx = (row + 31) / 32 * 32;
     if (bx > 256) bx = 256;
     const unsigned by = 256 / bx;
     blk = dim3(bx, by, 1);
-    grd = dim3(((unsigned)L_ + bx - 1) / bx, ((unsigned)L_ + by - 1) / by, (unsigned)L_);
+    grd = dim3((row + bx - 1) / bx, ((unsigned)L_ + by - 1) / by, (unsigned)L_);
+  }
+  // staged corrections of marked nodes: 19 values per node of a tile
+  size_t lb_stage_bytes(const dim3& blk) const {
+    return (size_t)Q * blk.x * blk.y * (pair_nodes() ? 2 : 1) * sizeof(R);
   }
 
   size_t bead_smem() const {
@@ -673,7 +694,7 @@ class EngineT final : public Engine {
     P.gs = (R)gs;
     P.gb = (R)gb;
     const bool noise = c.noise_fluid && c.kT > 0.0;
-    P.ncalls = noise ? (c.stress_only ? 1 : 3) : 0;
+    P.ncalls = noise ? (c.stress_only ? 1 : 2) : 0;
     const double mu = 3.0 * c.kT * c.h * c.h / pow(c.a, 5);
     for (int k = 0; k < Q; ++k) {
       double g = 0.0;

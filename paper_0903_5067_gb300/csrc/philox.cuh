@@ -6,8 +6,8 @@
 // xoring in the key, the key advanced by the two Weyl increments between rounds.
 //
 // Stream layout (library convention): key = (seed_lo32, tag | replica << 8); counter =
-// (step, index, call, 0); tag 0 = fluid modes (3 calls per node, each cut into six uniforms
-// of 21 bits), tag 1 = beads (1 call), tag 3 = Brownian dynamics (1 call).
+// (step, index, call, 0); tag 0 = fluid modes (2 calls per node, each 32-bit word one
+// Box-Muller pair), tag 1 = beads (1 call), tag 3 = Brownian dynamics (1 call).
 #pragma once
 #include <stdint.h>
 
@@ -99,46 +99,23 @@ __device__ __forceinline__ void box_muller(double u0, double u1, double& g0, dou
 }
 
 // ---------------------------------------------------------------------------------------
-// The fluid's noise stream.  Call c = 0, 1, 2 with counter (step, node, c, 0) gives a 128-bit
-// string w_0 .. w_3 (word j holds bits 32 j .. 32 j + 31, least significant first), cut into
-// six uniforms: uniform i = 0..5 takes the 21 bits 21 i .. 21 i + 20 as an integer k,
-// u = (k + 1/2) 2^-21.  Box-Muller pair p = 3 c + q turns uniforms (2q, 2q + 1) of call c into
-// (g_2p, g_2p+1); mode k = 4..18 takes g_(k-4).  The stress modes 4..9 thus draw on call 0
-// alone; the kinetic modes 10..18 on calls 1 and 2 (pairs 3..7; g_15 and pair 8 are not
-// formed).
+// The fluid's noise stream.  Call c = 0, 1 with counter (step, node, c, 0) gives four 32-bit
+// words; word j is Box-Muller pair p = 4 c + j: its 21 high bits k_r = w >> 11 give the radius
+// uniform u0 = (k_r + 1/2) 2^-21, its 11 low bits k_a = w & 0x7ff the angle uniform
+// u1 = (k_a + 1/2) 2^-11 (2048 equally spaced angles offset by half a step: every average of
+// cos^m sin^n of order below 2048 equals its continuous value, so each Gaussian's moments and
+// the independence of a pair's two Gaussians are those of the continuous angle).  Pair p gives
+// (g_2p, g_2p+1); mode k = 4..18 takes g_(k-4).  The stress modes 4..9 draw on words 0..2 of
+// call 0 alone; the kinetic modes 10..18 on word 3 of call 0 and the four words of call 1
+// (g_15 is not formed).
 // ---------------------------------------------------------------------------------------
-template <int J>
-__device__ __forceinline__ uint32_t word_of(const U4& w) {
-  static_assert(J >= 0 && J < 4, "a Philox call has four words");
-  return J == 0 ? w.x : J == 1 ? w.y : J == 2 ? w.z : w.w;
+// the radius uniform of a word as the float 1 + k_r 2^-21 (k_r in the top 21 mantissa bits)
+__device__ __forceinline__ float fluid_radius_1p(uint32_t w) {
+  return __uint_as_float(0x3f800000u | ((w >> 9) & 0x7ffffcu));
 }
-
-// uniform I of one call's words, as the 21-bit integer k (double) or as the float
-// 1 + k 2^-21 (the integer placed in the top 21 mantissa bits)
-template <int I>
-__device__ __forceinline__ uint32_t fluid_k21(const U4& w) {
-  constexpr int b = 21 * I, q = b / 32, s = b % 32;
-  static_assert(b + 21 <= 128, "six uniforms per call");
-  if constexpr (s + 21 <= 32)
-    return (word_of<q>(w) >> s) & 0x1fffffu;
-  else
-    return __funnelshift_r(word_of<q>(w), word_of<q + 1>(w), s) & 0x1fffffu;
-}
-template <int I>
-__device__ __forceinline__ float fluid_mant21(const U4& w) {
-  constexpr int b = 21 * I;
-  static_assert(b + 21 <= 128, "six uniforms per call");
-  uint32_t v;  // bits b .. b + 20 of the call's string at bit positions 2 .. 22
-  if constexpr (b == 0) {
-    v = w.x << 2;
-  } else {
-    constexpr int q = (b - 2) / 32, s = (b - 2) % 32;
-    if constexpr (s + 23 <= 32 || q == 3)  // (q == 3: bits up to b + 20 < 128 lie in word 3)
-      v = word_of<q>(w) >> s;
-    else
-      v = __funnelshift_r(word_of<q>(w), word_of<q + 1>(w), s);
-  }
-  return __uint_as_float(0x3f800000u | (v & 0x7ffffcu));
+// the angle uniform of a word as the float 1 + k_a 2^-11 (k_a in the top 11 mantissa bits)
+__device__ __forceinline__ float fluid_angle_1p(uint32_t w) {
+  return __uint_as_float(0x3f800000u | ((w << 12) & 0x7ff000u));
 }
 
 // Hardware approximations of the special-function unit in their flush-to-zero forms.  The
@@ -187,27 +164,28 @@ struct NoiseScale<float> {
   __device__ __forceinline__ explicit NoiseScale(float rho) : cl(-1.38629436112f * (rho > 0.0f ? rho : 1.0e-30f)) {}
 };
 
-// Box-Muller pair Q (0..2) of one call's words, times sqrt(rho) (Box & Muller 1958, angle in
-// (-pi, pi)).  Single precision: u0 and the angle come from the uniforms as floats 1 + k 2^-21,
-// both exact steps; log2, 1/sqrt, sin and cos on the special-function unit.  Near u0 = 1 the hardware log2's absolute error (2^-22) would dominate
-// -ln u0; there (t = 1 - u0 < 1e-3) log2(u0) is the series -(t + t^2/2 + t^3/3) / ln 2
-// (truncation below 3e-10 relative).  SECOND = false forms g0 only.
-template <int Q, bool SECOND>
-__device__ __forceinline__ void fluid_pair(const U4& w, const NoiseScale<float>& ns, float& g0, float& g1) {
-  const float u0 = fluid_mant21<2 * Q>(w) - 0x1.fffff8p-1f;  // (k0 + 1/2) 2^-21
+// Box-Muller pair of one word, times sqrt(rho) (Box & Muller 1958, angle in (-pi, pi)).
+// Single precision: u0 and the angle come from the uniforms as floats 1 + k 2^-21 and
+// 1 + k 2^-11, both exact steps; log2, 1/sqrt, sin and cos on the special-function unit.  Near
+// u0 = 1 the hardware log2's absolute error (2^-22) would dominate -ln u0; there
+// (t = 1 - u0 < 1e-3) log2(u0) is the series -(t + t^2/2 + t^3/3) / ln 2 (truncation below
+// 3e-10 relative).  SECOND = false forms g0 only.
+template <bool SECOND>
+__device__ __forceinline__ void fluid_pair(uint32_t w, const NoiseScale<float>& ns, float& g0, float& g1) {
+  const float u0 = fluid_radius_1p(w) - 0x1.fffff8p-1f;  // (k_r + 1/2) 2^-21
   const float t = 1.0f - u0;
   const float l2 = t < 1.0e-3f ? t * (-1.44269504f + t * (-0.721347520f + t * -0.480898347f)) : approx_lg2(u0);
   const float x = ns.cl * l2;  // rho (-2 ln u0): >= 1e-30 * 2^-22, a normal number
   const float r = x * approx_rsqrt(x);
-  const float d = fluid_mant21<2 * Q + 1>(w) - 1.5f;  // u1 - 1/2 - 2^-22, exact
-  const float th = fmaf(6.28318530717958647692f, d, 1.49802816e-6f);  // 2 pi (u1 - 1/2), |th| >= 1.5e-6
+  const float d = fluid_angle_1p(w) - 1.5f;                             // k_a 2^-11 - 1/2, exact
+  const float th = fmaf(6.28318530717958647692f, d, 1.53398078788564123e-3f);  // 2 pi (u1 - 1/2), |th| >= pi/2048
   g0 = r * approx_cos(th);
   if (SECOND) g1 = r * approx_sin(th);
 }
-template <int Q, bool SECOND>
-__device__ __forceinline__ void fluid_pair(const U4& w, const NoiseScale<double>& ns, double& g0, double& g1) {
-  const double u0 = ((double)fluid_k21<2 * Q>(w) + 0.5) * 0x1p-21;
-  const double u1 = ((double)fluid_k21<2 * Q + 1>(w) + 0.5) * 0x1p-21;
+template <bool SECOND>
+__device__ __forceinline__ void fluid_pair(uint32_t w, const NoiseScale<double>& ns, double& g0, double& g1) {
+  const double u0 = ((double)(w >> 11) + 0.5) * 0x1p-21;
+  const double u1 = ((double)(w & 0x7ffu) + 0.5) * 0x1p-11;
   const double r = ns.sr * sqrt(-2.0 * log(u0));
   double s, c;
   sincospi(2.0 * u1 - 1.0, &s, &c);
@@ -216,9 +194,9 @@ __device__ __forceinline__ void fluid_pair(const U4& w, const NoiseScale<double>
 }
 
 template <int P, bool SECOND = true, class R, class Emit>
-__device__ __forceinline__ void fluid_pair_emit(const U4& w, const NoiseScale<R>& ns, Emit& emit) {
+__device__ __forceinline__ void fluid_pair_emit(uint32_t w, const NoiseScale<R>& ns, Emit& emit) {
   R g0, g1;
-  fluid_pair<P % 3, SECOND>(w, ns, g0, g1);
+  fluid_pair<SECOND>(w, ns, g0, g1);
   emit(2 * P, g0);
   if (SECOND) emit(2 * P + 1, g1);
 }
@@ -229,17 +207,16 @@ template <class R, class Emit>
 __device__ __forceinline__ void fluid_noise(uint32_t step, uint32_t node, const RoundKeys& rk, bool kinetic,
                                             const NoiseScale<R>& ns, Emit emit) {
   U4 w = philox4x32_10_rk(U4{step, node, 0u, 0u}, rk);
-  fluid_pair_emit<0>(w, ns, emit);
-  fluid_pair_emit<1>(w, ns, emit);
-  fluid_pair_emit<2>(w, ns, emit);
+  fluid_pair_emit<0>(w.x, ns, emit);
+  fluid_pair_emit<1>(w.y, ns, emit);
+  fluid_pair_emit<2>(w.z, ns, emit);
   if (!kinetic) return;
+  fluid_pair_emit<3>(w.w, ns, emit);
   w = philox4x32_10_rk(U4{step, node, 1u, 0u}, rk);
-  fluid_pair_emit<3>(w, ns, emit);
-  fluid_pair_emit<4>(w, ns, emit);
-  fluid_pair_emit<5>(w, ns, emit);
-  w = philox4x32_10_rk(U4{step, node, 2u, 0u}, rk);
-  fluid_pair_emit<6>(w, ns, emit);
-  fluid_pair_emit<7, false>(w, ns, emit);
+  fluid_pair_emit<4>(w.x, ns, emit);
+  fluid_pair_emit<5>(w.y, ns, emit);
+  fluid_pair_emit<6>(w.z, ns, emit);
+  fluid_pair_emit<7, false>(w.w, ns, emit);
 }
 
 template <class R>

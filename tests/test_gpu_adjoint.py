@@ -171,7 +171,7 @@ def test_autograd_function_keeps_the_device_and_skips_the_adjoint_without_grad(l
     O.backward()
     assert x.grad.device == x.device and x.grad.dtype == torch.float64
     assert z.grad.device == z.device and z.grad.dtype == torch.float32
-    O_ref, gx, gz = _gpu_adjoint(lblib, L, X0, 20.8, T, K, seed, lblib.LB_FP64)
+    O_ref, gx, gz = _gpu_adjoint(lblib, L, X0, float(z.item()), T, K, seed, lblib.LB_FP64)  # zeta as FP32 holds it
     assert O.item() == pytest.approx(O_ref, rel=1e-14)
     assert np.allclose(x.grad.cpu().numpy(), gx, rtol=1e-12)
     assert float(z.grad) == pytest.approx(gz, rel=1e-6)

@@ -97,34 +97,50 @@ def test_box_muller_special_angles_and_radius():
     assert np.allclose(g1, [0.0, 1.0, -1.0], atol=1e-15)
 
 
-def test_fluid_uniforms_cut_each_call_into_six_21_bit_fields():
-    """Against the 128-bit string of each call built as one Python integer."""
+def test_fluid_uniforms_take_one_pair_from_each_word():
+    """Against each call's words read as Python integers: word j of call c is pair 4c + j,
+    radius uniform from its 21 high bits, angle uniform from its 11 low bits."""
     idx = np.array([0, 1, 77, 2 ** 21 + 5, 2 ** 32 - 1], dtype=np.uint64)
     u = o.fluid_uniforms(9, o.TAG_FLUID, 3, 41, idx)
-    assert u.shape == (18, idx.size)
+    assert u.shape == (2, 8, idx.size)
     k0, k1 = o.philox_key(9, o.TAG_FLUID, 3)
-    for c in range(3):
+    for c in range(2):
         w = o.philox4x32_10(41, idx, c, 0, k0, k1)
         for n in range(idx.size):
-            big = sum(int(w[j][n]) << (32 * j) for j in range(4))
-            for i in range(6):
-                k = (big >> (21 * i)) & (2 ** 21 - 1)
-                assert u[6 * c + i, n] == (k + 0.5) / 2 ** 21
+            for j in range(4):
+                word = int(w[j][n])
+                assert u[0, 4 * c + j, n] == ((word >> 11) + 0.5) / 2 ** 21
+                assert u[1, 4 * c + j, n] == ((word & 2047) + 0.5) / 2 ** 11
     assert np.all(u > 0) and np.all(u < 1)
-    # exact in single precision: k + 1/2 needs 22 significant bits
+    # exact in single precision: k + 1/2 needs 22 (radius) and 12 (angle) significant bits
     assert np.array_equal(u.astype(np.float32).astype(np.float64), u)
+
+
+def test_discrete_angles_keep_the_moments_of_a_uniform_angle():
+    """The 2048 angles theta_k = 2 pi ((k + 1/2)/2048 - 1/2): the averages of cos, sin,
+    cos sin, cos^2 - 1/2, cos^4 - 3/8, cos^6 - 5/16 and cos^2 sin^2 - 1/8 vanish exactly (they
+    are the continuous values; aliasing starts at order 2048), so the Gaussians g0 = r cos,
+    g1 = r sin have the mean, variance, skewness and kurtosis and the zero correlation of the
+    continuous construction."""
+    th = 2.0 * np.pi * ((np.arange(2048) + 0.5) / 2048 - 0.5)
+    c, s = np.cos(th), np.sin(th)
+    for v in (c, s, c * s, c * c - 0.5, c ** 4 - 3 / 8, c ** 6 - 5 / 16, (c * s) ** 2 - 1 / 8, c ** 3, s ** 3):
+        assert abs(v.mean()) < 1e-15
+    assert th.min() > -np.pi and th.max() < np.pi
 
 
 def test_box_muller_is_standard_normal():
     g = o.fluid_gaussians(seed=3, tag=o.TAG_FLUID, replica=0, step=11, index=np.arange(20000))
-    assert g.shape == (18, 20000)
+    assert g.shape == (16, 20000)
     flat = g.reshape(-1)
     assert stats.kstest(flat, "norm").pvalue > 1e-3
     assert abs(flat.mean()) < 4 / np.sqrt(flat.size)
     assert abs(flat.var() - 1) < 4 * np.sqrt(2 / flat.size)
+    kurt = (flat ** 4).mean()
+    assert abs(kurt - 3) < 4 * np.sqrt(96 / flat.size)
     c = np.corrcoef(g[:, :5000])
-    assert np.max(np.abs(c - np.eye(18))) < 0.07
-    # the pair angles are uniform on (-pi, pi)
+    assert np.max(np.abs(c - np.eye(16))) < 0.07
+    # the pair angles are uniform on (-pi, pi) (2048 levels: far below the KS resolution here)
     ang = np.arctan2(g[1::2], g[0::2]).reshape(-1)
     assert stats.kstest(ang, "uniform", args=(-np.pi, 2 * np.pi)).pvalue > 1e-3
 
