@@ -127,9 +127,13 @@ __device__ __forceinline__ void scaled_moment_adjoint(const R nb[Q], R ab[Q]) {
 //   n_ps(r) = pull(n*_k) ; n*_{k+1}(r) = collide(n_ps(r))   (corrections handled sparsely)
 //   nbar_ps(r) = J_collide(r)^T lambda_{k+1}(r);  lambda_k,i(r - e_i) = nbar_ps,i(r)   (push)
 // ---------------------------------------------------------------------------------------
+// sp: the bead adjoint's (rho-bar, J-bar) at the forced nodes of the step, dense [4][plane] and
+// zero elsewhere; each node folds its four values into its moment adjoint (the push then adds
+// rho-bar + c_i . J-bar to lambda_k,i(r - e_i)) and sets them back to zero.
 template <class S, class R, bool DEV, bool NOISE>
 __global__ void __launch_bounds__(256) k_adj_lb(const S* __restrict__ state, const R* __restrict__ lam_in,
-                                                 R* __restrict__ lam_out, const FluidK<R> P, const uint32_t step) {
+                                                 R* __restrict__ lam_out, R* __restrict__ sp, const FluidK<R> P,
+                                                 const uint32_t step) {
   const unsigned L = P.L;
   const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -180,6 +184,18 @@ __global__ void __launch_bounds__(256) k_adj_lb(const S* __restrict__ state, con
                    [&](int j, R g) { acc += P.ag[4 + j] * g * ab[4 + j]; });
     mb[0] += acc * R(0.5) / sqrt(rho);
   }
+  {
+    R v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = sp[(unsigned long long)q * P.plane + node];
+    if (v[0] != R(0) || v[1] != R(0) || v[2] != R(0) || v[3] != R(0)) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        mb[q] += v[q];
+        sp[(unsigned long long)q * P.plane + node] = R(0);
+      }
+    }
+  }
   // nbar_ps,i = sum_k e_k(c_i) mb_k, pushed to r - e_i
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -193,26 +209,11 @@ __global__ void __launch_bounds__(256) k_adj_lb(const S* __restrict__ state, con
   }
 }
 
-// lambda_k,i(r - e_i) += rhobar(r) + e_i . Jbar(r) at the sparse nodes of the bead adjoint
-template <class R>
-__global__ void __launch_bounds__(256) k_adj_sparse_add(R* __restrict__ lam, const FluidK<R> P,
-                                                         const int* __restrict__ s_node, const R* __restrict__ s_val,
-                                                         const int* __restrict__ s_count, int cap) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= *s_count) return;
-  const int i = blockIdx.y;
-  const int L = (int)P.L;
-  const int node = s_node[u];
-  const int x = node % L, y = (node / L) % L, z = node / (L * L);
-  const int sx = (x - cx(i) + L) % L, sy = (y - cy(i) + L) % L, sz = (z - cz(i) + L) % L;
-  const R v = s_val[u] + R(cx(i)) * s_val[cap + u] + R(cy(i)) * s_val[2 * cap + u] + R(cz(i)) * s_val[3 * cap + u];
-  lam[(unsigned long long)i * P.plane + (unsigned)(sx + L * (sy + L * sz))] += v;
-}
-
 // Chain part of the adjoint of one step, one thread block.
 // In:  bead state of step k (C.x/xl/img/v/F hold it), post-collision populations n*_k
 //      (`state`), lambda(n*_{k+1}) (`lam`), xbar/vbar/fbar of step k+1.
-// Out: xbar/vbar/fbar of step k (in place), zbar (+= d/dzeta), the sparse (rho, J) adjoints.
+// Out: xbar/vbar/fbar of step k (in place), zbar (+= d/dzeta), the (rho, J) adjoints at the
+//      forced nodes into A.sp (read and cleared by k_adj_lb of the same step).
 template <class R>
 struct AdjK {
   R *xbar, *vbar, *fbar;  // 3N each, in/out
@@ -226,9 +227,7 @@ struct AdjK {
   R* u_fb;    // 3 x cap: f-bar per unique node
   R* u_rb;    // 4 x cap: forced-node (rho, J) adjoint per unique node
   R* zb_b;    // N: zeta-bar per bead
-  int* s_node;  // sparse output: node, 4 x cap values, count
-  R* s_val;
-  int* s_count;
+  R* sp;       // output: (rho-bar, J-bar) at the forced nodes, dense [4][plane] (zero elsewhere)
 };
 
 template <class S, class R, bool DEV>
@@ -355,7 +354,6 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
       if (i < ne) slot[i] = lead ? base + __popc(mask & ((1u << tid) - 1u)) : -1;
       base += __popc(mask);
     }
-    if (tid == 0) *A.s_count = base;
   }
   __syncthreads();
   // per unique node p: forward force density f(p), force-correction adjoint -> fbar(p),
@@ -400,7 +398,6 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
     A.u_rb[C.cap + u] = Jb[0];
     A.u_rb[2 * C.cap + u] = Jb[1];
     A.u_rb[3 * C.cap + u] = Jb[2];
-    A.s_node[u] = node;
   }
   __syncthreads();
   // ---- per bead: spreading, friction, interpolation adjoints ---------------------------
@@ -479,7 +476,7 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
       for (int q = 0; q < 4; ++q) v[q] += A.e_rb[q * C.cap + e];
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) A.s_val[q * C.cap + u] = v[q];
+    for (int q = 0; q < 4; ++q) A.sp[(unsigned long long)q * P.plane + (unsigned)node] = v[q];
   }
   // ---- zeta-bar: fixed-order block sum ----------------------------------------------------
   __syncthreads();

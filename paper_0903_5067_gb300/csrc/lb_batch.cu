@@ -33,43 +33,41 @@ struct ReplicaK {
   PendK<R> pd[2];  // pending corrections of a step of parity j: writes slot j, reads slot j ^ 1
   unsigned long long nnodes;
   unsigned long long tile0;  // first global tile of this replica
-  float invL;
   int has_chain;
 };
 
 __global__ void k_set_step(uint32_t* d_step, uint32_t v) { *d_step = v; }
 __global__ void k_add_step(uint32_t* d_step, uint32_t v) { *d_step += v; }
 
-// Decompose node = x + L (y + L z), node < 2^24 (boxes up to 256^3), with a float
-// reciprocal and an exact integer correction.
-__device__ __forceinline__ unsigned div_small(unsigned n, unsigned L, float invL, unsigned& rem) {
-  int q = __float2int_rz(__uint2float_rn(n) * invL);
-  int r = (int)n - q * (int)L;
-  if (r < 0) {
-    --q;
-    r += (int)L;
-  } else if (r >= (int)L) {
-    ++q;
-    r -= (int)L;
-  }
-  rem = (unsigned)r;
-  return (unsigned)q;
+// n / d for n < 2^24 and 2 <= d <= 256 by one multiply-high with m = ceil(2^32 / d): with
+// e = m d - 2^32 < d, n m / 2^32 = n / d + n e / (d 2^32) and n e < 2^32 keeps the error below
+// the distance of n / d to the next integer (checked exhaustively for every d and n in range).
+__host__ __device__ __forceinline__ unsigned magic_of(unsigned d) {
+  return (unsigned)((0x100000000ull + d - 1) / d);
 }
+__device__ __forceinline__ unsigned div_magic(unsigned n, unsigned m) { return __umulhi(n, m); }
 
 // Per-replica fields of the batched LB kernel; the shared fluid parameters and up to
 // kBatchGroup replicas travel in the kernel's parameter block (constant bank), so the
 // collision's coefficients stay instruction operands as in the single-box kernel.
 constexpr int kBatchGroup = 64;
 
+// A replica's nodes are enumerated as thread slots: with two nodes per thread (even L) slot
+// s is the pair (x0 = 2 (s mod L/2), row = s div L/2), otherwise the node (s mod L, s div L);
+// row = y + L z.  Tiles of T consecutive slots; tile0 is the replica's first tile.
 template <class S, class R>
 struct BatchRep {
   S* pop[2];
-  unsigned long long nnodes, tile0, plane;
-  unsigned seg0;  // first mask word of the replica
+  unsigned long long tile0, plane;
+  unsigned nslots;   // L^3 / 2 (pairs) or L^3
+  unsigned rowlen;   // slots per row: L / 2 or L
+  unsigned mag_row;  // magic_of(rowlen)
+  unsigned mag_L;    // magic_of(L)
+  unsigned seg0;     // first mask word of the replica
   unsigned long long* nonpos;
   const R* p_dense[2];  // dense correction fields by slot
   unsigned L;
-  float invL;
+  int pair;
 };
 
 template <class S, class R>
@@ -83,42 +81,69 @@ struct BatchLB {
   RoundKeys rk[kBatchGroup];
 };
 
-// FP32: at most 42 registers (three 512-thread blocks per SM), as the single-box kernel; the
-// rare correction scatter would otherwise raise the whole kernel's register count
-constexpr unsigned kChunk = 2;
-
-// One tile (T = blockDim.x consecutive nodes of replica r): pull-stream + collide (Sec. II B).
+// One tile (T = blockDim.x consecutive thread slots of replica r): pull-stream + collide
+// (Sec. II B), one or two nodes per thread.  A node marked by the previous step adds that
+// step's corrections to what it pulls (replicas without a chain have no correction field and
+// are never marked); the pull is issued before the mark is known, and one copy of the
+// collision follows, as in lb_tile.  Coordinates come from the slot by two multiply-highs.
 template <class S, class R, bool DEV, bool NOISE>
 __device__ __forceinline__ void batch_tile(const BatchLB<S, R>& B, const int r, const unsigned long long tile,
                                            const int parity, const uint32_t step, unsigned char* dsm) {
   const unsigned T = blockDim.x;
   const int pslot = parity ^ 1;  // the previous step's corrections
   const BatchRep<S, R>& rp = B.rep[r];
-  const unsigned long long n0 = (tile - rp.tile0) * T;
-  const unsigned long long node = n0 + threadIdx.x;
-  if (node >= rp.nnodes) return;
-  // a node marked by the previous step adds that step's corrections to what it pulls
-  // (replicas without a chain have no correction field and are never marked); the pull is
-  // issued before the mark is known, and one copy of the collision follows, as in lb_tile.
-  // The node index handed on is formed again from (x, y, z) in 32 bits: the same value taken
-  // from the 64-bit tile arithmetic cost 17 us per step of the 64-replica batch.
-  const unsigned mw = rp.p_dense[pslot] != nullptr ? B.mask[pslot][rp.seg0 + ((unsigned)node >> kSegShift)] : 0u;
+  const unsigned sl = (unsigned)(tile - rp.tile0) * T + threadIdx.x;
+  if (sl >= rp.nslots) return;
   const unsigned L = rp.L;
-  unsigned x, y;
-  const unsigned t = div_small((unsigned)node, L, rp.invL, x);
-  const unsigned z = div_small(t, L, rp.invL, y);
+  const unsigned row = div_magic(sl, rp.mag_row);
+  const unsigned xs = sl - row * rp.rowlen;
+  const unsigned z = div_magic(row, rp.mag_L);
+  const unsigned y = row - z * L;
   const unsigned pl = (unsigned)rp.plane;
-  R n[Q];
-  lb_pull<S, R, unsigned>(rp.pop[parity], L, pl, x, y, z, n);
-  if ((mw >> ((unsigned)node & 31u)) & 1u) {
-    R* col = reinterpret_cast<R*>(dsm) + threadIdx.x;
-    stage_corrections<R>(rp.p_dense[pslot], rp.plane, L, x, y, z, col, T);
+  const bool corr = rp.p_dense[pslot] != nullptr;
+  R* col = reinterpret_cast<R*>(dsm);
+  if (sizeof(R) == 4 && rp.pair) {
+    const unsigned x0 = 2 * xs;
+    const unsigned node = x0 + L * row;
+    const unsigned mw = corr ? B.mask[pslot][rp.seg0 + (node >> kSegShift)] >> (node & 31u) : 0u;
+    R n0[Q], n1[Q];
+    lb_pull2<S, R, unsigned>(rp.pop[parity], L, pl, x0, y, z, n0, n1);
+    if (mw & 3u) {  // marked nodes stage their corrections one after the other
+#pragma unroll 1
+      for (unsigned j = 0; j < 2; ++j) {
+        if (!((mw >> j) & 1u)) continue;
+        stage_corrections<R>(rp.p_dense[pslot], rp.plane, L, x0 + j, y, z, col + threadIdx.x, T);
+        if (j == 0) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) n[i] += col[i * T];
+          for (int i = 0; i < Q; ++i) n0[i] += col[threadIdx.x + i * T];
+        } else {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) n1[i] += col[threadIdx.x + i * T];
+        }
+      }
+    }
+    R o0[Q], o1[Q];
+    lb_collide<R, DEV, NOISE>(n0, o0, B.P, B.rk[r], rp.nonpos, step, node);
+    lb_collide<R, DEV, NOISE>(n1, o1, B.P, B.rk[r], rp.nonpos, step, node + 1);
+    S* dst = rp.pop[parity ^ 1];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st2<S, R>(dst + ((unsigned)i * pl + node), o0[i], o1[i]);
+  } else {
+    const unsigned node = xs + L * row;
+    const unsigned mw = corr ? B.mask[pslot][rp.seg0 + (node >> kSegShift)] : 0u;
+    R n[Q];
+    lb_pull<S, R, unsigned>(rp.pop[parity], L, pl, xs, y, z, n);
+    if ((mw >> (node & 31u)) & 1u) {
+      stage_corrections<R>(rp.p_dense[pslot], rp.plane, L, xs, y, z, col + threadIdx.x, T);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) n[i] += col[threadIdx.x + i * T];
+    }
+    lb_collide_store<S, R, DEV, NOISE, unsigned>(n, rp.pop[parity ^ 1], B.P, pl, B.rk[r], rp.nonpos, step, node);
   }
-  lb_collide_store<S, R, DEV, NOISE, unsigned>(n, rp.pop[parity ^ 1], B.P, pl, B.rk[r], rp.nonpos, step,
-                                               x + L * (y + L * z));
 }
+
+// tiles a persistent block takes from the counter at a time
+constexpr unsigned kChunk = 2;
 
 // PERSIST: persistent blocks take tiles from a per-group counter in chunks of kChunk (blocks
 // that start late, e.g. beside a bead block, simply take fewer); each block's tiles increase,
@@ -127,8 +152,10 @@ __device__ __forceinline__ void batch_tile(const BatchLB<S, R>& B, const int r, 
 // index and the replica a binary search over the table, both uniform across the block, so the
 // replica's fields (its Philox round keys among them) stay in the constant bank and uniform
 // registers; the hardware block scheduler balances the load.
+// FP32: at most 64 registers (two 512-thread or four 256-thread blocks per SM), as the
+// single-box kernel with two nodes per thread.
 template <class S, class R, bool DEV, bool NOISE, bool PERSIST>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 3 : 1) k_batch_lb(const __grid_constant__ BatchLB<S, R> B, int parity,
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_batch_lb(const __grid_constant__ BatchLB<S, R> B, int parity,
                                                    const uint32_t* __restrict__ d_step, uint32_t j) {
   extern __shared__ __align__(16) unsigned char dsm[];  // staged corrections, 19 x T
   const uint32_t step = *d_step + j;
@@ -301,7 +328,7 @@ class BatchT final : public Batch {
     // the engines zeroed their pending counts; no node is marked
     cuda_check(cudaMemsetAsync(flags_[0], 0, 2 * max_segs_ * sizeof(unsigned), s), "memset marks");
     const size_t lbsm = (size_t)Q * 512 * sizeof(R);
-    if (lbsm > 48 * 1024) {  // FP64: staged corrections of a 512-node run
+    if (lbsm > 48 * 1024) {  // FP64: staged corrections of a 512-thread tile
       for (int v = 0; v < 4; ++v)
         cuda_check(cudaFuncSetAttribute(lb_kernel(v & 1, v >> 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)lbsm),
@@ -403,6 +430,10 @@ class BatchT final : public Batch {
     cuda_check(cudaGetLastError(), "batch clear");
   }
 
+  // two nodes per thread slot for even boxes in single-precision arithmetic (as the single-box
+  // kernel)
+  static bool pair_slots(unsigned L) { return (L & 1u) == 0 && sizeof(R) == 4; }
+
   // the batched LB kernel for noise on/off, persistent blocks or one block per tile
   using BatchLbKernel = void (*)(const BatchLB<S, R>, int, const uint32_t*, uint32_t);
   static BatchLbKernel lb_kernel(bool noise, bool persist) {
@@ -427,7 +458,6 @@ class BatchT final : public Batch {
       q.C = eng_[r]->chain_params();
       q.nnodes = eng_[r]->nodes();
       q.tile0 = t;
-      q.invL = 1.0f / (float)q.P.L;
       q.has_chain = eng_[r]->chain_length() > 0;
       for (int jj = 0; jj < 2; ++jj) {
         PendK<R>& pd = q.pd[jj];
@@ -445,7 +475,7 @@ class BatchT final : public Batch {
       }
       segs += (q.nnodes + 31) >> kSegShift;
       noise_ = q.P.ncalls > 0;
-      t += (q.nnodes + threads_ - 1) / threads_;
+      t += (q.nnodes / (pair_slots(q.P.L) ? 2 : 1) + threads_ - 1) / threads_;
     }
     total_tiles_ = t;
     groups_.clear();
@@ -463,16 +493,19 @@ class BatchT final : public Batch {
         BatchRep<S, R>& q = G.rep[r - g0];
         q.pop[0] = tab[r].pop[0];
         q.pop[1] = tab[r].pop[1];
-        q.nnodes = tab[r].nnodes;
         q.tile0 = tt;
         q.plane = tab[r].P.plane;
         q.nonpos = tab[r].P.nonpos;
         q.L = tab[r].P.L;
-        q.invL = tab[r].invL;
+        q.pair = pair_slots(q.L);
+        q.rowlen = q.pair ? q.L / 2 : q.L;
+        q.nslots = (unsigned)(tab[r].nnodes / (q.pair ? 2 : 1));
+        q.mag_row = magic_of(q.rowlen);
+        q.mag_L = magic_of(q.L);
         q.seg0 = tab[r].pd[0].seg0;
         for (int jj = 0; jj < 2; ++jj) q.p_dense[jj] = eng_[r]->pending_dense(jj);
         G.rk[r - g0] = tab[r].P.rk;
-        tt += (q.nnodes + threads_ - 1) / threads_;
+        tt += (q.nslots + threads_ - 1) / threads_;
       }
       G.total_tiles = tt;
       groups_.push_back(G);

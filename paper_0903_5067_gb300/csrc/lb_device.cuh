@@ -573,8 +573,8 @@ __device__ __forceinline__ void lb_pull2(const S* __restrict__ src, const unsign
 // One LB tile with two nodes per thread along x (L even): the 2 blockDim.x x blockDim.y nodes
 // at x = 2 (tx blockDim.x + threadIdx.x) + {0, 1}, y = ty blockDim.y + threadIdx.y, z.  The
 // same update as lb_tile, node by node, with the 19 post-collision pairs written by
-// two-element stores.  Marked nodes stage their corrections into
-// stage[(2 tid + j) + i * 2T] (j: the node of the pair).
+// two-element stores.  Marked nodes stage their corrections one node after the other into
+// stage[tid + i * T], the same 19 T values as lb_tile.
 template <class S, class R, bool DEV, bool NOISE, class I, bool CORR>
 __device__ __forceinline__ void lb_tile2(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
                                          const PendK<R>& Pd, const uint32_t step, unsigned tx, unsigned ty,
@@ -589,17 +589,18 @@ __device__ __forceinline__ void lb_tile2(const S* __restrict__ src, S* __restric
   R n0[Q], n1[Q];
   lb_pull2<S, R, I>(src, L, pl, x0, y, z, n0, n1);
   if (CORR && (mw & 3u)) {
-    const unsigned T2 = 2 * blockDim.x * blockDim.y, t2 = 2 * (threadIdx.x + blockDim.x * threadIdx.y);
+    const unsigned T = blockDim.x * blockDim.y, tid = threadIdx.x + blockDim.x * threadIdx.y;
 #pragma unroll 1
-    for (unsigned j = 0; j < 2; ++j)
-      if ((mw >> j) & 1u) stage_corrections<R>(Pd.prev_dense, Pd.plane, L, x0 + j, y, z, stage + t2 + j, T2);
-    if (mw & 1u) {
+    for (unsigned j = 0; j < 2; ++j) {
+      if (!((mw >> j) & 1u)) continue;
+      stage_corrections<R>(Pd.prev_dense, Pd.plane, L, x0 + j, y, z, stage + tid, T);
+      if (j == 0) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) n0[i] += stage[t2 + i * T2];
-    }
-    if (mw & 2u) {
+        for (int i = 0; i < Q; ++i) n0[i] += stage[tid + i * T];
+      } else {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) n1[i] += stage[t2 + 1 + i * T2];
+        for (int i = 0; i < Q; ++i) n1[i] += stage[tid + i * T];
+      }
     }
   }
   R o0[Q], o1[Q];

@@ -178,38 +178,55 @@ class EngineT final : public Engine {
       return o;
     };
     const size_t o_ck = take((size_t)nck * stb);
-    const size_t o_seg = take((size_t)K * stb);
+    const size_t o_pool = take((size_t)K * stb);  // states t0 + 1 .. t0 + K of a segment
     const size_t o_fin = take(stb);
     const size_t o_lam0 = take(lamb), o_lam1 = take(lamb);
+    const size_t o_sp = take(4 * (size_t)plane_ * sizeof(R));
     const size_t o_bar = take(3 * n3 * sizeof(R));
     const size_t o_adj = take(10 * n3 * sizeof(R) + (size_t)cap_ * (3 + 1 + 4) * sizeof(R) + cap_ * sizeof(int) +
                               (size_t)cap_ * 7 * sizeof(R) + N_ * sizeof(R) + 4096);
-    // count (256 B), nodes (cap ints, padded to 256 B), values (4 x cap)
-    const size_t o_sp = take(256 + align_up(cap_ * sizeof(int), 256) + 4 * (size_t)cap_ * sizeof(R));
     const size_t o_z = take(sizeof(double));
     unsigned char* base = nullptr;
     cuda_check(cudaMalloc(&base, off), "adjoint scratch");
-    struct Free {
+    S* const own_pop[2] = {pop_[0], pop_[1]};
+    struct Restore {  // the context's own population buffers and the scratch, also on an error
+      EngineT* e;
+      S* p0;
+      S* p1;
       unsigned char* p;
-      ~Free() { cudaFree(p); }
-    } guard{base};
+      ~Restore() {
+        e->pop_[0] = p0;
+        e->pop_[1] = p1;
+        cudaFree(p);
+      }
+    } guard{this, own_pop[0], own_pop[1], base};
     auto save_state = [&](unsigned char* dst) {
       cuda_check(cudaMemcpyAsync(dst, pop_[cur_], popb, cudaMemcpyDeviceToDevice, s), "save pops");
       cuda_check(cudaMemcpyAsync(dst + popb, bead0, beadb, cudaMemcpyDeviceToDevice, s), "save beads");
     };
-    auto load_state = [&](const unsigned char* src, bool pops) {
-      if (pops) cuda_check(cudaMemcpyAsync(pop_[cur_], src, popb, cudaMemcpyDeviceToDevice, s), "load pops");
-      cuda_check(cudaMemcpyAsync(bead0, src + popb, beadb, cudaMemcpyDeviceToDevice, s), "load beads");
-    };
     auto ck = [&](int i) { return base + o_ck + (size_t)i * stb; };
-    auto seg = [&](int i) { return base + o_seg + (size_t)i * stb; };
-    // 1. forward pass with checkpoints
+    auto pool = [&](int i) { return base + o_pool + (size_t)i * stb; };
+    // a state's bead arrays, at their offsets within the saved span
+    auto at = [&](unsigned char* st, const void* arr) {
+      return st + popb + (size_t)(reinterpret_cast<const unsigned char*>(arr) - bead0);
+    };
+    // 1. forward pass with checkpoints every K steps (deferred force corrections between
+    //    checkpoints, the same arithmetic as complete steps when the storage type is the
+    //    arithmetic type; complete steps otherwise)
     std::vector<double> x0h(n3), xTh(n3);
     get_beads(x0h.data(), nullptr, s);
+    const bool deferred = sizeof(S) == sizeof(R);
     for (int64_t t = 0; t < T; ++t) {
-      if (t % K == 0) save_state(ck((int)(t / K)));
-      step((uint32_t)(k0 + t), s, nullptr, nullptr);
+      if (t % K == 0) {
+        flush(s);
+        save_state(ck((int)(t / K)));
+      }
+      if (deferred)
+        step_deferred((uint32_t)(k0 + t), s, nullptr, nullptr);
+      else
+        step((uint32_t)(k0 + t), s, nullptr, nullptr);
     }
+    flush(s);
     save_state(base + o_fin);
     get_beads(xTh.data(), nullptr, s);
     double obj = 0.0;
@@ -250,12 +267,10 @@ class EngineT final : public Engine {
       A.u_rb = q; q += 4 * (size_t)cap_;
       A.zb_b = q; q += N_;
       A.e_slot = reinterpret_cast<int*>(q);
-      unsigned char* sp = base + o_sp;
-      A.s_count = reinterpret_cast<int*>(sp);
-      A.s_node = reinterpret_cast<int*>(sp + 256);
-      A.s_val = reinterpret_cast<R*>(sp + 256 + align_up(cap_ * sizeof(int), 256));
+      A.sp = reinterpret_cast<R*>(base + o_sp);
       A.zbar = reinterpret_cast<double*>(base + o_z);
     }
+    cuda_check(cudaMemsetAsync(A.sp, 0, 4 * (size_t)plane_ * sizeof(R), s), "sparse adjoint field");
     cuda_check(cudaMemsetAsync(A.zbar, 0, sizeof(double), s), "zbar");
     const ChainK<R> C = chain();
     const size_t ne = 8 * (size_t)N_;
@@ -268,41 +283,68 @@ class EngineT final : public Engine {
     dim3 blk, grd;
     lb_launch_shape(blk, grd, false);  // the adjoint LB kernel: one node per thread
     int cur_lam = 0;
-    // 3. reverse sweep over the segments
+    std::vector<unsigned char*> sl((size_t)K + 1);
+    // 3. reverse sweep over the segments.  The states t0 .. t1 - 1 of a segment: slot 0 is its
+    //    checkpoint; the recomputation steps with the context's population buffers pointed at
+    //    consecutive pool slots (each step reads slot i and writes slot i + 1, no copy of the
+    //    populations) and copies the bead arrays after each step into the next slot.  The
+    //    reverse steps read the bead state of a slot in place.
     for (int sgi = nck - 1; sgi >= 0; --sgi) {
       const int64_t t0 = (int64_t)sgi * K, t1 = t0 + K < T ? t0 + K : T;
-      load_state(ck(sgi), true);
+      sl[0] = ck(sgi);
+      for (int i = 1; i <= K; ++i) sl[i] = pool(i - 1);
+      cuda_check(cudaMemcpyAsync(bead0, sl[0] + popb, beadb, cudaMemcpyDeviceToDevice, s), "load beads");
       for (int64_t t = t0; t < t1; ++t) {
-        save_state(seg((int)(t - t0)));
+        const int i = (int)(t - t0);
+        pop_[cur_] = reinterpret_cast<S*>(sl[i]);
+        pop_[cur_ ^ 1] = reinterpret_cast<S*>(sl[i + 1]);
         step((uint32_t)(k0 + t), s, nullptr, nullptr);
+        if (t + 1 < t1)
+          cuda_check(cudaMemcpyAsync(sl[i + 1] + popb, bead0, beadb, cudaMemcpyDeviceToDevice, s), "save beads");
       }
       for (int64_t t = t1 - 1; t >= t0; --t) {
-        const unsigned char* st = seg((int)(t - t0));
-        load_state(st, false);
+        unsigned char* st = sl[(int)(t - t0)];
         const S* pops = reinterpret_cast<const S*>(st);
-        k_adj_bead<S, R, DEV><<<1, 512, smem, s>>>(pops, lam[cur_lam], P, C, A, (uint32_t)(k0 + t));
+        ChainK<R> Ct = C;
+        Ct.x = reinterpret_cast<R*>(at(st, x_));
+        Ct.xl = reinterpret_cast<R*>(at(st, xl_));
+        Ct.img = reinterpret_cast<int*>(at(st, img_));
+        Ct.v = reinterpret_cast<R*>(at(st, v_));
+        Ct.F = reinterpret_cast<R*>(at(st, F_));
+        Ct.Fc = reinterpret_cast<R*>(at(st, Fc_));
+        k_adj_bead<S, R, DEV><<<1, 512, smem, s>>>(pops, lam[cur_lam], P, Ct, A, (uint32_t)(k0 + t));
         cuda_check(cudaGetLastError(), "adjoint bead");
         if (P.ncalls > 0)
-          k_adj_lb<S, R, DEV, true><<<grd, blk, 0, s>>>(pops, lam[cur_lam], lam[cur_lam ^ 1], P, (uint32_t)(k0 + t));
+          k_adj_lb<S, R, DEV, true><<<grd, blk, 0, s>>>(pops, lam[cur_lam], lam[cur_lam ^ 1], A.sp, P,
+                                                        (uint32_t)(k0 + t));
         else
-          k_adj_lb<S, R, DEV, false><<<grd, blk, 0, s>>>(pops, lam[cur_lam], lam[cur_lam ^ 1], P, (uint32_t)(k0 + t));
+          k_adj_lb<S, R, DEV, false><<<grd, blk, 0, s>>>(pops, lam[cur_lam], lam[cur_lam ^ 1], A.sp, P,
+                                                         (uint32_t)(k0 + t));
         cuda_check(cudaGetLastError(), "adjoint LB");
-        k_adj_sparse_add<R><<<dim3((cap_ + 255) / 256, Q), 256, 0, s>>>(lam[cur_lam ^ 1], P, A.s_node, A.s_val,
-                                                                        A.s_count, cap_);
-        cuda_check(cudaGetLastError(), "adjoint sparse add");
         cur_lam ^= 1;
       }
     }
+    pop_[0] = own_pop[0];
+    pop_[1] = own_pop[1];
+    auto load_state = [&](const unsigned char* src) {
+      cuda_check(cudaMemcpyAsync(pop_[cur_], src, popb, cudaMemcpyDeviceToDevice, s), "load pops");
+      cuda_check(cudaMemcpyAsync(bead0, src + popb, beadb, cudaMemcpyDeviceToDevice, s), "load beads");
+    };
     // 4. the initial force F_0 = F_cons(x_0): xbar += H(x_0) fbar
-    load_state(ck(0), false);
-    k_chain_force_vjp<R><<<1, 512, 6 * n3 / 3 * sizeof(R), s>>>(C, A.fbar, A.xbar);
+    {
+      ChainK<R> C0 = C;
+      C0.x = reinterpret_cast<R*>(at(ck(0), x_));
+      C0.xl = reinterpret_cast<R*>(at(ck(0), xl_));
+      C0.img = reinterpret_cast<int*>(at(ck(0), img_));
+      k_chain_force_vjp<R><<<1, 512, 6 * n3 / 3 * sizeof(R), s>>>(C0, A.fbar, A.xbar);
+    }
     cuda_check(cudaGetLastError(), "initial force adjoint");
     std::vector<R> xbh(n3);
     double zb = 0.0;
     cuda_check(cudaMemcpyAsync(xbh.data(), A.xbar, n3 * sizeof(R), cudaMemcpyDeviceToHost, s), "dl xbar");
     cuda_check(cudaMemcpyAsync(&zb, A.zbar, sizeof(double), cudaMemcpyDeviceToHost, s), "dl zbar");
     // 5. leave the context at the end of the forward run
-    load_state(base + o_fin, true);
+    load_state(base + o_fin);
     cuda_check(cudaStreamSynchronize(s), "adjoint sync");
     *O = obj;
     for (size_t t = 0; t < n3; ++t) gx[t] = (double)xbh[t] - 2.0 * (xTh[t] - x0h[t]);
@@ -647,10 +689,8 @@ class EngineT final : public Engine {
     blk = dim3(bx, by, 1);
     grd = dim3((row + bx - 1) / bx, ((unsigned)L_ + by - 1) / by, (unsigned)L_);
   }
-  // staged corrections of marked nodes: 19 values per node of a tile
-  size_t lb_stage_bytes(const dim3& blk) const {
-    return (size_t)Q * blk.x * blk.y * (pair_nodes() ? 2 : 1) * sizeof(R);
-  }
+  // staged corrections of marked nodes: 19 values per thread of a tile
+  size_t lb_stage_bytes(const dim3& blk) const { return (size_t)Q * blk.x * blk.y * sizeof(R); }
 
   size_t bead_smem() const {
     // phase 5: up to kGroupHashMax entries a node table (4 x H ints, H >= 2 x entries), entry

@@ -8,7 +8,7 @@ populations, which at equilibrium are independent per population with variance m
     var(rho) = mu rho0 (1 - 1/L^3)      var(u_alpha) = kT / (rho0 a^3) (1 - 1/L^3)
 
 (the conserved totals remove one degree of freedom per conserved mode); the coupled beads
-reach <v^2>/3 = kT/m; the collision and the coupling conserve mass and total momentum, so in
+reach <v^2>/3 = kT/m up to the O(h) excess of the discrete coupling; the collision and the coupling conserve mass and total momentum, so in
 FP32 they drift only by rounding.  The moments are formed here from lb_get_populations
 snapshots with the oracle's (pinned) mode matrix.  Statistical bands: three standard errors
 of the mean over the snapshots (taken 500 steps apart), plus O(mu) = 3e-4 for the
@@ -65,11 +65,13 @@ def test_c2_equipartition_and_conservation_fp32(lblib):
     se_u = var_u.std(axis=0, ddof=1) / np.sqrt(n_s)
     print("var(u)/expected - 1:", mu_u / want_u - 1.0)
     assert np.all(np.abs(mu_u / want_u - 1.0) <= 3.0 * se_u / want_u + 3.0 * mu)
-    # beads: 180 samples of 64 beads (velocity correlation time m / zeta_eff ~ 7 steps << 50)
+    # beads: 180 samples of 64 beads (velocity correlation time m / zeta_eff ~ 7 steps << 50);
+    # allowance 4 h for the coupled step's O(h) excess (test_gpu_bead_temperature measures the
+    # slope, 2 to 3.5 per unit step, and the extrapolation to kT/m at h = 0)
     v2 = np.array(v2)
     se_v = v2.std(ddof=1) / np.sqrt(v2.size)
     print(f"bead <v^2>/3 = {v2.mean():.4f} +- {se_v:.4f} (kT/m = {kT / case.m})")
-    assert abs(v2.mean() - kT / case.m) <= 3.0 * se_v
+    assert abs(v2.mean() - kT / case.m) <= 3.0 * se_v + 4.0 * h
     # conservation in FP32: rounding only (about 1e-9 of the mass and of the box momentum at
     # one lattice unit of velocity over 10^4 steps); bounds 1e-7
     scale = L ** 3 * rho0 * a ** 4 / h

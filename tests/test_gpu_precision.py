@@ -106,9 +106,12 @@ def test_c3_precision_study_fp32_bf16_fp16_against_fp64(lblib):
     rounding only, about 1e-9, stated bound 1e-7; 16-bit storage: the random storage rounding
     of ~q |n - w rho0| per population and step, bound 10 q 0.02 sqrt(19 L^3 steps) / L^3 with
     q half an ulp at 1); the fluid velocity variance and the bead temperature against
-    kT/(rho a^3) and kT/m (three standard errors plus 3 mu for the fluid); R_g^2, the bead MSD
-    g1 and the centre-of-mass MSD g3 at lags of 100, 1000 and 5000 steps against the FP64 run
-    (reported, with the spread of the FP64 run as the scale)."""
+    kT/(rho a^3) and kT/m (three standard errors, plus 3 mu for the fluid and the coupled step's
+    O(h) excess, 4 h, for the beads: test_gpu_bead_temperature); R_g^2, the bead MSD
+    g1 and the centre-of-mass MSD g3 at lags of 100, 1000 and 5000 steps against the FP64 run:
+    FP32 within 1e-4 (R_g^2) and 1e-3 (g1, g3), since it follows the FP64 trajectory; BF16 and
+    FP16 within 2 % and 5 %, their trajectories decorrelating from the FP64 one (statistical
+    differences of one chain over 100 time units)."""
     steps = 10000
     runs = {"fp64": _c3_run(lblib, lblib.LB_FP64, steps), "fp32": _c3_run(lblib, lblib.LB_FP32, steps),
             "bf16": _c3_run(lblib, lblib.LB_BF16, steps), "fp16": _c3_run(lblib, lblib.LB_FP16, steps)}
@@ -136,6 +139,15 @@ def test_c3_precision_study_fp32_bf16_fp16_against_fp64(lblib):
             failures.append(f"{name}: drift")
         if not abs(r["varu"].mean() - kT / rho) <= 3 * se_u + 3 * mu:
             failures.append(f"{name}: var u")
-        if not abs(r["v2"].mean() - kT) <= 3 * se_v:
+        if not abs(r["v2"].mean() - kT) <= 3 * se_v + 4 * 0.01:  # O(h) coupling excess, h = 0.01
             failures.append(f"{name}: bead temperature")
+        # chain observables against the FP64 run: FP32 follows the FP64 trajectory (rounding
+        # grows over the 10^4 steps but stays far below the chain's own motion); 16-bit
+        # storage decorrelates the trajectory, so its averages differ by statistics only
+        if name != "fp64":
+            rg_tol, g_tol = (1e-4, 1e-3) if name == "fp32" else (2e-2, 5e-2)
+            if abs(r["rg2"].mean() / ref["rg2"].mean() - 1.0) > rg_tol:
+                failures.append(f"{name}: <R_g^2>")
+            if max(abs(v) for v in g1r + g3r) > g_tol:
+                failures.append(f"{name}: g1/g3")
     assert not failures, failures
