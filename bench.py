@@ -560,7 +560,8 @@ def run_ours(args):
     ke = args.steps
     barrier()
     t0 = time.perf_counter()
-    lb.lb_set_populations(ctx, n0)
+    lb.lb_set_populations(ctx, n0)  # synchronising
+    t1 = time.perf_counter()
     pending = []
     for k in range(ke):
         lb.lb_step(ctx, 1)
@@ -569,9 +570,12 @@ def run_ours(args):
             lb.lb_wait(ctx, pending.pop(0))
     for t in pending:
         lb.lb_wait(ctx, t)
-    lb.lb_get_populations(ctx, nout)
+    t2 = time.perf_counter()
+    lb.lb_get_populations(ctx, nout)  # synchronising
     barrier()
     te = time.perf_counter() - t0
+    e2e_phases = {"upload_ms": (t1 - t0) * 1e3, "steps_ms": (t2 - t1) * 1e3,
+                  "download_ms": (time.perf_counter() - t2) * 1e3}
     lb.lb_destroy(ctx)
     e2e_val, _ = aggregate_throughput(L ** 3 * ke / 1e6, te, ws, dev)
     h2d = n0.nbytes / ke
@@ -607,6 +611,7 @@ def run_ours(args):
         "adjoint_c5": adj,
         "variants": variants,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "phases": e2e_phases,
                 "path": "C ABI, pinned host buffers: set_populations, K x (step + asynchronous bead read-back, each waited for one step later), get_populations"},
         # per step one bead launch (a cluster grid) and one LB launch; lb_step leaves the last
         # step's force correction pending (applied when the fluid is next read, after the

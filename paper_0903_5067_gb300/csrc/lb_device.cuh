@@ -1348,21 +1348,36 @@ __global__ void k_init_rest(S* __restrict__ pop, unsigned long long nnodes, unsi
 }
 
 // one population plane: full FP64 values <-> storage
+// planes p0 .. p0 + gridDim.y - 1 of the stored populations as full FP64 populations:
+// dst[(i - p0) n + t] = n_i(t) (+ w_i rho0 for deviation storage); dst may be page-locked host
+// memory the device addresses directly
 template <class S, class R, bool DEV>
-__global__ void k_plane_from_f64(S* __restrict__ dst, const double* __restrict__ src, unsigned long long n,
-                                 double wrho) {
-  const unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const double v = DEV ? src[t] - wrho : src[t];
-  st<S, R>(dst + t, (R)v);
+__global__ void __launch_bounds__(256) k_planes_to_f64(double* __restrict__ dst, const S* __restrict__ src,
+                                                       unsigned long long n, unsigned long long plane, int p0,
+                                                       double rho0) {
+  const int i = p0 + (int)blockIdx.y;
+  const double wr = DEV ? rho0 * (double)w36(i) / 36.0 : 0.0;
+  const S* s = src + (unsigned long long)i * plane;
+  double* d = dst + (unsigned long long)blockIdx.y * n;
+  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < n;
+       t += (unsigned long long)gridDim.x * blockDim.x)
+  {
+    const double v = (double)ld<S, R>(s + t);
+    d[t] = DEV ? v + wr : v;
+  }
 }
+// the inverse: planes p0 .. p0 + gridDim.y - 1 of the stored populations from FP64 src
 template <class S, class R, bool DEV>
-__global__ void k_plane_to_f64(double* __restrict__ dst, const S* __restrict__ src, unsigned long long n,
-                               double wrho) {
-  const unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const double v = (double)ld<S, R>(src + t);
-  dst[t] = DEV ? v + wrho : v;
+__global__ void __launch_bounds__(256) k_planes_from_f64(S* __restrict__ dst, const double* __restrict__ src,
+                                                         unsigned long long n, unsigned long long plane, int p0,
+                                                         double rho0) {
+  const int i = p0 + (int)blockIdx.y;
+  const double wr = DEV ? rho0 * (double)w36(i) / 36.0 : 0.0;
+  S* d = dst + (unsigned long long)i * plane;
+  const double* s = src + (unsigned long long)blockIdx.y * n;
+  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < n;
+       t += (unsigned long long)gridDim.x * blockDim.x)
+    st<S, R>(d + t, (R)(DEV ? s[t] - wr : s[t]));
 }
 
 // per-block FP64 partial sums of (sum n, Jx, Jy, Jz) of the stored populations

@@ -369,32 +369,50 @@ class EngineT final : public Engine {
   int chain_length() const { return N_; }
   const Config& config() const { return cfg_; }
 
+  // The full FP64 populations to or from the caller's host array.  Page-locked host memory that
+  // the device addresses directly (pinned or registered, the whole array inside one
+  // allocation) is written or read by one conversion kernel over all 19 planes, with no
+  // staging copy; other host memory goes through the second population buffer in chunks of
+  // as many FP64 planes as it holds, one conversion kernel and one copy per chunk.
   void get_populations(double* out, cudaStream_t s) override {
     flush(s);
-    double* stage = reinterpret_cast<double*>(pop_[cur_ ^ 1]);
-    const unsigned nb = (unsigned)((nnodes_ + 255) / 256);
-    for (int i = 0; i < Q; ++i) {
-      const double wr = cfg_.rho * (double)w36(i) / 36.0;
-      k_plane_to_f64<S, R, DEV><<<nb, 256, 0, s>>>(stage, pop_[cur_] + (size_t)i * plane_, nnodes_, wr);
-      cuda_check(cudaGetLastError(), "plane to f64");
-      cuda_check(cudaMemcpyAsync(out + (size_t)i * nnodes_, stage, nnodes_ * sizeof(double),
-                                 cudaMemcpyDeviceToHost, s),
-                 "download plane");
+    double* direct = static_cast<double*>(device_view(out, (size_t)Q * nnodes_ * sizeof(double)));
+    if (direct) {
+      k_planes_to_f64<S, R, DEV><<<conv_grid(Q), 256, 0, s>>>(direct, pop_[cur_], nnodes_, plane_, 0, cfg_.rho);
+      cuda_check(cudaGetLastError(), "planes to f64");
+    } else {
+      double* stage = reinterpret_cast<double*>(pop_[cur_ ^ 1]);
+      const int chunk = stage_planes();
+      for (int p0 = 0; p0 < Q; p0 += chunk) {
+        const int np = p0 + chunk <= Q ? chunk : Q - p0;
+        k_planes_to_f64<S, R, DEV><<<conv_grid(np), 256, 0, s>>>(stage, pop_[cur_], nnodes_, plane_, p0, cfg_.rho);
+        cuda_check(cudaGetLastError(), "planes to f64");
+        cuda_check(cudaMemcpyAsync(out + (size_t)p0 * nnodes_, stage, (size_t)np * nnodes_ * sizeof(double),
+                                   cudaMemcpyDeviceToHost, s),
+                   "download planes");
+      }
     }
     cuda_check(cudaStreamSynchronize(s), "sync download");
   }
 
   void set_populations(const double* in, cudaStream_t s) override {
     flush(s);
-    double* stage = reinterpret_cast<double*>(pop_[cur_ ^ 1]);
-    const unsigned nb = (unsigned)((nnodes_ + 255) / 256);
-    for (int i = 0; i < Q; ++i) {
-      const double wr = cfg_.rho * (double)w36(i) / 36.0;
-      cuda_check(cudaMemcpyAsync(stage, in + (size_t)i * nnodes_, nnodes_ * sizeof(double),
-                                 cudaMemcpyHostToDevice, s),
-                 "upload plane");
-      k_plane_from_f64<S, R, DEV><<<nb, 256, 0, s>>>(pop_[cur_] + (size_t)i * plane_, stage, nnodes_, wr);
-      cuda_check(cudaGetLastError(), "plane from f64");
+    const double* direct =
+        static_cast<const double*>(device_view(in, (size_t)Q * nnodes_ * sizeof(double)));
+    if (direct) {
+      k_planes_from_f64<S, R, DEV><<<conv_grid(Q), 256, 0, s>>>(pop_[cur_], direct, nnodes_, plane_, 0, cfg_.rho);
+      cuda_check(cudaGetLastError(), "planes from f64");
+    } else {
+      double* stage = reinterpret_cast<double*>(pop_[cur_ ^ 1]);
+      const int chunk = stage_planes();
+      for (int p0 = 0; p0 < Q; p0 += chunk) {
+        const int np = p0 + chunk <= Q ? chunk : Q - p0;
+        cuda_check(cudaMemcpyAsync(stage, in + (size_t)p0 * nnodes_, (size_t)np * nnodes_ * sizeof(double),
+                                   cudaMemcpyHostToDevice, s),
+                   "upload planes");
+        k_planes_from_f64<S, R, DEV><<<conv_grid(np), 256, 0, s>>>(pop_[cur_], stage, nnodes_, plane_, p0, cfg_.rho);
+        cuda_check(cudaGetLastError(), "planes from f64");
+      }
     }
     cuda_check(cudaStreamSynchronize(s), "sync upload");
   }
@@ -654,6 +672,34 @@ class EngineT final : public Engine {
   }
 
   size_t nsegs() const { return (size_t)((nnodes_ + 31) >> kSegShift); }
+
+  // FP64 planes the second population buffer holds as a staging area (at least one: a plane
+  // of L^3 doubles fits in 19 planes of any storage type)
+  int stage_planes() const {
+    const size_t fit = (size_t)Q * plane_ * sizeof(S) / ((size_t)nnodes_ * sizeof(double));
+    return fit < 1 ? 1 : (fit > (size_t)Q ? Q : (int)fit);
+  }
+  // conversion grid: np planes, blocks of 256 threads striding over a plane
+  dim3 conv_grid(int np) const {
+    unsigned long long bx = (nnodes_ + 255) / 256;
+    if (bx > 1024) bx = 1024;
+    return dim3((unsigned)bx, (unsigned)np);
+  }
+  // the device's address of a host range [p, p + bytes) in one page-locked allocation it can
+  // address, or null (pageable memory, or a range not inside one such allocation)
+  static void* device_view(const void* p, size_t bytes) {
+    cudaPointerAttributes a0, a1;
+    const unsigned char* last = static_cast<const unsigned char*>(p) + bytes - 1;
+    if (cudaPointerGetAttributes(&a0, p) != cudaSuccess || cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+      cudaGetLastError();  // an unregistered pointer is not an error of the caller's stream
+      return nullptr;
+    }
+    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+      return nullptr;
+    if (static_cast<unsigned char*>(a1.devicePointer) != static_cast<unsigned char*>(a0.devicePointer) + (bytes - 1))
+      return nullptr;
+    return a0.devicePointer;
+  }
 
   // the LB kernel for noise on/off, 32-bit (all 19 planes below 2^32 elements) or 64-bit
   // element offsets, with or without the deferred force corrections (a chain), and with two
