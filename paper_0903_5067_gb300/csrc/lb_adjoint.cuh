@@ -327,20 +327,32 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
   for (int i = tid; i < M; i += nt)
     keys[i] = (i < ne) ? (((unsigned long long)(unsigned)C.e_node[i] << 32) | (unsigned)i) : ~0ull;
   __syncthreads();
-  for (int k = 2; k <= M; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < M; i += nt) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const unsigned long long ka = keys[i], kb = keys[ixj];
-          const bool up = (i & k) == 0;
-          if ((ka > kb) == up) {
-            keys[i] = kb;
-            keys[ixj] = ka;
+  if (ne <= nt) {
+    // few entries: each thread places its key by its rank among all keys (distinct: the entry
+    // index is in the low bits), two barriers instead of the bitonic network's log2(M)^2 / 2
+    const unsigned long long mine = tid < ne ? keys[tid] : 0ull;
+    int rank = 0;
+    if (tid < ne)
+      for (int j = 0; j < ne; ++j) rank += keys[j] < mine;
+    __syncthreads();
+    if (tid < ne) keys[rank] = mine;
+    __syncthreads();
+  } else {
+    for (int k = 2; k <= M; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < M; i += nt) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const unsigned long long ka = keys[i], kb = keys[ixj];
+            const bool up = (i & k) == 0;
+            if ((ka > kb) == up) {
+              keys[i] = kb;
+              keys[ixj] = ka;
+            }
           }
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
   int* slot = reinterpret_cast<int*>(keys + M);
