@@ -207,6 +207,16 @@ int lb_philox4x32_10(const uint32_t* ctr_dev, int64_t n, uint32_t k0, uint32_t k
 int lb_cell_index_f32(const float* x_dev, int64_t n, float a, int L, int32_t* out_dev,
                       void* stream);
 
+/* Test hook: the coupling's cells as the bead kernel of the last step used them (Sec. II B,
+ * last paragraph: the 8 nodes around each bead).  nodes receives the 8 N s corner nodes of
+ * the last step's s MD substeps, entry 8 (s' N + b) + c for substep s', bead b and corner
+ * c = dx + 2 dy + 4 dz (node index x + L (y + L z)); x_stored receives the 3 N stored
+ * coordinates (high part of the compensated position, wrapped into [0, L a), in the
+ * context's arithmetic precision, as doubles) from which the last substep took its cells.
+ * cap >= 8 N s for nodes and >= 3 N for x_stored (either pointer may be NULL).  Needs a chain
+ * (LB_ERR_STATE) and a stepped context; synchronising. */
+int lb_debug_coupling_cells(lb_ctx* ctx, int32_t* nodes, double* x_stored, size_t cap);
+
 /* --- batched replicas ------------------------------------------------------------------
  * R independent boxes advanced in lockstep by one launch per kernel stage (the ensemble of
  * box sizes and chain lengths the paper runs for its finite-size and cost studies, Sec. II E,

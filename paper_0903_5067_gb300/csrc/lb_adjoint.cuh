@@ -127,13 +127,15 @@ __device__ __forceinline__ void scaled_moment_adjoint(const R nb[Q], R ab[Q]) {
 //   n_ps(r) = pull(n*_k) ; n*_{k+1}(r) = collide(n_ps(r))   (corrections handled sparsely)
 //   nbar_ps(r) = J_collide(r)^T lambda_{k+1}(r);  lambda_k,i(r - e_i) = nbar_ps,i(r)   (push)
 // ---------------------------------------------------------------------------------------
-// sp: the bead adjoint's (rho-bar, J-bar) at the forced nodes of the step, dense [4][plane] and
-// zero elsewhere; each node folds its four values into its moment adjoint (the push then adds
-// rho-bar + c_i . J-bar to lambda_k,i(r - e_i)) and sets them back to zero.
+// Launched with programmatic stream serialization after the previous reverse step's bead
+// adjoint: it waits for that grid (which has added its forced-node terms to lam_in) before
+// reading, then releases the bead adjoint of its own step, which runs beside it (see
+// k_adj_bead).
 template <class S, class R, bool DEV, bool NOISE>
 __global__ void __launch_bounds__(256) k_adj_lb(const S* __restrict__ state, const R* __restrict__ lam_in,
-                                                 R* __restrict__ lam_out, R* __restrict__ sp, const FluidK<R> P,
-                                                 const uint32_t step) {
+                                                 R* __restrict__ lam_out, const FluidK<R> P, const uint32_t step) {
+  grid_dependency_wait();
+  allow_dependent_launch();
   const unsigned L = P.L;
   const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -184,18 +186,6 @@ __global__ void __launch_bounds__(256) k_adj_lb(const S* __restrict__ state, con
                    [&](int j, R g) { acc += P.ag[4 + j] * g * ab[4 + j]; });
     mb[0] += acc * R(0.5) / sqrt(rho);
   }
-  {
-    R v[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = sp[(unsigned long long)q * P.plane + node];
-    if (v[0] != R(0) || v[1] != R(0) || v[2] != R(0) || v[3] != R(0)) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        mb[q] += v[q];
-        sp[(unsigned long long)q * P.plane + node] = R(0);
-      }
-    }
-  }
   // nbar_ps,i = sum_k e_k(c_i) mb_k, pushed to r - e_i
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -212,8 +202,11 @@ __global__ void __launch_bounds__(256) k_adj_lb(const S* __restrict__ state, con
 // Chain part of the adjoint of one step, one thread block.
 // In:  bead state of step k (C.x/xl/img/v/F hold it), post-collision populations n*_k
 //      (`state`), lambda(n*_{k+1}) (`lam`), xbar/vbar/fbar of step k+1.
-// Out: xbar/vbar/fbar of step k (in place), zbar (+= d/dzeta), the (rho, J) adjoints at the
-//      forced nodes into A.sp (read and cleared by k_adj_lb of the same step).
+// Out: xbar/vbar/fbar of step k (in place), zbar (+= d/dzeta), and lambda(n*_k) (`lam_out`)
+//      completed: lambda_k,i(r - e_i) += rho-bar(r) + c_i . J-bar(r) at the forced nodes r.
+// Launched with programmatic stream serialization after k_adj_lb of the same step, which writes
+// the rest of lambda(n*_k): everything up to that last addition runs beside it, and the
+// addition waits for it.
 template <class R>
 struct AdjK {
   R *xbar, *vbar, *fbar;  // 3N each, in/out
@@ -227,13 +220,14 @@ struct AdjK {
   R* u_fb;    // 3 x cap: f-bar per unique node
   R* u_rb;    // 4 x cap: forced-node (rho, J) adjoint per unique node
   R* zb_b;    // N: zeta-bar per bead
-  R* sp;       // output: (rho-bar, J-bar) at the forced nodes, dense [4][plane] (zero elsewhere)
+  R* u_sp;     // 4 x cap: (rho-bar, J-bar) summed per unique forced node
+  int* u_node;  // cap: the unique forced nodes
 };
 
 template <class S, class R, bool DEV>
 __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, const R* __restrict__ lam,
-                                                   const FluidK<R> P, const ChainK<R> C, const AdjK<R> A,
-                                                   const uint32_t step) {
+                                                   R* __restrict__ lam_out, const FluidK<R> P, const ChainK<R> C,
+                                                   const AdjK<R> A, const uint32_t step) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = C.N, tid = threadIdx.x, nt = blockDim.x, L = (int)P.L;
   const R h = C.h;
@@ -356,6 +350,7 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
     }
   }
   int* slot = reinterpret_cast<int*>(keys + M);
+  __shared__ int s_nu;  // number of unique forced nodes
   if (tid < 32) {
     int base = 0;
     for (int c0 = 0; c0 < ne; c0 += 32) {
@@ -366,6 +361,7 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
       if (i < ne) slot[i] = lead ? base + __popc(mask & ((1u << tid) - 1u)) : -1;
       base += __popc(mask);
     }
+    if (tid == 0) s_nu = base;
   }
   __syncthreads();
   // per unique node p: forward force density f(p), force-correction adjoint -> fbar(p),
@@ -488,7 +484,8 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
       for (int q = 0; q < 4; ++q) v[q] += A.e_rb[q * C.cap + e];
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) A.sp[(unsigned long long)q * P.plane + (unsigned)node] = v[q];
+    for (int q = 0; q < 4; ++q) A.u_sp[q * C.cap + u] = v[q];
+    A.u_node[u] = node;
   }
   // ---- zeta-bar: fixed-order block sum ----------------------------------------------------
   __syncthreads();
@@ -496,6 +493,20 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
     double acc = 0.0;
     for (int b = 0; b < N; ++b) acc += (double)A.zb_b[b];
     *A.zbar += acc;
+  }
+  // ---- lambda_k,i(r - e_i) += rho-bar(r) + c_i . J-bar(r) at the forced nodes, once the
+  //      adjoint LB kernel of this step has written lambda_k (each (i, r - e_i) target belongs
+  //      to one forced node r, so the additions do not collide) --------------------------
+  grid_dependency_wait();
+  const int nu = s_nu;
+  for (int k = tid; k < Q * nu; k += nt) {
+    const int i = k / nu, u = k - i * nu;
+    const int node = A.u_node[u];
+    const int x = node % L, y = (node / L) % L, z = node / (L * L);
+    const int sx = (x - cx(i) + L) % L, sy = (y - cy(i) + L) % L, sz = (z - cz(i) + L) % L;
+    const R v = A.u_sp[u] + R(cx(i)) * A.u_sp[C.cap + u] + R(cy(i)) * A.u_sp[2 * C.cap + u] +
+                R(cz(i)) * A.u_sp[3 * C.cap + u];
+    lam_out[(unsigned long long)i * P.plane + (unsigned)(sx + L * (sy + L * sz))] += v;
   }
 }
 

@@ -632,6 +632,18 @@ int lb_philox4x32_10(const uint32_t* ctr_dev, int64_t n, uint32_t k0, uint32_t k
   return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ERR_CUDA;
 }
 
+int lb_debug_coupling_cells(lb_ctx* ctx, int32_t* nodes, double* x_stored, size_t cap) {
+  if (!ctx) return fail(LB_ERR_ARG, "invalid argument: !ctx");
+  if (ctx->cfg.N == 0) return fail(LB_ERR_STATE, "no chain");
+  if (!ctx->live) return fail(LB_ERR_STATE, "the context has not stepped");
+  if ((nodes && cap < 8 * (size_t)ctx->cfg.N * ctx->cfg.substeps) || (x_stored && cap < 3 * (size_t)ctx->cfg.N))
+    return fail(LB_ERR_ARG, "buffer too small");
+  return guarded([&] {
+    ctx->eng->debug_coupling_cells(nodes, x_stored, ctx->stream);
+    return (int)LB_OK;
+  });
+}
+
 int lb_cell_index_f32(const float* x_dev, int64_t n, float a, int L, int32_t* out_dev, void* stream) {
   if (n < 0 || L < 1 || !(a > 0) || (n > 0 && (!x_dev || !out_dev))) return fail(LB_ERR_ARG, "invalid argument: n < 0 || L < 1 || !(a > 0) || (n > 0 && (!x_dev || !out_dev))");
   if (n == 0) return LB_OK;

@@ -136,7 +136,11 @@ struct ChainK {
   int nsub;         // MD steps per LB step (h above is the MD step h_LB / nsub)
   R spread;         // 1 / nsub: each MD step's reaction, averaged over the LB step
   R* fc_hist;       // nsub x 3N coupling forces of the MD substeps
-  // bead state (global, 3N each, bead-major)
+  // bead state (global, 3N each, bead-major).  The bead kernel reads the state at the start
+  // of a step from the *_in arrays (normally the same arrays; the adjoint's recomputation
+  // reads one saved state and writes the next) and writes the end state to x .. Fc
+  const R *x_in, *xl_in, *v_in, *F_in;
+  const int* img_in;
   R* x;    // wrapped positions in [0, box): high part
   R* xl;   // low part: position = x + xl + img * box (compensated, ~2x the precision of R)
   int* img;  // periodic image counters
@@ -985,19 +989,25 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
   const int eoff = sub * 8 * N;
   // 1. first half kick and drift: v_half = v + h F/2m, x' = x + h v_half, in compensated
   //    (hi, lo) arithmetic, then wrapped into [0, box) with the image counter
+  const bool first = sub == 0;  // later substeps continue from the written state
+  const R* const vin = first ? C.v_in : C.v;
+  const R* const Fin = first ? C.F_in : C.F;
+  const R* const xin = first ? C.x_in : C.x;
+  const R* const xlin = first ? C.xl_in : C.xl;
+  const int* const imgin = first ? C.img_in : C.img;
   for (int t = tid; t < 3 * N; t += nt) {
-    const R vh = C.v[t] + h * C.F[t] / (R(2) * C.m);
+    const R vh = vin[t] + h * Fin[t] / (R(2) * C.m);
     const R dx = h * vh;
-    const R xh = C.x[t];
+    const R xh = xin[t];
     R hi = xh + dx;
     const R bp = hi - xh;
-    R lo = C.xl[t] + ((xh - (hi - bp)) + (dx - bp));
+    R lo = xlin[t] + ((xh - (hi - bp)) + (dx - bp));
     {
       const R s2 = hi + lo;
       lo = lo - (s2 - hi);
       hi = s2;
     }
-    int im = C.img[t];
+    int im = imgin[t];
     if (hi < R(0)) {
       const R s2 = C.box + hi;
       lo += hi - (s2 - C.box);

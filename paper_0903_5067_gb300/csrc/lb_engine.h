@@ -78,6 +78,8 @@ class Engine {
   // write the current unwrapped bead positions (3N doubles) to device memory
   virtual void record_frame(double* dst, cudaStream_t s) = 0;
   virtual unsigned read_status(cudaStream_t s) = 0;
+  // the last step's corner nodes (8 N s) and stored bead coordinates (3 N, high part), to host
+  virtual void debug_coupling_cells(int* nodes, double* x_stored, cudaStream_t s) = 0;
   // adjoint: objective O = sum_b |x_b(T) - x_b(0)|^2 over T steps from the current state,
   // its gradient with respect to the current bead positions (3N) and zeta, noise fixed,
   // forward checkpoints every K steps; leaves the state at step k0 + T

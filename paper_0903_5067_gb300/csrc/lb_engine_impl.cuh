@@ -137,6 +137,20 @@ class EngineT final : public Engine {
     cur_ ^= 1;
   }
 
+  // One complete step with the bead kernel's state arrays given (the adjoint's recomputation:
+  // read a saved state, write the next one); the context's own bead arrays are not touched.
+  void step_with_chain(uint32_t k, cudaStream_t s, const ChainK<R>& C) {
+    flush(s);
+    const FluidK<R> P = fluid();
+    const S* A = pop_[cur_];
+    S* Bo = pop_[cur_ ^ 1];
+    const PendK<R> Pd = pend(false);
+    launch_bead(A, P, Pd, k, s, true, &C);
+    launch_lb(A, Bo, P, Pd, k, s, nullptr, nullptr);
+    apply(Bo, P, pslot_, s);
+    cur_ ^= 1;
+  }
+
   // apply the pending force correction of the last deferred step
   void flush(cudaStream_t s) override {
     if (!open_) return;
@@ -181,10 +195,10 @@ class EngineT final : public Engine {
     const size_t o_pool = take((size_t)K * stb);  // states t0 + 1 .. t0 + K of a segment
     const size_t o_fin = take(stb);
     const size_t o_lam0 = take(lamb), o_lam1 = take(lamb);
-    const size_t o_sp = take(4 * (size_t)plane_ * sizeof(R));
     const size_t o_bar = take(3 * n3 * sizeof(R));
     const size_t o_adj = take(10 * n3 * sizeof(R) + (size_t)cap_ * (3 + 1 + 4) * sizeof(R) + cap_ * sizeof(int) +
-                              (size_t)cap_ * 7 * sizeof(R) + N_ * sizeof(R) + 4096);
+                              (size_t)cap_ * 7 * sizeof(R) + N_ * sizeof(R) + (size_t)cap_ * 4 * sizeof(R) +
+                              cap_ * sizeof(int) + 4096);
     const size_t o_z = take(sizeof(double));
     unsigned char* base = nullptr;
     cuda_check(cudaMalloc(&base, off), "adjoint scratch");
@@ -266,11 +280,11 @@ class EngineT final : public Engine {
       A.u_fb = q; q += 3 * (size_t)cap_;
       A.u_rb = q; q += 4 * (size_t)cap_;
       A.zb_b = q; q += N_;
+      A.u_sp = q; q += 4 * (size_t)cap_;
       A.e_slot = reinterpret_cast<int*>(q);
-      A.sp = reinterpret_cast<R*>(base + o_sp);
+      A.u_node = A.e_slot + cap_;
       A.zbar = reinterpret_cast<double*>(base + o_z);
     }
-    cuda_check(cudaMemsetAsync(A.sp, 0, 4 * (size_t)plane_ * sizeof(R), s), "sparse adjoint field");
     cuda_check(cudaMemsetAsync(A.zbar, 0, sizeof(double), s), "zbar");
     const ChainK<R> C = chain();
     const size_t ne = 8 * (size_t)N_;
@@ -293,14 +307,26 @@ class EngineT final : public Engine {
       const int64_t t0 = (int64_t)sgi * K, t1 = t0 + K < T ? t0 + K : T;
       sl[0] = ck(sgi);
       for (int i = 1; i <= K; ++i) sl[i] = pool(i - 1);
-      cuda_check(cudaMemcpyAsync(bead0, sl[0] + popb, beadb, cudaMemcpyDeviceToDevice, s), "load beads");
       for (int64_t t = t0; t < t1; ++t) {
         const int i = (int)(t - t0);
         pop_[cur_] = reinterpret_cast<S*>(sl[i]);
         pop_[cur_ ^ 1] = reinterpret_cast<S*>(sl[i + 1]);
-        step((uint32_t)(k0 + t), s, nullptr, nullptr);
-        if (t + 1 < t1)
-          cuda_check(cudaMemcpyAsync(sl[i + 1] + popb, bead0, beadb, cudaMemcpyDeviceToDevice, s), "save beads");
+        ChainK<R> Cs = C;  // read the bead state of slot i, write the next state into slot i + 1
+        Cs.x_in = reinterpret_cast<const R*>(at(sl[i], x_));
+        Cs.xl_in = reinterpret_cast<const R*>(at(sl[i], xl_));
+        Cs.img_in = reinterpret_cast<const int*>(at(sl[i], img_));
+        Cs.v_in = reinterpret_cast<const R*>(at(sl[i], v_));
+        Cs.F_in = reinterpret_cast<const R*>(at(sl[i], F_));
+        if (t + 1 < t1) {  // (the state after the segment's last step is not needed)
+          Cs.x = reinterpret_cast<R*>(at(sl[i + 1], x_));
+          Cs.xl = reinterpret_cast<R*>(at(sl[i + 1], xl_));
+          Cs.img = reinterpret_cast<int*>(at(sl[i + 1], img_));
+          Cs.v = reinterpret_cast<R*>(at(sl[i + 1], v_));
+          Cs.F = reinterpret_cast<R*>(at(sl[i + 1], F_));
+          Cs.Fc = reinterpret_cast<R*>(at(sl[i + 1], Fc_));
+        }
+        Cs.snap = nullptr;
+        step_with_chain((uint32_t)(k0 + t), s, Cs);
       }
       for (int64_t t = t1 - 1; t >= t0; --t) {
         unsigned char* st = sl[(int)(t - t0)];
@@ -312,15 +338,30 @@ class EngineT final : public Engine {
         Ct.v = reinterpret_cast<R*>(at(st, v_));
         Ct.F = reinterpret_cast<R*>(at(st, F_));
         Ct.Fc = reinterpret_cast<R*>(at(st, Fc_));
-        k_adj_bead<S, R, DEV><<<1, 512, smem, s>>>(pops, lam[cur_lam], P, Ct, A, (uint32_t)(k0 + t));
-        cuda_check(cudaGetLastError(), "adjoint bead");
+        const uint32_t kt = (uint32_t)(k0 + t);
+        // the adjoint LB kernel (all nodes) and, beside it, the bead adjoint (one block), which
+        // adds its forced-node terms to lambda once the LB kernel has written it
+        cudaLaunchAttribute at1[1];
+        at1[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at1[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t la;
+        memset(&la, 0, sizeof(la));
+        la.gridDim = grd;
+        la.blockDim = blk;
+        la.stream = s;
+        la.attrs = at1;
+        la.numAttrs = 1;
+        const R* lin = lam[cur_lam];
+        R* lout = lam[cur_lam ^ 1];
         if (P.ncalls > 0)
-          k_adj_lb<S, R, DEV, true><<<grd, blk, 0, s>>>(pops, lam[cur_lam], lam[cur_lam ^ 1], A.sp, P,
-                                                        (uint32_t)(k0 + t));
+          cuda_check(cudaLaunchKernelEx(&la, k_adj_lb<S, R, DEV, true>, pops, lin, lout, P, kt), "adjoint LB");
         else
-          k_adj_lb<S, R, DEV, false><<<grd, blk, 0, s>>>(pops, lam[cur_lam], lam[cur_lam ^ 1], A.sp, P,
-                                                         (uint32_t)(k0 + t));
-        cuda_check(cudaGetLastError(), "adjoint LB");
+          cuda_check(cudaLaunchKernelEx(&la, k_adj_lb<S, R, DEV, false>, pops, lin, lout, P, kt), "adjoint LB");
+        cudaLaunchConfig_t lbd = la;
+        lbd.gridDim = dim3(1);
+        lbd.blockDim = dim3(512);
+        lbd.dynamicSmemBytes = smem;
+        cuda_check(cudaLaunchKernelEx(&lbd, k_adj_bead<S, R, DEV>, pops, lin, lout, P, Ct, A, kt), "adjoint bead");
         cur_lam ^= 1;
       }
     }
@@ -520,6 +561,17 @@ class EngineT final : public Engine {
     cuda_check(cudaGetLastError(), "record frame");
   }
 
+  void debug_coupling_cells(int* nodes, double* x_stored, cudaStream_t s) override {
+    if (N_ == 0) throw LbError(S_STATE, "no chain");
+    if (nodes) cuda_check(cudaMemcpyAsync(nodes, e_node_, (size_t)cap_ * sizeof(int), cudaMemcpyDeviceToHost, s),
+                          "corner nodes");
+    std::vector<R> xs(3 * (size_t)N_);
+    cuda_check(cudaMemcpyAsync(xs.data(), x_, xs.size() * sizeof(R), cudaMemcpyDeviceToHost, s), "stored x");
+    cuda_check(cudaStreamSynchronize(s), "sync debug");
+    if (x_stored)
+      for (size_t t = 0; t < xs.size(); ++t) x_stored[t] = (double)xs[t];
+  }
+
   unsigned read_status(cudaStream_t s) override {
     unsigned st = 0;
     cuda_check(cudaMemcpyAsync(&st, status_, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "status");
@@ -582,7 +634,8 @@ class EngineT final : public Engine {
   // Bead kernel of step k: one cluster of bead_cluster() blocks; with `chained`, launched with
   // programmatic stream serialization (it waits for the previous grid before reading, so only
   // its launch overlaps).
-  void launch_bead(const S* A, const FluidK<R>& P, const PendK<R>& Pd, uint32_t k, cudaStream_t s, bool chained) {
+  void launch_bead(const S* A, const FluidK<R>& P, const PendK<R>& Pd, uint32_t k, cudaStream_t s, bool chained,
+                   const ChainK<R>* Cover = nullptr) {
     if (snap_pending_[k & 1u]) {  // this kernel rewrites the snapshot slot being read back
       cuda_check(cudaStreamWaitEvent(s, copy_ev_[k & 1u], 0), "wait read-back");
       snap_pending_[k & 1u] = false;
@@ -608,7 +661,7 @@ class EngineT final : public Engine {
     }
     lc.attrs = at;
     lc.numAttrs = (unsigned)na;
-    cuda_check(cudaLaunchKernelEx(&lc, k_bead_step<S, R, DEV>, A, P, chain(), Pd, k), "bead kernel");
+    cuda_check(cudaLaunchKernelEx(&lc, k_bead_step<S, R, DEV>, A, P, Cover ? *Cover : chain(), Pd, k), "bead kernel");
     cuda_check(cudaGetLastError(), "bead kernel");
   }
 
@@ -844,6 +897,11 @@ class EngineT final : public Engine {
     C.v = v_;
     C.F = F_;
     C.Fc = Fc_;
+    C.x_in = x_;
+    C.xl_in = xl_;
+    C.img_in = img_;
+    C.v_in = v_;
+    C.F_in = F_;
     C.vh = vh_;
     C.fcons = fcons_;
     C.e_node = e_node_;

@@ -74,6 +74,7 @@ _SIGS = {
     "lb_last_error": (C.c_size_t, [C.c_char_p, C.c_size_t]),
     "lb_philox4x32_10": (C.c_int, [_vp, C.c_int64, C.c_uint32, C.c_uint32, _vp, _vp]),
     "lb_cell_index_f32": (C.c_int, [_vp, C.c_int64, C.c_float, C.c_int, _vp, _vp]),
+    "lb_debug_coupling_cells": (C.c_int, [_vp, C.POINTER(C.c_int32), _dp, C.c_size_t]),
     "lb_fluid_sums_noalloc": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double, _dp, _vp]),
     "lb_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_uint64), C.c_double, C.c_double, C.c_double, C.c_double,
@@ -317,6 +318,17 @@ def lb_destroy(ctx):
 def lb_philox4x32_10(ctr_dev_ptr: int, n: int, k0: int, k1: int, out_dev_ptr: int, stream: int = 0):
     _check(_lib.lb_philox4x32_10(_vp(ctr_dev_ptr), n, k0, k1, _vp(out_dev_ptr), _vp(stream) if stream else None),
            "lb_philox4x32_10")
+
+
+def lb_debug_coupling_cells(ctx, N: int, substeps: int = 1):
+    """Test hook: (corner nodes (substeps, N, 8) int32, stored coordinates (N, 3)) of the last
+    step's coupling, as the bead kernel used them."""
+    cap = max(8 * N * substeps, 3 * N)
+    nodes = np.empty(cap, dtype=np.int32)
+    xs = np.empty(cap, dtype=np.float64)
+    _check(_lib.lb_debug_coupling_cells(ctx, nodes.ctypes.data_as(C.POINTER(C.c_int32)), _dbuf(xs), cap),
+           "lb_debug_coupling_cells")
+    return nodes[:8 * N * substeps].reshape(substeps, N, 8), xs[:3 * N].reshape(N, 3)
 
 
 def lb_cell_index_f32(x_dev_ptr: int, n: int, a: float, L: int, out_dev_ptr: int, stream: int = 0):

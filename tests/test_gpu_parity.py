@@ -426,3 +426,43 @@ def test_populations_through_pinned_and_pageable_host_memory(lblib, prec):
     b.step(4)
     assert np.array_equal(b.populations(), ref)
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_bead_kernel_cells_match_the_oracle_step_by_step(lblib, prec):
+    """The 8 cells around each bead that the running bead kernel coupled to (Sec. II B, last
+    paragraph), read back after every step of the L = 16, N = 8 workload (100 steps):
+    (1) bit-exact against the oracle's cell function applied to the kernel's own stored
+    coordinate (floor(x/a) mod L in the stored precision), and (2) equal to the cells of the
+    oracle's own FP64 trajectory except for coordinates closer to a cell face than the path's
+    parity bar on positions (1e-9 of the box in FP64, 1e-5 in FP32), which are counted."""
+    p = lblib.LB_FP64 if prec == "fp64" else lblib.LB_FP32
+    dtype = np.float64 if prec == "fp64" else np.float32
+    band = (1e-9 if prec == "fp64" else 1e-5) * 16
+    case = Case(L=16, N=8, steps=0, seed=1)
+    fp, cp = case.fluid(), case.chain()
+    L, a = case.L, case.a
+    st = o.init_state(fp, cp, case.x0())
+    sim = gpu_sim(lblib, case, p)
+    offs = np.array([[c & 1, (c >> 1) & 1, (c >> 2) & 1] for c in range(8)])
+
+    def corners(cells):  # (N, 3) cells -> (N, 8) node indices in the kernel's corner order
+        q = (cells[:, None, :] + offs[None]) % L
+        return q[..., 0] + L * (q[..., 1] + L * q[..., 2])
+
+    near = compared = 0
+    for _ in range(100):
+        sim.step(1)
+        st = o.step(st, fp, cp)
+        nodes, xs = lblib.lb_debug_coupling_cells(sim.ctx, case.N)
+        nodes = nodes[0]
+        assert np.array_equal(nodes, corners(o.cell_index(xs.astype(dtype), dtype(a), L)))
+        s = st.X / a
+        frac = s - np.floor(s)
+        ok = np.all(np.minimum(frac, 1.0 - frac) * a > band, axis=1)
+        near += int((~ok).sum())
+        compared += int(ok.sum())
+        assert np.array_equal(nodes[ok], corners(o.cell_index(st.X, a, L))[ok])
+    sim.close()
+    print(f"{prec}: {compared} bead-steps compared against the oracle trajectory, {near} within the band")
+    assert compared >= 0.95 * 100 * case.N
