@@ -139,8 +139,9 @@ class EngineT final : public Engine {
 
   // One complete step with the bead kernel's state arrays given (the adjoint's recomputation:
   // read a saved state, write the next one); the context's own bead arrays are not touched.
-  void step_with_chain(uint32_t k, cudaStream_t s, const ChainK<R>& C, const FluidK<R>& P) {
+  void step_with_chain(uint32_t k, cudaStream_t s, const ChainK<R>& C) {
     flush(s);
+    const FluidK<R> P = fluid();
     const S* A = pop_[cur_];
     S* Bo = pop_[cur_ ^ 1];
     const PendK<R> Pd = pend(false);
@@ -191,7 +192,7 @@ class EngineT final : public Engine {
       return o;
     };
     const size_t o_ck = take((size_t)nck * stb);
-    const size_t o_pool = take((size_t)(K + 1) * stb);  // states t0 .. t0 + K of a segment
+    const size_t o_pool = take((size_t)K * stb);  // states t0 + 1 .. t0 + K of a segment
     const size_t o_fin = take(stb);
     const size_t o_lam0 = take(lamb), o_lam1 = take(lamb);
     const size_t o_bar = take(3 * n3 * sizeof(R));
@@ -199,29 +200,20 @@ class EngineT final : public Engine {
                               (size_t)cap_ * 7 * sizeof(R) + N_ * sizeof(R) + (size_t)cap_ * 4 * sizeof(R) +
                               cap_ * sizeof(int) + 4096);
     const size_t o_z = take(sizeof(double));
-    const size_t o_dstep = take(sizeof(uint32_t));
     unsigned char* base = nullptr;
     cuda_check(cudaMalloc(&base, off), "adjoint scratch");
     S* const own_pop[2] = {pop_[0], pop_[1]};
-    struct Restore {  // the context's own population buffers, the scratch and the segment
-      EngineT* e;     // graphs, also on an error
+    struct Restore {  // the context's own population buffers and the scratch, also on an error
+      EngineT* e;
       S* p0;
       S* p1;
       unsigned char* p;
-      cudaGraphExec_t g[2];
-      cudaStream_t cs;
       ~Restore() {
         e->pop_[0] = p0;
         e->pop_[1] = p1;
-        for (int j = 0; j < 2; ++j)
-          if (g[j]) cudaGraphExecDestroy(g[j]);
-        if (cs) {
-          cudaStreamSynchronize(cs);
-          cudaStreamDestroy(cs);
-        }
         cudaFree(p);
       }
-    } guard{this, own_pop[0], own_pop[1], base, {nullptr, nullptr}, nullptr};
+    } guard{this, own_pop[0], own_pop[1], base};
     auto save_state = [&](unsigned char* dst) {
       cuda_check(cudaMemcpyAsync(dst, pop_[cur_], popb, cudaMemcpyDeviceToDevice, s), "save pops");
       cuda_check(cudaMemcpyAsync(dst + popb, bead0, beadb, cudaMemcpyDeviceToDevice, s), "save beads");
@@ -306,18 +298,15 @@ class EngineT final : public Engine {
     lb_launch_shape(blk, grd, false);  // the adjoint LB kernel: one node per thread
     int cur_lam = 0;
     std::vector<unsigned char*> sl((size_t)K + 1);
-    for (int i = 0; i <= K; ++i) sl[i] = pool(i);
-    uint32_t* d_step = reinterpret_cast<uint32_t*>(base + o_dstep);
-    FluidK<R> Prel = P;  // kernels of the segment graphs: step = *d_step + argument
-    Prel.d_step = d_step;
-    // 3. reverse sweep over the segments.  The states t0 .. t1 - 1 of a segment sit in pool
-    //    slots 0 .. t1 - t0 - 1: slot 0 a copy of the segment's checkpoint, the others written
-    //    by the recomputation, whose steps read the populations and bead state of slot i and
-    //    write those of slot i + 1 (the context's population buffers pointed at the slots).
-    //    The reverse steps read a slot's state in place.  A full segment (K steps) is the same
-    //    sequence of launches at other step numbers: it is captured once as a CUDA graph whose
-    //    kernels take their step from a device counter, and replayed.
-    auto segment = [&](int64_t t0, int64_t t1, cudaStream_t st, const FluidK<R>& Pk, bool relative) {
+    // 3. reverse sweep over the segments.  The states t0 .. t1 - 1 of a segment: slot 0 is its
+    //    checkpoint; the recomputation steps with the context's population buffers pointed at
+    //    consecutive pool slots (each step reads slot i and writes slot i + 1, no copy of the
+    //    populations) and copies the bead arrays after each step into the next slot.  The
+    //    reverse steps read the bead state of a slot in place.
+    for (int sgi = nck - 1; sgi >= 0; --sgi) {
+      const int64_t t0 = (int64_t)sgi * K, t1 = t0 + K < T ? t0 + K : T;
+      sl[0] = ck(sgi);
+      for (int i = 1; i <= K; ++i) sl[i] = pool(i - 1);
       for (int64_t t = t0; t < t1; ++t) {
         const int i = (int)(t - t0);
         pop_[cur_] = reinterpret_cast<S*>(sl[i]);
@@ -328,26 +317,28 @@ class EngineT final : public Engine {
         Cs.img_in = reinterpret_cast<const int*>(at(sl[i], img_));
         Cs.v_in = reinterpret_cast<const R*>(at(sl[i], v_));
         Cs.F_in = reinterpret_cast<const R*>(at(sl[i], F_));
-        Cs.x = reinterpret_cast<R*>(at(sl[i + 1], x_));
-        Cs.xl = reinterpret_cast<R*>(at(sl[i + 1], xl_));
-        Cs.img = reinterpret_cast<int*>(at(sl[i + 1], img_));
-        Cs.v = reinterpret_cast<R*>(at(sl[i + 1], v_));
-        Cs.F = reinterpret_cast<R*>(at(sl[i + 1], F_));
-        Cs.Fc = reinterpret_cast<R*>(at(sl[i + 1], Fc_));
+        if (t + 1 < t1) {  // (the state after the segment's last step is not needed)
+          Cs.x = reinterpret_cast<R*>(at(sl[i + 1], x_));
+          Cs.xl = reinterpret_cast<R*>(at(sl[i + 1], xl_));
+          Cs.img = reinterpret_cast<int*>(at(sl[i + 1], img_));
+          Cs.v = reinterpret_cast<R*>(at(sl[i + 1], v_));
+          Cs.F = reinterpret_cast<R*>(at(sl[i + 1], F_));
+          Cs.Fc = reinterpret_cast<R*>(at(sl[i + 1], Fc_));
+        }
         Cs.snap = nullptr;
-        step_with_chain(relative ? (uint32_t)(t - t0) : (uint32_t)(k0 + t), st, Cs, Pk);
+        step_with_chain((uint32_t)(k0 + t), s, Cs);
       }
       for (int64_t t = t1 - 1; t >= t0; --t) {
-        unsigned char* stt = sl[(int)(t - t0)];
-        const S* pops = reinterpret_cast<const S*>(stt);
+        unsigned char* st = sl[(int)(t - t0)];
+        const S* pops = reinterpret_cast<const S*>(st);
         ChainK<R> Ct = C;
-        Ct.x = reinterpret_cast<R*>(at(stt, x_));
-        Ct.xl = reinterpret_cast<R*>(at(stt, xl_));
-        Ct.img = reinterpret_cast<int*>(at(stt, img_));
-        Ct.v = reinterpret_cast<R*>(at(stt, v_));
-        Ct.F = reinterpret_cast<R*>(at(stt, F_));
-        Ct.Fc = reinterpret_cast<R*>(at(stt, Fc_));
-        const uint32_t kt = relative ? (uint32_t)(t - t0) : (uint32_t)(k0 + t);
+        Ct.x = reinterpret_cast<R*>(at(st, x_));
+        Ct.xl = reinterpret_cast<R*>(at(st, xl_));
+        Ct.img = reinterpret_cast<int*>(at(st, img_));
+        Ct.v = reinterpret_cast<R*>(at(st, v_));
+        Ct.F = reinterpret_cast<R*>(at(st, F_));
+        Ct.Fc = reinterpret_cast<R*>(at(st, Fc_));
+        const uint32_t kt = (uint32_t)(k0 + t);
         // the adjoint LB kernel (all nodes) and, beside it, the bead adjoint (one block), which
         // adds its forced-node terms to lambda once the LB kernel has written it
         cudaLaunchAttribute at1[1];
@@ -357,46 +348,22 @@ class EngineT final : public Engine {
         memset(&la, 0, sizeof(la));
         la.gridDim = grd;
         la.blockDim = blk;
-        la.stream = st;
+        la.stream = s;
         la.attrs = at1;
         la.numAttrs = 1;
         const R* lin = lam[cur_lam];
         R* lout = lam[cur_lam ^ 1];
-        if (Pk.ncalls > 0)
-          cuda_check(cudaLaunchKernelEx(&la, k_adj_lb<S, R, DEV, true>, pops, lin, lout, Pk, kt), "adjoint LB");
+        if (P.ncalls > 0)
+          cuda_check(cudaLaunchKernelEx(&la, k_adj_lb<S, R, DEV, true>, pops, lin, lout, P, kt), "adjoint LB");
         else
-          cuda_check(cudaLaunchKernelEx(&la, k_adj_lb<S, R, DEV, false>, pops, lin, lout, Pk, kt), "adjoint LB");
+          cuda_check(cudaLaunchKernelEx(&la, k_adj_lb<S, R, DEV, false>, pops, lin, lout, P, kt), "adjoint LB");
         cudaLaunchConfig_t lbd = la;
         lbd.gridDim = dim3(1);
         lbd.blockDim = dim3(512);
         lbd.dynamicSmemBytes = smem;
-        cuda_check(cudaLaunchKernelEx(&lbd, k_adj_bead<S, R, DEV>, pops, lin, lout, Pk, Ct, A, kt), "adjoint bead");
+        cuda_check(cudaLaunchKernelEx(&lbd, k_adj_bead<S, R, DEV>, pops, lin, lout, P, Ct, A, kt), "adjoint bead");
         cur_lam ^= 1;
       }
-    };
-    for (int sgi = nck - 1; sgi >= 0; --sgi) {
-      const int64_t t0 = (int64_t)sgi * K, t1 = t0 + K < T ? t0 + K : T;
-      cuda_check(cudaMemcpyAsync(sl[0], ck(sgi), stb, cudaMemcpyDeviceToDevice, s), "segment checkpoint");
-      if (t1 - t0 < K) {  // the partial last segment: direct launches
-        segment(t0, t1, s, P, false);
-        continue;
-      }
-      k_store_value<uint32_t><<<1, 1, 0, s>>>(d_step, (uint32_t)(k0 + t0));
-      cuda_check(cudaGetLastError(), "step counter");
-      const int par = cur_lam;
-      if (!guard.g[par]) {
-        if (!guard.cs) cuda_check(cudaStreamCreateWithFlags(&guard.cs, cudaStreamNonBlocking), "capture stream");
-        cudaGraph_t g = nullptr;
-        cuda_check(cudaStreamBeginCapture(guard.cs, cudaStreamCaptureModeThreadLocal), "begin capture");
-        segment(t0, t1, guard.cs, Prel, true);
-        cuda_check(cudaStreamEndCapture(guard.cs, &g), "end capture");
-        const cudaError_t ie = cudaGraphInstantiate(&guard.g[par], g, 0);
-        cudaGraphDestroy(g);
-        cuda_check(ie, "instantiate segment graph");
-      } else {
-        cur_lam ^= (K & 1);  // what the captured sequence leaves
-      }
-      cuda_check(cudaGraphLaunch(guard.g[par], s), "segment graph");
     }
     pop_[0] = own_pop[0];
     pop_[1] = own_pop[1];
