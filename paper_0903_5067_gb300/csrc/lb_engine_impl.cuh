@@ -192,34 +192,51 @@ class EngineT final : public Engine {
       return o;
     };
     const size_t o_ck = take((size_t)nck * stb);
-    const size_t o_pool = take((size_t)K * stb);  // states t0 + 1 .. t0 + K of a segment
+    // two pools of the states t0 + 1 .. t0 + K of a segment: the recomputation of one segment
+    // fills one pool while the reverse sweep of the segment after it reads the other
+    const size_t o_pool = take(2 * (size_t)K * stb);
     const size_t o_fin = take(stb);
     const size_t o_lam0 = take(lamb), o_lam1 = take(lamb);
     const size_t o_bar = take(3 * n3 * sizeof(R));
+    // bead adjoint scratch, and its own corner entries (node, weight, rho and J): the
+    // recomputation running beside it uses the context's
     const size_t o_adj = take(10 * n3 * sizeof(R) + (size_t)cap_ * (3 + 1 + 4) * sizeof(R) + cap_ * sizeof(int) +
                               (size_t)cap_ * 7 * sizeof(R) + N_ * sizeof(R) + (size_t)cap_ * 4 * sizeof(R) +
-                              cap_ * sizeof(int) + 4096);
+                              cap_ * sizeof(int) + (size_t)cap_ * 5 * sizeof(R) + cap_ * sizeof(int) + 4096);
     const size_t o_z = take(sizeof(double));
     unsigned char* base = nullptr;
     cuda_check(cudaMalloc(&base, off), "adjoint scratch");
     S* const own_pop[2] = {pop_[0], pop_[1]};
-    struct Restore {  // the context's own population buffers and the scratch, also on an error
-      EngineT* e;
+    struct Restore {  // the context's own population buffers, the scratch, the second stream
+      EngineT* e;     // and the events, also on an error
       S* p0;
       S* p1;
       unsigned char* p;
+      cudaStream_t s2;
+      std::vector<cudaEvent_t> ev;
       ~Restore() {
         e->pop_[0] = p0;
         e->pop_[1] = p1;
+        if (s2) {
+          cudaStreamSynchronize(s2);
+          cudaStreamDestroy(s2);
+        }
+        for (cudaEvent_t x : ev) cudaEventDestroy(x);
         cudaFree(p);
       }
-    } guard{this, own_pop[0], own_pop[1], base};
+    } guard{this, own_pop[0], own_pop[1], base, nullptr, {}};
+    auto new_event = [&]() {
+      cudaEvent_t x = nullptr;
+      cuda_check(cudaEventCreateWithFlags(&x, cudaEventDisableTiming), "adjoint event");
+      guard.ev.push_back(x);
+      return x;
+    };
     auto save_state = [&](unsigned char* dst) {
       cuda_check(cudaMemcpyAsync(dst, pop_[cur_], popb, cudaMemcpyDeviceToDevice, s), "save pops");
       cuda_check(cudaMemcpyAsync(dst + popb, bead0, beadb, cudaMemcpyDeviceToDevice, s), "save beads");
     };
     auto ck = [&](int i) { return base + o_ck + (size_t)i * stb; };
-    auto pool = [&](int i) { return base + o_pool + (size_t)i * stb; };
+    auto pool = [&](int pid, int i) { return base + o_pool + ((size_t)pid * K + i) * stb; };
     // a state's bead arrays, at their offsets within the saved span
     auto at = [&](unsigned char* st, const void* arr) {
       return st + popb + (size_t)(reinterpret_cast<const unsigned char*>(arr) - bead0);
@@ -256,6 +273,9 @@ class EngineT final : public Engine {
     cuda_check(cudaMemsetAsync(lam[1], 0, lamb, s), "lambda");
     AdjK<R> A;
     memset(&A, 0, sizeof(A));
+    R* rev_e_w = nullptr;
+    R* rev_e_mom = nullptr;
+    int* rev_e_node = nullptr;
     R* bars = reinterpret_cast<R*>(base + o_bar);
     A.xbar = bars;
     A.vbar = bars + n3;
@@ -281,8 +301,11 @@ class EngineT final : public Engine {
       A.u_rb = q; q += 4 * (size_t)cap_;
       A.zb_b = q; q += N_;
       A.u_sp = q; q += 4 * (size_t)cap_;
+      rev_e_w = q; q += cap_;
+      rev_e_mom = q; q += 4 * (size_t)cap_;
       A.e_slot = reinterpret_cast<int*>(q);
       A.u_node = A.e_slot + cap_;
+      rev_e_node = A.u_node + cap_;
       A.zbar = reinterpret_cast<double*>(base + o_z);
     }
     cuda_check(cudaMemsetAsync(A.zbar, 0, sizeof(double), s), "zbar");
@@ -297,47 +320,52 @@ class EngineT final : public Engine {
     dim3 blk, grd;
     lb_launch_shape(blk, grd, false);  // the adjoint LB kernel: one node per thread
     int cur_lam = 0;
-    std::vector<unsigned char*> sl((size_t)K + 1);
     // 3. reverse sweep over the segments.  The states t0 .. t1 - 1 of a segment: slot 0 is its
-    //    checkpoint; the recomputation steps with the context's population buffers pointed at
-    //    consecutive pool slots (each step reads slot i and writes slot i + 1, no copy of the
-    //    populations) and copies the bead arrays after each step into the next slot.  The
-    //    reverse steps read the bead state of a slot in place.
-    for (int sgi = nck - 1; sgi >= 0; --sgi) {
+    //    checkpoint, slots 1 .. are written by the recomputation, whose steps read the
+    //    populations and bead state of slot i and write those of slot i + 1 (the context's
+    //    population buffers pointed at the slots; no copies).  The reverse steps read a slot's
+    //    state in place.  The recomputation of segment k - 1 needs only its checkpoint, so it
+    //    runs on a second stream beside the reverse sweep of segment k, in the other pool.
+    auto slot = [&](int sgi, int pid, int i) { return i == 0 ? ck(sgi) : pool(pid, i - 1); };
+    auto recompute = [&](int sgi, int pid, cudaStream_t st) {
       const int64_t t0 = (int64_t)sgi * K, t1 = t0 + K < T ? t0 + K : T;
-      sl[0] = ck(sgi);
-      for (int i = 1; i <= K; ++i) sl[i] = pool(i - 1);
       for (int64_t t = t0; t < t1; ++t) {
         const int i = (int)(t - t0);
-        pop_[cur_] = reinterpret_cast<S*>(sl[i]);
-        pop_[cur_ ^ 1] = reinterpret_cast<S*>(sl[i + 1]);
+        unsigned char* a = slot(sgi, pid, i);
+        unsigned char* b = slot(sgi, pid, i + 1);
+        pop_[cur_] = reinterpret_cast<S*>(a);
+        pop_[cur_ ^ 1] = reinterpret_cast<S*>(b);
         ChainK<R> Cs = C;  // read the bead state of slot i, write the next state into slot i + 1
-        Cs.x_in = reinterpret_cast<const R*>(at(sl[i], x_));
-        Cs.xl_in = reinterpret_cast<const R*>(at(sl[i], xl_));
-        Cs.img_in = reinterpret_cast<const int*>(at(sl[i], img_));
-        Cs.v_in = reinterpret_cast<const R*>(at(sl[i], v_));
-        Cs.F_in = reinterpret_cast<const R*>(at(sl[i], F_));
-        if (t + 1 < t1) {  // (the state after the segment's last step is not needed)
-          Cs.x = reinterpret_cast<R*>(at(sl[i + 1], x_));
-          Cs.xl = reinterpret_cast<R*>(at(sl[i + 1], xl_));
-          Cs.img = reinterpret_cast<int*>(at(sl[i + 1], img_));
-          Cs.v = reinterpret_cast<R*>(at(sl[i + 1], v_));
-          Cs.F = reinterpret_cast<R*>(at(sl[i + 1], F_));
-          Cs.Fc = reinterpret_cast<R*>(at(sl[i + 1], Fc_));
-        }
+        Cs.x_in = reinterpret_cast<const R*>(at(a, x_));
+        Cs.xl_in = reinterpret_cast<const R*>(at(a, xl_));
+        Cs.img_in = reinterpret_cast<const int*>(at(a, img_));
+        Cs.v_in = reinterpret_cast<const R*>(at(a, v_));
+        Cs.F_in = reinterpret_cast<const R*>(at(a, F_));
+        Cs.x = reinterpret_cast<R*>(at(b, x_));
+        Cs.xl = reinterpret_cast<R*>(at(b, xl_));
+        Cs.img = reinterpret_cast<int*>(at(b, img_));
+        Cs.v = reinterpret_cast<R*>(at(b, v_));
+        Cs.F = reinterpret_cast<R*>(at(b, F_));
+        Cs.Fc = reinterpret_cast<R*>(at(b, Fc_));
         Cs.snap = nullptr;
-        step_with_chain((uint32_t)(k0 + t), s, Cs);
+        step_with_chain((uint32_t)(k0 + t), st, Cs);
       }
+    };
+    auto reverse = [&](int sgi, int pid, cudaStream_t st) {
+      const int64_t t0 = (int64_t)sgi * K, t1 = t0 + K < T ? t0 + K : T;
       for (int64_t t = t1 - 1; t >= t0; --t) {
-        unsigned char* st = sl[(int)(t - t0)];
-        const S* pops = reinterpret_cast<const S*>(st);
+        unsigned char* stt = slot(sgi, pid, (int)(t - t0));
+        const S* pops = reinterpret_cast<const S*>(stt);
         ChainK<R> Ct = C;
-        Ct.x = reinterpret_cast<R*>(at(st, x_));
-        Ct.xl = reinterpret_cast<R*>(at(st, xl_));
-        Ct.img = reinterpret_cast<int*>(at(st, img_));
-        Ct.v = reinterpret_cast<R*>(at(st, v_));
-        Ct.F = reinterpret_cast<R*>(at(st, F_));
-        Ct.Fc = reinterpret_cast<R*>(at(st, Fc_));
+        Ct.x = reinterpret_cast<R*>(at(stt, x_));
+        Ct.xl = reinterpret_cast<R*>(at(stt, xl_));
+        Ct.img = reinterpret_cast<int*>(at(stt, img_));
+        Ct.v = reinterpret_cast<R*>(at(stt, v_));
+        Ct.F = reinterpret_cast<R*>(at(stt, F_));
+        Ct.Fc = reinterpret_cast<R*>(at(stt, Fc_));
+        Ct.e_node = rev_e_node;
+        Ct.e_w = rev_e_w;
+        Ct.e_mom = rev_e_mom;
         const uint32_t kt = (uint32_t)(k0 + t);
         // the adjoint LB kernel (all nodes) and, beside it, the bead adjoint (one block), which
         // adds its forced-node terms to lambda once the LB kernel has written it
@@ -348,7 +376,7 @@ class EngineT final : public Engine {
         memset(&la, 0, sizeof(la));
         la.gridDim = grd;
         la.blockDim = blk;
-        la.stream = s;
+        la.stream = st;
         la.attrs = at1;
         la.numAttrs = 1;
         const R* lin = lam[cur_lam];
@@ -364,6 +392,29 @@ class EngineT final : public Engine {
         cuda_check(cudaLaunchKernelEx(&lbd, k_adj_bead<S, R, DEV>, pops, lin, lout, P, Ct, A, kt), "adjoint bead");
         cur_lam ^= 1;
       }
+    };
+    cuda_check(cudaStreamCreateWithFlags(&guard.s2, cudaStreamNonBlocking), "adjoint stream");
+    {
+      cudaEvent_t fwd = new_event();  // the forward pass and its checkpoints are complete
+      cuda_check(cudaEventRecord(fwd, s), "event");
+      cuda_check(cudaStreamWaitEvent(guard.s2, fwd, 0), "wait");
+    }
+    std::vector<cudaEvent_t> rec_done(nck), rev_done(nck);
+    recompute(nck - 1, 0, guard.s2);
+    rec_done[nck - 1] = new_event();
+    cuda_check(cudaEventRecord(rec_done[nck - 1], guard.s2), "event");
+    for (int sgi = nck - 1; sgi >= 0; --sgi) {
+      const int pid = (nck - 1 - sgi) & 1;
+      if (sgi >= 1) {  // the next segment's recomputation, into the pool the last reverse sweep read
+        if (sgi + 1 <= nck - 1) cuda_check(cudaStreamWaitEvent(guard.s2, rev_done[sgi + 1], 0), "wait");
+        recompute(sgi - 1, pid ^ 1, guard.s2);
+        rec_done[sgi - 1] = new_event();
+        cuda_check(cudaEventRecord(rec_done[sgi - 1], guard.s2), "event");
+      }
+      cuda_check(cudaStreamWaitEvent(s, rec_done[sgi], 0), "wait");
+      reverse(sgi, pid, s);
+      rev_done[sgi] = new_event();
+      cuda_check(cudaEventRecord(rev_done[sgi], s), "event");
     }
     pop_[0] = own_pop[0];
     pop_[1] = own_pop[1];
