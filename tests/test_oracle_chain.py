@@ -309,3 +309,27 @@ def _re2_not_squared(X):  # planted: |r_N - r_1| instead of its square
 def test_planted_size_observable_mistakes_are_caught(rg2, re2):
     """Each planted normalisation, centre or index mistake fails at least one closed form."""
     assert _size_pin_failures(rg2, re2)
+
+
+def test_mass_and_momentum_observables_match_closed_forms():
+    """total_mass, fluid_momentum and total_momentum against their definitions on states with a
+    closed form (Sec. II B: rho = sum_i n_i and j = sum_i n_i c_i per node, c_i = e_i a/h; the
+    box holds L^3 nodes of volume a^3 each): a fluid at rest has mass rho0 L^3 a^3 and no
+    momentum; the equilibrium populations of a uniform velocity u (Eq. 4) carry rho0 u L^3 a^3;
+    beads add m sum v + (dt/2) sum F_c (dt the MD step)."""
+    fp = o.FluidParams(L=5, rho=0.864, a=0.7, h=0.02)
+    L, a, h = fp.L, fp.a, fp.h
+    st = o.init_state(fp, None)
+    assert o.total_mass(st, fp) == pytest.approx(fp.rho * L ** 3 * a ** 3, rel=1e-14)
+    assert np.allclose(o.fluid_momentum(st, fp), 0.0, atol=1e-14)
+    u = np.array([0.013, -0.021, 0.007])  # physical velocity
+    U = u * h / a  # lattice velocity
+    rho = np.full((L, L, L), fp.rho)
+    st.n = o.n_eq(rho, np.broadcast_to(U[:, None, None, None], (3, L, L, L)))
+    assert o.total_mass(st, fp) == pytest.approx(fp.rho * L ** 3 * a ** 3, rel=1e-13)
+    assert np.allclose(o.fluid_momentum(st, fp), fp.rho * u * L ** 3 * a ** 3, rtol=1e-12, atol=0)
+    cp = o.ChainParams(N=3, m=1.7, substeps=2)
+    st.V = np.array([[0.1, 0.2, -0.3], [0.0, 0.5, 0.1], [-0.2, 0.1, 0.4]])
+    st.Fc = np.array([[1.0, -2.0, 0.5], [0.3, 0.1, -0.2], [-0.4, 0.6, 0.9]])
+    want = fp.rho * u * L ** 3 * a ** 3 + cp.m * st.V.sum(axis=0) + 0.5 * (h / 2) * st.Fc.sum(axis=0)
+    assert np.allclose(o.total_momentum(st, fp, cp), want, rtol=1e-12, atol=0)
