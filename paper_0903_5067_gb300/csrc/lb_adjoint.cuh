@@ -209,27 +209,66 @@ __global__ void __launch_bounds__(256) k_adj_lb(const S* __restrict__ state, con
 // addition waits for it.
 template <class R>
 struct AdjK {
-  R *xbar, *vbar, *fbar;  // 3N each, in/out
-  double* zbar;           // accumulated d objective / d zeta
-  // scratch (global)
-  R *xp, *xpl, *vh, *ub, *g, *fc, *fct, *vhb, *xpb, *fcb;  // 3N each
-  R* e_gw;    // 3 x 8N weight gradients (per unit length)
-  R* e_wb;    // 8N
-  R* e_rb;    // 4 x 8N (rho-bar, J-bar) per entry
+  R *xbar, *vbar, *fbar;  // 3N each, in/out across the reverse steps (global)
+  double* zbar;           // accumulated d objective / d zeta (global)
+  // scratch of one reverse step: carved from the kernel's dynamic shared memory at byte
+  // offset smem_off when smem_scratch is set (small chains), else global memory
+  R *vh, *ub, *g, *fc, *fct, *vhb, *xpb;  // 3N each
+  R* e_gw;      // 3 x 8N weight gradients (per unit length)
+  R* e_rb;      // 4 x 8N (rho-bar, J-bar) per entry
+  R* u_fb;      // 3 x cap: f-bar per unique node
+  R* u_rb;      // 4 x cap: forced-node (rho, J) adjoint per unique node
+  R* u_sp;      // 4 x cap: (rho-bar, J-bar) summed per unique forced node
+  R* zb_b;      // N: zeta-bar per bead
+  R* ce_w;      // 8N: trilinear weight of each corner entry
+  R* ce_mom;    // 4 x 8N: post-stream rho and J at each entry's node
   int* e_slot;  // 8N: unique-node slot of each entry
-  R* u_fb;    // 3 x cap: f-bar per unique node
-  R* u_rb;    // 4 x cap: forced-node (rho, J) adjoint per unique node
-  R* zb_b;    // N: zeta-bar per bead
-  R* u_sp;     // 4 x cap: (rho-bar, J-bar) summed per unique forced node
   int* u_node;  // cap: the unique forced nodes
+  int* ce_node; // 8N: node of each corner entry
+  int smem_scratch;
+  unsigned smem_off;
 };
+
+// Carve the per-step scratch of AdjK from one region starting at base (16-byte aligned pieces,
+// in a fixed order); returns its size.  base may be null to compute the size only.
+template <class R>
+__host__ __device__ inline size_t carve_adj_scratch(AdjK<R>& A, unsigned char* base, int N, int cap) {
+  size_t off = 0;
+  auto piece = [&](size_t bytes) {
+    unsigned char* p = base ? base + off : nullptr;
+    off += (bytes + 15) / 16 * 16;
+    return p;
+  };
+  const size_t n3 = 3 * (size_t)N, ne = (size_t)cap;
+  A.vh = reinterpret_cast<R*>(piece(n3 * sizeof(R)));
+  A.ub = reinterpret_cast<R*>(piece(n3 * sizeof(R)));
+  A.g = reinterpret_cast<R*>(piece(n3 * sizeof(R)));
+  A.fc = reinterpret_cast<R*>(piece(n3 * sizeof(R)));
+  A.fct = reinterpret_cast<R*>(piece(n3 * sizeof(R)));
+  A.vhb = reinterpret_cast<R*>(piece(n3 * sizeof(R)));
+  A.xpb = reinterpret_cast<R*>(piece(n3 * sizeof(R)));
+  A.e_gw = reinterpret_cast<R*>(piece(3 * ne * sizeof(R)));
+  A.e_rb = reinterpret_cast<R*>(piece(4 * ne * sizeof(R)));
+  A.u_fb = reinterpret_cast<R*>(piece(3 * ne * sizeof(R)));
+  A.u_rb = reinterpret_cast<R*>(piece(4 * ne * sizeof(R)));
+  A.u_sp = reinterpret_cast<R*>(piece(4 * ne * sizeof(R)));
+  A.zb_b = reinterpret_cast<R*>(piece((size_t)N * sizeof(R)));
+  A.ce_w = reinterpret_cast<R*>(piece(ne * sizeof(R)));
+  A.ce_mom = reinterpret_cast<R*>(piece(4 * ne * sizeof(R)));
+  A.e_slot = reinterpret_cast<int*>(piece(ne * sizeof(int)));
+  A.u_node = reinterpret_cast<int*>(piece(ne * sizeof(int)));
+  A.ce_node = reinterpret_cast<int*>(piece(ne * sizeof(int)));
+  return off;
+}
 
 template <class S, class R, bool DEV>
 __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, const R* __restrict__ lam,
                                                    R* __restrict__ lam_out, const FluidK<R> P, const ChainK<R> C,
-                                                   const AdjK<R> A, const uint32_t step) {
+                                                   const AdjK<R> A0, const uint32_t step) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = C.N, tid = threadIdx.x, nt = blockDim.x, L = (int)P.L;
+  AdjK<R> A = A0;
+  if (A0.smem_scratch) carve_adj_scratch(A, smem + A0.smem_off, N, C.cap);
   const R h = C.h;
   R* sx = reinterpret_cast<R*>(smem);
   R* sl = sx + 3 * N;
@@ -281,20 +320,20 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
     const int qx = (cl[0] + d3[0]) % L, qy = (cl[1] + d3[1]) % L, qz = (cl[2] + d3[2]) % L;
     R mom[4];
     gather_node<S, R, DEV>(state, P, qx, qy, qz, mom);
-    C.e_node[e] = qx + L * (qy + L * qz);
-    C.e_w[e] = w;
+    A.ce_node[e] = qx + L * (qy + L * qz);
+    A.ce_w[e] = w;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) C.e_mom[q * C.cap + e] = mom[q];
+    for (int q = 0; q < 4; ++q) A.ce_mom[q * C.cap + e] = mom[q];
   }
   __syncthreads();
   for (int b = tid; b < N; b += nt) {
     R ub[3] = {R(0), R(0), R(0)};
     for (int c = 0; c < 8; ++c) {
       const int e = 8 * b + c;
-      const R w = C.e_w[e], ir = R(1) / C.e_mom[e];
-      ub[0] += w * C.e_mom[C.cap + e] * ir;
-      ub[1] += w * C.e_mom[2 * C.cap + e] * ir;
-      ub[2] += w * C.e_mom[3 * C.cap + e] * ir;
+      const R w = A.ce_w[e], ir = R(1) / A.ce_mom[e];
+      ub[0] += w * A.ce_mom[C.cap + e] * ir;
+      ub[1] += w * A.ce_mom[2 * C.cap + e] * ir;
+      ub[2] += w * A.ce_mom[3 * C.cap + e] * ir;
     }
     R g[4] = {R(0), R(0), R(0), R(0)};
     if (C.amp != R(0)) gauss4<R>(step, (uint32_t)b, 0u, C.k0, C.k1, g);
@@ -319,7 +358,7 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem + 6 * N * sizeof(R) + 16);
   keys = reinterpret_cast<unsigned long long*>((reinterpret_cast<uintptr_t>(keys) + 15) & ~(uintptr_t)15);
   for (int i = tid; i < M; i += nt)
-    keys[i] = (i < ne) ? (((unsigned long long)(unsigned)C.e_node[i] << 32) | (unsigned)i) : ~0ull;
+    keys[i] = (i < ne) ? (((unsigned long long)(unsigned)A.ce_node[i] << 32) | (unsigned)i) : ~0ull;
   __syncthreads();
   if (ne <= nt) {
     // few entries: each thread places its key by its rank among all keys (distinct: the entry
@@ -376,11 +415,11 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
       const int e = (int)(keys[r] & 0xffffffffu);
       const int b = e >> 3;
       A.e_slot[e] = u;
-      f[0] -= C.e_w[e] * A.fc[3 * b + 0] * C.inv_a3;
-      f[1] -= C.e_w[e] * A.fc[3 * b + 1] * C.inv_a3;
-      f[2] -= C.e_w[e] * A.fc[3 * b + 2] * C.inv_a3;
+      f[0] -= A.ce_w[e] * A.fc[3 * b + 0] * C.inv_a3;
+      f[1] -= A.ce_w[e] * A.fc[3 * b + 1] * C.inv_a3;
+      f[2] -= A.ce_w[e] * A.fc[3 * b + 2] * C.inv_a3;
     }
-    const R rho = C.e_mom[e0], jx = C.e_mom[C.cap + e0], jy = C.e_mom[2 * C.cap + e0], jz = C.e_mom[3 * C.cap + e0];
+    const R rho = A.ce_mom[e0], jx = A.ce_mom[C.cap + e0], jy = A.ce_mom[2 * C.cap + e0], jz = A.ce_mom[3 * C.cap + e0];
     R nb[Q], ab[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) nb[q] = lam[(unsigned long long)q * P.plane + (unsigned)node];
@@ -418,7 +457,7 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
     for (int c = 0; c < 8; ++c) {
       const int e = 8 * b + c, u = A.e_slot[e];
       const R fbx = A.u_fb[u], fby = A.u_fb[C.cap + u], fbz = A.u_fb[2 * C.cap + u];
-      const R w = C.e_w[e];
+      const R w = A.ce_w[e];
       fcb[0] -= w * C.inv_a3 * fbx;
       fcb[1] -= w * C.inv_a3 * fby;
       fcb[2] -= w * C.inv_a3 * fbz;
@@ -438,8 +477,8 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
     // interpolation: u_b = sum_e w_e J_e / rho_e (a/h)
     for (int c = 0; c < 8; ++c) {
       const int e = 8 * b + c;
-      const R w = C.e_w[e], rho = C.e_mom[e], ir = R(1) / rho;
-      const R J[3] = {C.e_mom[C.cap + e], C.e_mom[2 * C.cap + e], C.e_mom[3 * C.cap + e]};
+      const R w = A.ce_w[e], rho = A.ce_mom[e], ir = R(1) / rho;
+      const R J[3] = {A.ce_mom[C.cap + e], A.ce_mom[2 * C.cap + e], A.ce_mom[3 * C.cap + e]};
       R ue[3], uJ = R(0);
 #pragma unroll
       for (int q = 0; q < 3; ++q) ue[q] = J[q] * ir * C.u_scale;

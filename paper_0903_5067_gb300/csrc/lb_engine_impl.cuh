@@ -198,11 +198,17 @@ class EngineT final : public Engine {
     const size_t o_fin = take(stb);
     const size_t o_lam0 = take(lamb), o_lam1 = take(lamb);
     const size_t o_bar = take(3 * n3 * sizeof(R));
-    // bead adjoint scratch, and its own corner entries (node, weight, rho and J): the
-    // recomputation running beside it uses the context's
-    const size_t o_adj = take(10 * n3 * sizeof(R) + (size_t)cap_ * (3 + 1 + 4) * sizeof(R) + cap_ * sizeof(int) +
-                              (size_t)cap_ * 7 * sizeof(R) + N_ * sizeof(R) + (size_t)cap_ * 4 * sizeof(R) +
-                              cap_ * sizeof(int) + (size_t)cap_ * 5 * sizeof(R) + cap_ * sizeof(int) + 4096);
+    // bead adjoint scratch with its own corner entries (the recomputation running beside it
+    // uses the context's): in the kernel's shared memory when it fits, else here
+    AdjK<R> A;
+    memset(&A, 0, sizeof(A));
+    const size_t adj_scratch = carve_adj_scratch<R>(A, nullptr, N_, cap_);
+    const size_t ne = 8 * (size_t)N_;
+    size_t M = 1;
+    while (M < ne) M <<= 1;
+    const size_t smem_base = align_up(align_up(6 * n3 / 3 * sizeof(R) + 32, 16) + M * 8 + ne * 4 + 64, 16);
+    const bool scratch_in_smem = smem_base + adj_scratch <= 200 * 1024;
+    const size_t o_adj = take(scratch_in_smem ? 16 : adj_scratch);
     const size_t o_z = take(sizeof(double));
     unsigned char* base = nullptr;
     cuda_check(cudaMalloc(&base, off), "adjoint scratch");
@@ -271,49 +277,22 @@ class EngineT final : public Engine {
     R* lam[2] = {reinterpret_cast<R*>(base + o_lam0), reinterpret_cast<R*>(base + o_lam1)};
     cuda_check(cudaMemsetAsync(lam[0], 0, lamb, s), "lambda");
     cuda_check(cudaMemsetAsync(lam[1], 0, lamb, s), "lambda");
-    AdjK<R> A;
-    memset(&A, 0, sizeof(A));
-    R* rev_e_w = nullptr;
-    R* rev_e_mom = nullptr;
-    int* rev_e_node = nullptr;
     R* bars = reinterpret_cast<R*>(base + o_bar);
     A.xbar = bars;
     A.vbar = bars + n3;
     A.fbar = bars + 2 * n3;
     cuda_check(cudaMemsetAsync(bars, 0, 3 * n3 * sizeof(R), s), "bars");
     cuda_check(cudaMemcpyAsync(A.xbar, xb0.data(), n3 * sizeof(R), cudaMemcpyHostToDevice, s), "xbar");
-    {
-      R* q = reinterpret_cast<R*>(base + o_adj);
-      A.xp = q; q += n3;
-      A.xpl = q; q += n3;
-      A.vh = q; q += n3;
-      A.ub = q; q += n3;
-      A.g = q; q += n3;
-      A.fc = q; q += n3;
-      A.fct = q; q += n3;
-      A.vhb = q; q += n3;
-      A.xpb = q; q += n3;
-      A.fcb = q; q += n3;
-      A.e_gw = q; q += 3 * (size_t)cap_;
-      A.e_wb = q; q += cap_;
-      A.e_rb = q; q += 4 * (size_t)cap_;
-      A.u_fb = q; q += 3 * (size_t)cap_;
-      A.u_rb = q; q += 4 * (size_t)cap_;
-      A.zb_b = q; q += N_;
-      A.u_sp = q; q += 4 * (size_t)cap_;
-      rev_e_w = q; q += cap_;
-      rev_e_mom = q; q += 4 * (size_t)cap_;
-      A.e_slot = reinterpret_cast<int*>(q);
-      A.u_node = A.e_slot + cap_;
-      rev_e_node = A.u_node + cap_;
-      A.zbar = reinterpret_cast<double*>(base + o_z);
+    if (scratch_in_smem) {
+      A.smem_scratch = 1;
+      A.smem_off = (unsigned)smem_base;
+    } else {
+      carve_adj_scratch<R>(A, base + o_adj, N_, cap_);
     }
+    A.zbar = reinterpret_cast<double*>(base + o_z);
     cuda_check(cudaMemsetAsync(A.zbar, 0, sizeof(double), s), "zbar");
     const ChainK<R> C = chain();
-    const size_t ne = 8 * (size_t)N_;
-    size_t M = 1;
-    while (M < ne) M <<= 1;
-    const size_t smem = align_up(6 * n3 / 3 * sizeof(R) + 32, 16) + M * 8 + ne * 4 + 64;
+    const size_t smem = scratch_in_smem ? smem_base + adj_scratch : smem_base;
     if (smem > 48 * 1024)
       cuda_check(cudaFuncSetAttribute(k_adj_bead<S, R, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                  "adjoint smem");
@@ -363,9 +342,6 @@ class EngineT final : public Engine {
         Ct.v = reinterpret_cast<R*>(at(stt, v_));
         Ct.F = reinterpret_cast<R*>(at(stt, F_));
         Ct.Fc = reinterpret_cast<R*>(at(stt, Fc_));
-        Ct.e_node = rev_e_node;
-        Ct.e_w = rev_e_w;
-        Ct.e_mom = rev_e_mom;
         const uint32_t kt = (uint32_t)(k0 + t);
         // the adjoint LB kernel (all nodes) and, beside it, the bead adjoint (one block), which
         // adds its forced-node terms to lambda once the LB kernel has written it
