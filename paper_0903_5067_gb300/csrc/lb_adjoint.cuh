@@ -133,9 +133,10 @@ __device__ __forceinline__ void scaled_moment_adjoint(const R nb[Q], R ab[Q]) {
 // k_adj_bead).
 template <class S, class R, bool DEV, bool NOISE>
 __global__ void __launch_bounds__(256) k_adj_lb(const S* __restrict__ state, const R* __restrict__ lam_in,
-                                                 R* __restrict__ lam_out, const FluidK<R> P, const uint32_t step) {
+                                                 R* __restrict__ lam_out, const FluidK<R> P, const uint32_t step_arg) {
   grid_dependency_wait();
   allow_dependent_launch();
+  const uint32_t step = launch_step(P, step_arg);
   const unsigned L = P.L;
   const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -264,7 +265,8 @@ __host__ __device__ inline size_t carve_adj_scratch(AdjK<R>& A, unsigned char* b
 template <class S, class R, bool DEV>
 __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, const R* __restrict__ lam,
                                                    R* __restrict__ lam_out, const FluidK<R> P, const ChainK<R> C,
-                                                   const AdjK<R> A0, const uint32_t step) {
+                                                   const AdjK<R> A0, const uint32_t step_arg) {
+  const uint32_t step = launch_step(P, step_arg);
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = C.N, tid = threadIdx.x, nt = blockDim.x, L = (int)P.L;
   AdjK<R> A = A0;

@@ -120,7 +120,20 @@ struct FluidK {
   unsigned long long* nonpos;  // counter of non-positive densities met by the noise
   int pdl;         // launch chaining of the LB kernel: bit 0 waits for the previous grid before
                    // reading, bit 1 waits for it before completing (see k_lb_step)
+  // null, or a device counter the step kernels add their step argument to (graph replays of a
+  // fixed sequence of launches at other step numbers)
+  const uint32_t* d_step;
 };
+
+// the step number of a launch: its argument, offset by the device counter when there is one
+template <class R>
+__device__ __forceinline__ uint32_t launch_step(const FluidK<R>& P, uint32_t step) {
+  return P.d_step ? *P.d_step + step : step;
+}
+
+// *p = v on the stream (a device step counter before a graph replay)
+template <class T>
+__global__ void k_store_value(T* p, T v) { *p = v; }
 
 template <class R>
 struct ChainK {
@@ -649,11 +662,12 @@ __global__ void __launch_bounds__(256, LbMinBlocks<R, PAIR>::value) k_lb_step(co
   }
   if (P.pdl & 1) grid_dependency_wait();
   allow_dependent_launch();
+  const uint32_t k = launch_step(P, step);
   if constexpr (PAIR)
-    lb_tile2<S, R, DEV, NOISE, I, CORR>(src, dst, P, Pd, step, blockIdx.x, blockIdx.y, blockIdx.z,
+    lb_tile2<S, R, DEV, NOISE, I, CORR>(src, dst, P, Pd, k, blockIdx.x, blockIdx.y, blockIdx.z,
                                         reinterpret_cast<R*>(lsm));
   else
-    lb_tile<S, R, DEV, NOISE, I, CORR>(src, dst, P, Pd, step, blockIdx.x, blockIdx.y, blockIdx.z,
+    lb_tile<S, R, DEV, NOISE, I, CORR>(src, dst, P, Pd, k, blockIdx.x, blockIdx.y, blockIdx.z,
                                        reinterpret_cast<R*>(lsm));
 }
 
@@ -1300,7 +1314,7 @@ __global__ void __launch_bounds__(512) k_bead_step(const S* __restrict__ pop, co
   asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(G));
   grid_dependency_wait();
   allow_dependent_launch();
-  bead_step_block<S, R, DEV>(pop, P, C, Pd, step, smem, (int)rank, (int)G);
+  bead_step_block<S, R, DEV>(pop, P, C, Pd, launch_step(P, step), smem, (int)rank, (int)G);
 }
 
 // B[i][node] += dn_i at every pending node (each node appears once in the list), and the

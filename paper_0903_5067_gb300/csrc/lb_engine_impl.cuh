@@ -139,9 +139,8 @@ class EngineT final : public Engine {
 
   // One complete step with the bead kernel's state arrays given (the adjoint's recomputation:
   // read a saved state, write the next one); the context's own bead arrays are not touched.
-  void step_with_chain(uint32_t k, cudaStream_t s, const ChainK<R>& C) {
+  void step_with_chain(uint32_t k, cudaStream_t s, const ChainK<R>& C, const FluidK<R>& P) {
     flush(s);
-    const FluidK<R> P = fluid();
     const S* A = pop_[cur_];
     S* Bo = pop_[cur_ ^ 1];
     const PendK<R> Pd = pend(false);
@@ -192,9 +191,10 @@ class EngineT final : public Engine {
       return o;
     };
     const size_t o_ck = take((size_t)nck * stb);
-    // two pools of the states t0 + 1 .. t0 + K of a segment: the recomputation of one segment
-    // fills one pool while the reverse sweep of the segment after it reads the other
-    const size_t o_pool = take(2 * (size_t)K * stb);
+    // two pools of the states t0 .. t0 + K of a segment (slot 0 a copy of its checkpoint): the
+    // recomputation of one segment fills one pool while the reverse sweep of the segment after
+    // it reads the other
+    const size_t o_pool = take(2 * (size_t)(K + 1) * stb);
     const size_t o_fin = take(stb);
     const size_t o_lam0 = take(lamb), o_lam1 = take(lamb);
     const size_t o_bar = take(3 * n3 * sizeof(R));
@@ -210,6 +210,7 @@ class EngineT final : public Engine {
     const bool scratch_in_smem = smem_base + adj_scratch <= 200 * 1024;
     const size_t o_adj = take(scratch_in_smem ? 16 : adj_scratch);
     const size_t o_z = take(sizeof(double));
+    const size_t o_ctr = take(2 * sizeof(uint32_t));  // step counters of the segment graphs
     unsigned char* base = nullptr;
     cuda_check(cudaMalloc(&base, off), "adjoint scratch");
     S* const own_pop[2] = {pop_[0], pop_[1]};
@@ -218,19 +219,23 @@ class EngineT final : public Engine {
       S* p0;
       S* p1;
       unsigned char* p;
-      cudaStream_t s2;
+      cudaStream_t s2, cs;
       std::vector<cudaEvent_t> ev;
+      cudaGraphExec_t g[6];  // recomputation by pool, reverse sweep by pool and lambda parity
       ~Restore() {
         e->pop_[0] = p0;
         e->pop_[1] = p1;
-        if (s2) {
-          cudaStreamSynchronize(s2);
-          cudaStreamDestroy(s2);
-        }
+        for (cudaStream_t x : {s2, cs})
+          if (x) {
+            cudaStreamSynchronize(x);
+            cudaStreamDestroy(x);
+          }
+        for (cudaGraphExec_t x : g)
+          if (x) cudaGraphExecDestroy(x);
         for (cudaEvent_t x : ev) cudaEventDestroy(x);
         cudaFree(p);
       }
-    } guard{this, own_pop[0], own_pop[1], base, nullptr, {}};
+    } guard{this, own_pop[0], own_pop[1], base, nullptr, nullptr, {}, {}};
     auto new_event = [&]() {
       cudaEvent_t x = nullptr;
       cuda_check(cudaEventCreateWithFlags(&x, cudaEventDisableTiming), "adjoint event");
@@ -242,7 +247,7 @@ class EngineT final : public Engine {
       cuda_check(cudaMemcpyAsync(dst + popb, bead0, beadb, cudaMemcpyDeviceToDevice, s), "save beads");
     };
     auto ck = [&](int i) { return base + o_ck + (size_t)i * stb; };
-    auto pool = [&](int pid, int i) { return base + o_pool + ((size_t)pid * K + i) * stb; };
+    auto pool = [&](int pid, int i) { return base + o_pool + ((size_t)pid * (K + 1) + i) * stb; };
     // a state's bead arrays, at their offsets within the saved span
     auto at = [&](unsigned char* st, const void* arr) {
       return st + popb + (size_t)(reinterpret_cast<const unsigned char*>(arr) - bead0);
@@ -299,19 +304,24 @@ class EngineT final : public Engine {
     dim3 blk, grd;
     lb_launch_shape(blk, grd, false);  // the adjoint LB kernel: one node per thread
     int cur_lam = 0;
-    // 3. reverse sweep over the segments.  The states t0 .. t1 - 1 of a segment: slot 0 is its
-    //    checkpoint, slots 1 .. are written by the recomputation, whose steps read the
-    //    populations and bead state of slot i and write those of slot i + 1 (the context's
-    //    population buffers pointed at the slots; no copies).  The reverse steps read a slot's
-    //    state in place.  The recomputation of segment k - 1 needs only its checkpoint, so it
-    //    runs on a second stream beside the reverse sweep of segment k, in the other pool.
-    auto slot = [&](int sgi, int pid, int i) { return i == 0 ? ck(sgi) : pool(pid, i - 1); };
-    auto recompute = [&](int sgi, int pid, cudaStream_t st) {
-      const int64_t t0 = (int64_t)sgi * K, t1 = t0 + K < T ? t0 + K : T;
+    // 3. reverse sweep over the segments.  The states t0 .. t1 - 1 of a segment sit in the
+    //    slots of a pool: slot 0 a copy of its checkpoint, slots 1 .. written by the
+    //    recomputation, whose steps read the populations and bead state of slot i and write
+    //    those of slot i + 1 (the context's population buffers pointed at the slots).  The
+    //    reverse steps read a slot's state in place.  The recomputation of segment k - 1 needs
+    //    only its checkpoint, so it runs on a second stream beside the reverse sweep of segment
+    //    k, in the other pool.  A full segment's recomputation or reverse sweep is the same
+    //    sequence of launches at other step numbers: each is captured once as a CUDA graph whose
+    //    kernels add their step argument to a device counter, and replayed.
+    uint32_t* d_ctr = reinterpret_cast<uint32_t*>(base + o_ctr);
+    FluidK<R> Prec = P, Prev = P;
+    Prec.d_step = d_ctr;
+    Prev.d_step = d_ctr + 1;
+    auto recompute_ops = [&](int64_t t0, int64_t t1, int pid, cudaStream_t st, const FluidK<R>& Pk, bool rel) {
       for (int64_t t = t0; t < t1; ++t) {
         const int i = (int)(t - t0);
-        unsigned char* a = slot(sgi, pid, i);
-        unsigned char* b = slot(sgi, pid, i + 1);
+        unsigned char* a = pool(pid, i);
+        unsigned char* b = pool(pid, i + 1);
         pop_[cur_] = reinterpret_cast<S*>(a);
         pop_[cur_ ^ 1] = reinterpret_cast<S*>(b);
         ChainK<R> Cs = C;  // read the bead state of slot i, write the next state into slot i + 1
@@ -327,13 +337,12 @@ class EngineT final : public Engine {
         Cs.F = reinterpret_cast<R*>(at(b, F_));
         Cs.Fc = reinterpret_cast<R*>(at(b, Fc_));
         Cs.snap = nullptr;
-        step_with_chain((uint32_t)(k0 + t), st, Cs);
+        step_with_chain(rel ? (uint32_t)(t - t0) : (uint32_t)(k0 + t), st, Cs, Pk);
       }
     };
-    auto reverse = [&](int sgi, int pid, cudaStream_t st) {
-      const int64_t t0 = (int64_t)sgi * K, t1 = t0 + K < T ? t0 + K : T;
+    auto reverse_ops = [&](int64_t t0, int64_t t1, int pid, cudaStream_t st, const FluidK<R>& Pk, bool rel) {
       for (int64_t t = t1 - 1; t >= t0; --t) {
-        unsigned char* stt = slot(sgi, pid, (int)(t - t0));
+        unsigned char* stt = pool(pid, (int)(t - t0));
         const S* pops = reinterpret_cast<const S*>(stt);
         ChainK<R> Ct = C;
         Ct.x = reinterpret_cast<R*>(at(stt, x_));
@@ -342,7 +351,7 @@ class EngineT final : public Engine {
         Ct.v = reinterpret_cast<R*>(at(stt, v_));
         Ct.F = reinterpret_cast<R*>(at(stt, F_));
         Ct.Fc = reinterpret_cast<R*>(at(stt, Fc_));
-        const uint32_t kt = (uint32_t)(k0 + t);
+        const uint32_t kt = rel ? (uint32_t)(t - t0) : (uint32_t)(k0 + t);
         // the adjoint LB kernel (all nodes) and, beside it, the bead adjoint (one block), which
         // adds its forced-node terms to lambda once the LB kernel has written it
         cudaLaunchAttribute at1[1];
@@ -357,17 +366,57 @@ class EngineT final : public Engine {
         la.numAttrs = 1;
         const R* lin = lam[cur_lam];
         R* lout = lam[cur_lam ^ 1];
-        if (P.ncalls > 0)
-          cuda_check(cudaLaunchKernelEx(&la, k_adj_lb<S, R, DEV, true>, pops, lin, lout, P, kt), "adjoint LB");
+        if (Pk.ncalls > 0)
+          cuda_check(cudaLaunchKernelEx(&la, k_adj_lb<S, R, DEV, true>, pops, lin, lout, Pk, kt), "adjoint LB");
         else
-          cuda_check(cudaLaunchKernelEx(&la, k_adj_lb<S, R, DEV, false>, pops, lin, lout, P, kt), "adjoint LB");
+          cuda_check(cudaLaunchKernelEx(&la, k_adj_lb<S, R, DEV, false>, pops, lin, lout, Pk, kt), "adjoint LB");
         cudaLaunchConfig_t lbd = la;
         lbd.gridDim = dim3(1);
         lbd.blockDim = dim3(512);
         lbd.dynamicSmemBytes = smem;
-        cuda_check(cudaLaunchKernelEx(&lbd, k_adj_bead<S, R, DEV>, pops, lin, lout, P, Ct, A, kt), "adjoint bead");
+        cuda_check(cudaLaunchKernelEx(&lbd, k_adj_bead<S, R, DEV>, pops, lin, lout, Pk, Ct, A, kt), "adjoint bead");
         cur_lam ^= 1;
       }
+    };
+    // run ops on stream st: directly for a partial segment, else as the graph g (captured on
+    // the first use; ctr is the graph's step counter, set to the segment's first step)
+    auto run_segment = [&](int64_t t0, int64_t t1, cudaStream_t st, cudaGraphExec_t& g, uint32_t* ctr,
+                           auto&& ops) {
+      if (t1 - t0 < K) {
+        ops(st, P, false);
+        return;
+      }
+      k_store_value<uint32_t><<<1, 1, 0, st>>>(ctr, (uint32_t)(k0 + t0));
+      cuda_check(cudaGetLastError(), "step counter");
+      if (!g) {
+        if (!guard.cs) cuda_check(cudaStreamCreateWithFlags(&guard.cs, cudaStreamNonBlocking), "capture stream");
+        cudaGraph_t gr = nullptr;
+        cuda_check(cudaStreamBeginCapture(guard.cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+        ops(guard.cs, P, true);
+        cuda_check(cudaStreamEndCapture(guard.cs, &gr), "end capture");
+        const cudaError_t ie = cudaGraphInstantiate(&g, gr, 0);
+        cudaGraphDestroy(gr);
+        cuda_check(ie, "instantiate segment graph");
+      } else {
+        ops(nullptr, P, false);  // host-side bookkeeping only (see below)
+      }
+      cuda_check(cudaGraphLaunch(g, st), "segment graph");
+    };
+    auto recompute = [&](int sgi, int pid) {
+      const int64_t t0 = (int64_t)sgi * K, t1 = t0 + K < T ? t0 + K : T;
+      cuda_check(cudaMemcpyAsync(pool(pid, 0), ck(sgi), stb, cudaMemcpyDeviceToDevice, guard.s2), "checkpoint");
+      run_segment(t0, t1, guard.s2, guard.g[pid], d_ctr, [&](cudaStream_t st, const FluidK<R>&, bool rel) {
+        if (st) recompute_ops(t0, t1, pid, st, rel ? Prec : P, rel);
+      });
+    };
+    auto reverse = [&](int sgi, int pid) {
+      const int64_t t0 = (int64_t)sgi * K, t1 = t0 + K < T ? t0 + K : T;
+      run_segment(t0, t1, s, guard.g[2 + 2 * pid + cur_lam], d_ctr + 1, [&](cudaStream_t st, const FluidK<R>&, bool rel) {
+        if (st)
+          reverse_ops(t0, t1, pid, st, rel ? Prev : P, rel);
+        else
+          cur_lam ^= (int)((t1 - t0) & 1);  // what the captured sequence does to the parity
+      });
     };
     cuda_check(cudaStreamCreateWithFlags(&guard.s2, cudaStreamNonBlocking), "adjoint stream");
     {
@@ -376,19 +425,19 @@ class EngineT final : public Engine {
       cuda_check(cudaStreamWaitEvent(guard.s2, fwd, 0), "wait");
     }
     std::vector<cudaEvent_t> rec_done(nck), rev_done(nck);
-    recompute(nck - 1, 0, guard.s2);
+    recompute(nck - 1, 0);
     rec_done[nck - 1] = new_event();
     cuda_check(cudaEventRecord(rec_done[nck - 1], guard.s2), "event");
     for (int sgi = nck - 1; sgi >= 0; --sgi) {
       const int pid = (nck - 1 - sgi) & 1;
       if (sgi >= 1) {  // the next segment's recomputation, into the pool the last reverse sweep read
         if (sgi + 1 <= nck - 1) cuda_check(cudaStreamWaitEvent(guard.s2, rev_done[sgi + 1], 0), "wait");
-        recompute(sgi - 1, pid ^ 1, guard.s2);
+        recompute(sgi - 1, pid ^ 1);
         rec_done[sgi - 1] = new_event();
         cuda_check(cudaEventRecord(rec_done[sgi - 1], guard.s2), "event");
       }
       cuda_check(cudaStreamWaitEvent(s, rec_done[sgi], 0), "wait");
-      reverse(sgi, pid, s);
+      reverse(sgi, pid);
       rev_done[sgi] = new_event();
       cuda_check(cudaEventRecord(rev_done[sgi], s), "event");
     }
