@@ -378,12 +378,14 @@ class EngineT final : public Engine {
         cur_lam ^= 1;
       }
     };
-    // run ops on stream st: directly for a partial segment, else as the graph g (captured on
-    // the first use; ctr is the graph's step counter, set to the segment's first step)
-    auto run_segment = [&](int64_t t0, int64_t t1, cudaStream_t st, cudaGraphExec_t& g, uint32_t* ctr,
-                           auto&& ops) {
+    // Run a segment's launches on stream st: directly for a partial segment, else as the graph
+    // g (captured on the first use; ctr is the graph's step counter, set to the segment's first
+    // step).  ops(stream, relative) enqueues the launches; book() does on the host what they do
+    // to its state, for a replay.
+    auto run_segment = [&](int64_t t0, int64_t t1, cudaStream_t st, cudaGraphExec_t& g, uint32_t* ctr, auto&& ops,
+                           auto&& book) {
       if (t1 - t0 < K) {
-        ops(st, P, false);
+        ops(st, false);
         return;
       }
       k_store_value<uint32_t><<<1, 1, 0, st>>>(ctr, (uint32_t)(k0 + t0));
@@ -392,31 +394,29 @@ class EngineT final : public Engine {
         if (!guard.cs) cuda_check(cudaStreamCreateWithFlags(&guard.cs, cudaStreamNonBlocking), "capture stream");
         cudaGraph_t gr = nullptr;
         cuda_check(cudaStreamBeginCapture(guard.cs, cudaStreamCaptureModeThreadLocal), "begin capture");
-        ops(guard.cs, P, true);
+        ops(guard.cs, true);
         cuda_check(cudaStreamEndCapture(guard.cs, &gr), "end capture");
         const cudaError_t ie = cudaGraphInstantiate(&g, gr, 0);
         cudaGraphDestroy(gr);
         cuda_check(ie, "instantiate segment graph");
       } else {
-        ops(nullptr, P, false);  // host-side bookkeeping only (see below)
+        book();
       }
       cuda_check(cudaGraphLaunch(g, st), "segment graph");
     };
     auto recompute = [&](int sgi, int pid) {
       const int64_t t0 = (int64_t)sgi * K, t1 = t0 + K < T ? t0 + K : T;
       cuda_check(cudaMemcpyAsync(pool(pid, 0), ck(sgi), stb, cudaMemcpyDeviceToDevice, guard.s2), "checkpoint");
-      run_segment(t0, t1, guard.s2, guard.g[pid], d_ctr, [&](cudaStream_t st, const FluidK<R>&, bool rel) {
-        if (st) recompute_ops(t0, t1, pid, st, rel ? Prec : P, rel);
-      });
+      run_segment(
+          t0, t1, guard.s2, guard.g[pid], d_ctr,
+          [&](cudaStream_t st, bool rel) { recompute_ops(t0, t1, pid, st, rel ? Prec : P, rel); }, [] {});
     };
     auto reverse = [&](int sgi, int pid) {
       const int64_t t0 = (int64_t)sgi * K, t1 = t0 + K < T ? t0 + K : T;
-      run_segment(t0, t1, s, guard.g[2 + 2 * pid + cur_lam], d_ctr + 1, [&](cudaStream_t st, const FluidK<R>&, bool rel) {
-        if (st)
-          reverse_ops(t0, t1, pid, st, rel ? Prev : P, rel);
-        else
-          cur_lam ^= (int)((t1 - t0) & 1);  // what the captured sequence does to the parity
-      });
+      run_segment(
+          t0, t1, s, guard.g[2 + 2 * pid + cur_lam], d_ctr + 1,
+          [&](cudaStream_t st, bool rel) { reverse_ops(t0, t1, pid, st, rel ? Prev : P, rel); },
+          [&] { cur_lam ^= (int)((t1 - t0) & 1); });  // the captured sequence's effect on the parity
     };
     cuda_check(cudaStreamCreateWithFlags(&guard.s2, cudaStreamNonBlocking), "adjoint stream");
     {

@@ -68,6 +68,22 @@ def test_adjoint_fp64_matches_finite_differences_of_the_gpu_path(lblib):
     assert gz == pytest.approx(fdz, rel=1e-5, abs=1e-8)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_adjoint_is_independent_of_the_checkpoint_interval(lblib, prec):
+    """The gradient does not depend on how the T steps are cut into checkpoint segments: a
+    single segment longer than T (launched directly), full segments replayed as graphs with a
+    partial last segment, and full segments only, all against one segment of T steps (the same
+    states are recomputed bit for bit, so the results agree to round-off of nothing)."""
+    p = lblib.LB_FP64 if prec == "fp64" else lblib.LB_FP32
+    L, N, seed = 8, 4, 21
+    X0 = inputs.chain_walk(N, L=L, bond=0.97, seed=seed, self_avoiding=True)
+    for T, Ks in ((7, (10, 3)), (23, (5, 4)), (24, (6, 5))):
+        O, gx, gz = _gpu_adjoint(lblib, L, X0, 20.8, T, T, seed, p)
+        for K in Ks:
+            O2, gx2, gz2 = _gpu_adjoint(lblib, L, X0, 20.8, T, K, seed, p)
+            assert O2 == O and np.array_equal(gx2, gx) and gz2 == gz, (T, K)
+
+
 def test_adjoint_c5_workload_matches_oracle_finite_differences(lblib):
     """L=32, N=16, 100 steps, checkpoints every 10, noise fixed by seed 7: FP32 adjoint
     within 1e-3 and FP64 adjoint within 1e-6 of central differences of the FP64 oracle with
