@@ -33,6 +33,11 @@ L_BENCH, N_BENCH, SEED = 128, 128, 3
 PARAMS = dict(rho=1.0, eta=3.0, eta_b=3.0, kT=1.0, h=0.01, a=1.0)
 CHAIN = dict(m=1.0, zeta=20.8, k_fene=30.0, R0=1.5, eps=1.0, sigma=1.0)
 BYTES_PER_NODE = {"f32": 19 * 4 * 2, "f64": 19 * 8 * 2, "bf16": 19 * 2 * 2}  # algorithmic: 19 reads + 19 writes
+# FP64 operations per node update of the plain FP64 kernel with noise (ncu op counts at L = 128:
+# (DADD + DMUL + 2 DFMA) / nodes = 2.223e9 / 2,097,152); that kernel is bound by FP64 arithmetic
+FP64_FLOPS_PER_NODE = 1060
+# GB300's dense FP64 rate: 152 SMs x 2 FP64 FMA per SM and clock x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 1.26
 KERNEL_SOURCES = ["paper_0903_5067_gb300/csrc/lb_device.cuh", "paper_0903_5067_gb300/csrc/d3q19.cuh",
                   "paper_0903_5067_gb300/csrc/philox.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "lb_step_f32_L128_traffic.json")
@@ -602,6 +607,12 @@ def run_ours(args):
                      "peak_kind": f"{peak_kind} (STREAM copy, burst)"},
         "fp64_plain": {"value": v64, "unit": "MLUPS", "steps": k64, "ms_per_step": t64 / k64 * 1e3,
                        "roofline_frac": BYTES_PER_NODE["f64"] * L ** 3 / (t64 / k64) / 1e9 / peak,
+                       "roofline": {"bound": "fp64",
+                                    "achieved": FP64_FLOPS_PER_NODE * L ** 3 / (t64 / k64) / 1e12,
+                                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                    "frac": FP64_FLOPS_PER_NODE * L ** 3 / (t64 / k64) / 1e12 / FP64_PEAK_TFLOPS,
+                                    "flops_per_node": FP64_FLOPS_PER_NODE,
+                                    "peak_kind": "nominal (152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz)"},
                        "fp32_over_fp64": value / v64},
         "bead_steps_per_s": N * args.steps * ws / tmax,
         "batch_c4": batch,
