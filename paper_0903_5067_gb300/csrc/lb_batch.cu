@@ -122,12 +122,8 @@ __device__ __forceinline__ void batch_tile(const BatchLB<S, R>& B, const int r, 
         }
       }
     }
-    R o0[Q], o1[Q];
-    lb_collide<R, DEV, NOISE>(n0, o0, B.P, B.rk[r], rp.nonpos, step, node);
-    lb_collide<R, DEV, NOISE>(n1, o1, B.P, B.rk[r], rp.nonpos, step, node + 1);
-    S* dst = rp.pop[parity ^ 1];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) st2<S, R>(dst + ((unsigned)i * pl + node), o0[i], o1[i]);
+    lb_collide2_store<S, R, DEV, NOISE, unsigned>(n0, n1, rp.pop[parity ^ 1], B.P, pl, B.rk[r], rp.nonpos, step,
+                                                  node);
   } else {
     const unsigned node = xs + L * row;
     const unsigned mw = corr ? B.mask[pslot][rp.seg0 + (node >> kSegShift)] : 0u;

@@ -469,6 +469,82 @@ __device__ __forceinline__ void lb_collide(const R* n, R out[Q], const FluidK<R>
   pops_from_w2scaled<R>(a, out);
 }
 
+// The two nodes of a thread as the two lanes of packed single-precision arithmetic
+// (add.f32x2, mul.f32x2, fma.f32x2: one instruction for both nodes, each lane rounded as the
+// scalar operation), so that the moment transforms above serve both nodes at once.
+struct f2 {
+  float2 v;
+  __device__ __forceinline__ f2() {}
+  __device__ __forceinline__ explicit f2(float s) : v(make_float2(s, s)) {}
+  __device__ __forceinline__ f2(float a, float b) : v(make_float2(a, b)) {}
+};
+__device__ __forceinline__ f2 mk2(float2 v) {
+  f2 r;
+  r.v = v;
+  return r;
+}
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return mk2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return mk2(__fadd2_rn(a.v, make_float2(-b.v.x, -b.v.y))); }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return mk2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return mk2(__ffma2_rn(a.v, b.v, c.v)); }
+
+// lb_collide for the two nodes of a thread (node, node + 1), lane by lane the same update:
+// moments, relaxation and back-transform in packed arithmetic, the noise node by node.
+template <bool DEV, bool NOISE>
+__device__ __forceinline__ void lb_collide_pair(const f2 n[Q], f2 out[Q], const FluidK<float>& P,
+                                                const RoundKeys& rk, unsigned long long* nonpos,
+                                                const uint32_t step, const unsigned node) {
+  f2 m[10];
+  moments_0_9<f2>(n, m);
+  const f2 rho = DEV ? f2(P.rho0) + m[0] : m[0];
+  const f2 jx = m[1], jy = m[2], jz = m[3];
+  const f2 ir(lb_rcp<float>(rho.v.x), lb_rcp<float>(rho.v.y));
+  const f2 xx = jx * jx * ir, yy = jy * jy * ir, zz = jz * jz * ir;
+  f2 a[Q];
+  a[0] = m[0] * f2((float)(1.0 / 36.0));
+  a[1] = jx * f2((float)(InvB<1>::v / 36.0));
+  a[2] = jy * f2((float)(InvB<2>::v / 36.0));
+  a[3] = jz * f2((float)(InvB<3>::v / 36.0));
+  {
+    const f2 e4 = xx + yy + zz, e5 = f2(2.0f) * xx - yy - zz, e6 = yy - zz;
+    const f2 e7 = jx * jy * ir, e8 = jy * jz * ir, e9 = jx * jz * ir;
+    a[4] = fma2(f2(P.wam[4]), m[4], f2(P.wae[4]) * e4);
+    a[5] = fma2(f2(P.wam[5]), m[5], f2(P.wae[5]) * e5);
+    a[6] = fma2(f2(P.wam[6]), m[6], f2(P.wae[6]) * e6);
+    a[7] = fma2(f2(P.wam[7]), m[7], f2(P.wae[7]) * e7);
+    a[8] = fma2(f2(P.wam[8]), m[8], f2(P.wae[8]) * e8);
+    a[9] = fma2(f2(P.wam[9]), m[9], f2(P.wae[9]) * e9);
+  }
+#pragma unroll
+  for (int k = 10; k < Q; ++k) a[k] = f2(0.0f);
+
+  if (NOISE) {
+    if (!(rho.v.x > 0.0f) || !(rho.v.y > 0.0f))
+      atomicAdd(nonpos, (unsigned long long)(!(rho.v.x > 0.0f)) + (unsigned long long)(!(rho.v.y > 0.0f)));
+    fluid_noise<float>(step, node, rk, P.ncalls > 1, NoiseScale<float>(rho.v.x),
+                       [&](int j, float g) { a[4 + j].v.x = fmaf(P.wag[4 + j], g, a[4 + j].v.x); });
+    fluid_noise<float>(step, node + 1, rk, P.ncalls > 1, NoiseScale<float>(rho.v.y),
+                       [&](int j, float g) { a[4 + j].v.y = fmaf(P.wag[4 + j], g, a[4 + j].v.y); });
+  }
+
+  if (P.body_on) {
+    float d0[10], d1[10];
+    force_moments(rho.v.x, jx.v.x, jy.v.x, jz.v.x, P.body_dJ[0], P.body_dJ[1], P.body_dJ[2], P.gs, P.gb, d0);
+    force_moments(rho.v.y, jx.v.y, jy.v.y, jz.v.y, P.body_dJ[0], P.body_dJ[1], P.body_dJ[2], P.gs, P.gb, d1);
+    a[1] = fma2(f2(d0[1], d1[1]), f2((float)(InvB<1>::v / 36.0)), a[1]);
+    a[2] = fma2(f2(d0[2], d1[2]), f2((float)(InvB<2>::v / 36.0)), a[2]);
+    a[3] = fma2(f2(d0[3], d1[3]), f2((float)(InvB<3>::v / 36.0)), a[3]);
+    a[4] = fma2(f2(d0[4], d1[4]), f2((float)(InvB<4>::v / 36.0)), a[4]);
+    a[5] = fma2(f2(d0[5], d1[5]), f2((float)(InvB<5>::v / 36.0)), a[5]);
+    a[6] = fma2(f2(d0[6], d1[6]), f2((float)(InvB<6>::v / 36.0)), a[6]);
+    a[7] = fma2(f2(d0[7], d1[7]), f2((float)(InvB<7>::v / 36.0)), a[7]);
+    a[8] = fma2(f2(d0[8], d1[8]), f2((float)(InvB<8>::v / 36.0)), a[8]);
+    a[9] = fma2(f2(d0[9], d1[9]), f2((float)(InvB<9>::v / 36.0)), a[9]);
+  }
+
+  pops_from_w2scaled<f2>(a, out);
+}
+
 template <class S, class R, bool DEV, bool NOISE, class I>
 __device__ __forceinline__ void lb_collide_store(const R* n, S* __restrict__ dst, const FluidK<R>& P, const I pl,
                                                  const RoundKeys& rk, unsigned long long* nonpos,
@@ -559,6 +635,29 @@ __device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict
   lb_collide_store<S, R, DEV, NOISE, I>(n, dst, P, pl, P.rk, P.nonpos, step, node);
 }
 
+// Collide the pulled populations n0, n1 of the nodes (node, node + 1) and store the pairs
+// (single precision: packed arithmetic for both nodes, lb_collide_pair).
+template <class S, class R, bool DEV, bool NOISE, class I>
+__device__ __forceinline__ void lb_collide2_store(const R n0[Q], const R n1[Q], S* __restrict__ dst,
+                                                  const FluidK<R>& P, const I pl, const RoundKeys& rk,
+                                                  unsigned long long* nonpos, const uint32_t step,
+                                                  const unsigned node) {
+  if constexpr (sizeof(R) == 4) {
+    f2 n[Q], o[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) n[i] = f2(n0[i], n1[i]);
+    lb_collide_pair<DEV, NOISE>(n, o, P, rk, nonpos, step, node);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st2<S, R>(dst + ((I)i * pl + (I)node), o[i].v.x, o[i].v.y);
+  } else {
+    R o0[Q], o1[Q];
+    lb_collide<R, DEV, NOISE>(n0, o0, P, rk, nonpos, step, node);
+    lb_collide<R, DEV, NOISE>(n1, o1, P, rk, nonpos, step, node + 1);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st2<S, R>(dst + ((I)i * pl + (I)node), o0[i], o1[i]);
+  }
+}
+
 // The populations the two nodes (x0, y, z) and (x0 + 1, y, z), x0 even, pull from their
 // neighbours (periodic; Sec. II B, Eq. 3): n0 for x0, n1 for x0 + 1.  The planes with c_x = 0
 // read both nodes' sources with one two-element access (x0 even and L even keep it aligned);
@@ -620,11 +719,7 @@ __device__ __forceinline__ void lb_tile2(const S* __restrict__ src, S* __restric
       }
     }
   }
-  R o0[Q], o1[Q];
-  lb_collide<R, DEV, NOISE>(n0, o0, P, P.rk, P.nonpos, step, node);
-  lb_collide<R, DEV, NOISE>(n1, o1, P, P.rk, P.nonpos, step, node + 1);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) st2<S, R>(dst + ((I)i * pl + (I)node), o0[i], o1[i]);
+  lb_collide2_store<S, R, DEV, NOISE, I>(n0, n1, dst, P, pl, P.rk, P.nonpos, step, node);
 }
 
 // Programmatic dependent launch (a grid launched with programmatic stream serialization may
