@@ -488,9 +488,55 @@ __device__ __forceinline__ f2 operator-(f2 a, f2 b) { return mk2(__fadd2_rn(a.v,
 __device__ __forceinline__ f2 operator*(f2 a, f2 b) { return mk2(__fmul2_rn(a.v, b.v)); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return mk2(__ffma2_rn(a.v, b.v, c.v)); }
 
+// Box-Muller pairs of the noise words w0 (node) and w1 (node + 1): lane by lane the
+// arithmetic of fluid_pair<float>, the special-function operations per lane, the rest packed.
+template <bool SECOND>
+__device__ __forceinline__ void fluid_pair2(uint32_t w0, uint32_t w1, f2 cl, f2& g, f2& h) {
+  const f2 u0 = f2(fluid_radius_1p(w0), fluid_radius_1p(w1)) - f2(0x1.fffff8p-1f);  // (k_r + 1/2) 2^-21
+  const f2 t = f2(1.0f) - u0;
+  const f2 ser = t * fma2(t, fma2(t, f2(-0.480898347f), f2(-0.721347520f)), f2(-1.44269504f));
+  const f2 l2(t.v.x < 1.0e-3f ? ser.v.x : approx_lg2(u0.v.x), t.v.y < 1.0e-3f ? ser.v.y : approx_lg2(u0.v.y));
+  const f2 x = cl * l2;
+  const f2 r = x * f2(approx_rsqrt(x.v.x), approx_rsqrt(x.v.y));
+  const f2 d = f2(fluid_angle_1p(w0), fluid_angle_1p(w1)) - f2(1.5f);  // k_a 2^-11 - 1/2, exact
+  const f2 th = fma2(f2(6.28318530717958647692f), d, f2(1.53398078788564123e-3f));
+  g = r * f2(approx_cos(th.v.x), approx_cos(th.v.y));
+  if (SECOND) h = r * f2(approx_sin(th.v.x), approx_sin(th.v.y));
+}
+template <int PR, bool SECOND = true, class Emit>
+__device__ __forceinline__ void fluid_pair2_emit(uint32_t w0, uint32_t w1, f2 cl, Emit& emit) {
+  f2 g, h;
+  fluid_pair2<SECOND>(w0, w1, cl, g, h);
+  emit(2 * PR, g);
+  if (SECOND) emit(2 * PR + 1, h);
+}
+// fluid_noise for the nodes (node, node + 1) at once: emit(j, (g_j of node, g_j of node + 1))
+template <class Emit>
+__device__ __forceinline__ void fluid_noise2(uint32_t step, uint32_t node, const RoundKeys& rk, bool kinetic, f2 cl,
+                                             Emit emit) {
+  U4 a = philox4x32_10_rk(U4{step, node, 0u, 0u}, rk);
+  U4 b = philox4x32_10_rk(U4{step, node + 1u, 0u, 0u}, rk);
+  fluid_pair2_emit<0>(a.x, b.x, cl, emit);
+  fluid_pair2_emit<1>(a.y, b.y, cl, emit);
+  fluid_pair2_emit<2>(a.z, b.z, cl, emit);
+  if (!kinetic) return;
+  fluid_pair2_emit<3>(a.w, b.w, cl, emit);
+  a = philox4x32_10_rk(U4{step, node, 1u, 0u}, rk);
+  b = philox4x32_10_rk(U4{step, node + 1u, 1u, 0u}, rk);
+  fluid_pair2_emit<4>(a.x, b.x, cl, emit);
+  fluid_pair2_emit<5>(a.y, b.y, cl, emit);
+  fluid_pair2_emit<6>(a.z, b.z, cl, emit);
+  fluid_pair2_emit<7, false>(a.w, b.w, cl, emit);
+}
+
 // lb_collide for the two nodes of a thread (node, node + 1), lane by lane the same update:
-// moments, relaxation and back-transform in packed arithmetic, the noise node by node.
-template <bool DEV, bool NOISE>
+// moments, relaxation and back-transform in packed arithmetic; the noise packed too
+// (PACKED_NOISE: both nodes' Philox words turned into Gaussians together, fluid_noise2) or
+// node by node.  Measured at L = 128: the packed noise cuts the warp instructions per 32 nodes
+// from 541 to 483 and the 16-bit-storage step from 49.5 to 46.1 us, but holds two Philox
+// states at once and slows the FP32-storage kernel (53.0 to 54.1 us), which waits on memory
+// more than on issue slots; so FP32 storage takes the noise node by node.
+template <bool DEV, bool NOISE, bool PACKED_NOISE>
 __device__ __forceinline__ void lb_collide_pair(const f2 n[Q], f2 out[Q], const FluidK<float>& P,
                                                 const RoundKeys& rk, unsigned long long* nonpos,
                                                 const uint32_t step, const unsigned node) {
@@ -521,10 +567,17 @@ __device__ __forceinline__ void lb_collide_pair(const f2 n[Q], f2 out[Q], const 
   if (NOISE) {
     if (!(rho.v.x > 0.0f) || !(rho.v.y > 0.0f))
       atomicAdd(nonpos, (unsigned long long)(!(rho.v.x > 0.0f)) + (unsigned long long)(!(rho.v.y > 0.0f)));
-    fluid_noise<float>(step, node, rk, P.ncalls > 1, NoiseScale<float>(rho.v.x),
-                       [&](int j, float g) { a[4 + j].v.x = fmaf(P.wag[4 + j], g, a[4 + j].v.x); });
-    fluid_noise<float>(step, node + 1, rk, P.ncalls > 1, NoiseScale<float>(rho.v.y),
-                       [&](int j, float g) { a[4 + j].v.y = fmaf(P.wag[4 + j], g, a[4 + j].v.y); });
+    if constexpr (PACKED_NOISE) {
+      // NoiseScale<float> of each lane: -2 ln(2) rho, a non-positive rho as 1e-30
+      const f2 cl = f2(-1.38629436112f) * f2(rho.v.x > 0.0f ? rho.v.x : 1.0e-30f, rho.v.y > 0.0f ? rho.v.y : 1.0e-30f);
+      fluid_noise2(step, node, rk, P.ncalls > 1, cl,
+                   [&](int j, f2 g) { a[4 + j] = fma2(f2(P.wag[4 + j]), g, a[4 + j]); });
+    } else {
+      fluid_noise<float>(step, node, rk, P.ncalls > 1, NoiseScale<float>(rho.v.x),
+                         [&](int j, float g) { a[4 + j].v.x = fmaf(P.wag[4 + j], g, a[4 + j].v.x); });
+      fluid_noise<float>(step, node + 1, rk, P.ncalls > 1, NoiseScale<float>(rho.v.y),
+                         [&](int j, float g) { a[4 + j].v.y = fmaf(P.wag[4 + j], g, a[4 + j].v.y); });
+    }
   }
 
   if (P.body_on) {
@@ -636,7 +689,8 @@ __device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict
 }
 
 // Collide the pulled populations n0, n1 of the nodes (node, node + 1) and store the pairs
-// (single precision: packed arithmetic for both nodes, lb_collide_pair).
+// (single precision: packed arithmetic for both nodes, lb_collide_pair; the noise packed
+// too for 16-bit storage).
 template <class S, class R, bool DEV, bool NOISE, class I>
 __device__ __forceinline__ void lb_collide2_store(const R n0[Q], const R n1[Q], S* __restrict__ dst,
                                                   const FluidK<R>& P, const I pl, const RoundKeys& rk,
@@ -646,7 +700,7 @@ __device__ __forceinline__ void lb_collide2_store(const R n0[Q], const R n1[Q], 
     f2 n[Q], o[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) n[i] = f2(n0[i], n1[i]);
-    lb_collide_pair<DEV, NOISE>(n, o, P, rk, nonpos, step, node);
+    lb_collide_pair<DEV, NOISE, sizeof(S) == 2>(n, o, P, rk, nonpos, step, node);
 #pragma unroll
     for (int i = 0; i < Q; ++i) st2<S, R>(dst + ((I)i * pl + (I)node), o[i].v.x, o[i].v.y);
   } else {
