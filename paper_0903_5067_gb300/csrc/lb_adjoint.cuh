@@ -274,6 +274,9 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
   const R h = C.h;
   R* sx = reinterpret_cast<R*>(smem);
   R* sl = sx + 3 * N;
+  // d/dzeta so far, read now so that the update at the end is a plain store (no other grid
+  // writes it while this one runs: the previous reverse step has completed)
+  const double zbar_in = tid == 0 ? *A.zbar : 0.0;
   // ---- forward recomputation of step k ------------------------------------------------
   for (int t = tid; t < 3 * N; t += nt) {
     const R vh = C.v[t] + h * C.F[t] / (R(2) * C.m);
@@ -533,21 +536,38 @@ __global__ void __launch_bounds__(512) k_adj_bead(const S* __restrict__ state, c
   if (tid == 0) {
     double acc = 0.0;
     for (int b = 0; b < N; ++b) acc += (double)A.zb_b[b];
-    *A.zbar += acc;
+    *A.zbar = zbar_in + acc;
   }
   // ---- lambda_k,i(r - e_i) += rho-bar(r) + c_i . J-bar(r) at the forced nodes, once the
   //      adjoint LB kernel of this step has written lambda_k (each (i, r - e_i) target belongs
   //      to one forced node r, so the additions do not collide) --------------------------
+  //      In chunks of kAddBatch targets per thread: all loads of a chunk, then its stores (one
+  //      memory round trip per chunk instead of one per target).
   grid_dependency_wait();
-  const int nu = s_nu;
-  for (int k = tid; k < Q * nu; k += nt) {
-    const int i = k / nu, u = k - i * nu;
-    const int node = A.u_node[u];
-    const int x = node % L, y = (node / L) % L, z = node / (L * L);
-    const int sx = (x - cx(i) + L) % L, sy = (y - cy(i) + L) % L, sz = (z - cz(i) + L) % L;
-    const R v = A.u_sp[u] + R(cx(i)) * A.u_sp[C.cap + u] + R(cy(i)) * A.u_sp[2 * C.cap + u] +
-                R(cz(i)) * A.u_sp[3 * C.cap + u];
-    lam_out[(unsigned long long)i * P.plane + (unsigned)(sx + L * (sy + L * sz))] += v;
+  const int nu = s_nu, total = Q * nu;
+  constexpr int kAddBatch = 8;
+  for (int k0 = tid; k0 < total; k0 += kAddBatch * nt) {
+    unsigned long long at[kAddBatch];
+    R v[kAddBatch], old[kAddBatch];
+#pragma unroll
+    for (int j = 0; j < kAddBatch; ++j) {
+      const int k = k0 + j * nt;
+      if (k >= total) break;
+      const int i = k / nu, u = k - i * nu;
+      const int node = A.u_node[u];
+      const int x = node % L, y = (node / L) % L, z = node / (L * L);
+      const int ex = unpack_component(pack_component(0), i), ey = unpack_component(pack_component(1), i),
+                ez = unpack_component(pack_component(2), i);
+      const int sx = (x - ex + L) % L, sy = (y - ey + L) % L, sz = (z - ez + L) % L;
+      v[j] = A.u_sp[u] + R(ex) * A.u_sp[C.cap + u] + R(ey) * A.u_sp[2 * C.cap + u] + R(ez) * A.u_sp[3 * C.cap + u];
+      at[j] = (unsigned long long)i * P.plane + (unsigned)(sx + L * (sy + L * sz));
+      old[j] = lam_out[at[j]];
+    }
+#pragma unroll
+    for (int j = 0; j < kAddBatch; ++j) {
+      if (k0 + j * nt >= total) break;
+      lam_out[at[j]] = old[j] + v[j];
+    }
   }
 }
 
