@@ -120,6 +120,7 @@ struct FluidK {
   unsigned long long* nonpos;  // counter of non-positive densities met by the noise
   int pdl;         // launch chaining of the LB kernel: bit 0 waits for the previous grid before
                    // reading, bit 1 waits for it before completing (see k_lb_step)
+  int angle_tab;   // double precision: the LB kernel's Box-Muller angles from per-block tables
   // null, or a device counter the step kernels add their step argument to (graph replays of a
   // fixed sequence of launches at other step numbers)
   const uint32_t* d_step;
@@ -417,7 +418,8 @@ __host__ __device__ __forceinline__ void pops_from_w2scaled(const R a[Q], R n[Q]
 // i * pl + node for population i).
 template <class R, bool DEV, bool NOISE>
 __device__ __forceinline__ void lb_collide(const R* n, R out[Q], const FluidK<R>& P, const RoundKeys& rk,
-                                           unsigned long long* nonpos, const uint32_t step, const unsigned node) {
+                                           unsigned long long* nonpos, const uint32_t step, const unsigned node,
+                                           const AngleTab* tab = nullptr) {
   // moments 0..9 (the kinetic modes relax to zero and are not needed)
   R m[10];
   moments_0_9<R>(n, m);
@@ -449,7 +451,7 @@ __device__ __forceinline__ void lb_collide(const R* n, R out[Q], const FluidK<R>
   if (NOISE) {
     if (!(rho > R(0))) atomicAdd(nonpos, 1ull);
     fluid_noise<R>(step, node, rk, P.ncalls > 1, NoiseScale<R>(rho),
-                   [&](int j, R g) { a[4 + j] += P.wag[4 + j] * g; });
+                   [&](int j, R g) { a[4 + j] += P.wag[4 + j] * g; }, tab);
   }
 
   if (P.body_on) {
@@ -601,9 +603,10 @@ __device__ __forceinline__ void lb_collide_pair(const f2 n[Q], f2 out[Q], const 
 template <class S, class R, bool DEV, bool NOISE, class I>
 __device__ __forceinline__ void lb_collide_store(const R* n, S* __restrict__ dst, const FluidK<R>& P, const I pl,
                                                  const RoundKeys& rk, unsigned long long* nonpos,
-                                                 const uint32_t step, const unsigned node) {
+                                                 const uint32_t step, const unsigned node,
+                                                 const AngleTab* tab = nullptr) {
   R out[Q];
-  lb_collide<R, DEV, NOISE>(n, out, P, rk, nonpos, step, node);
+  lb_collide<R, DEV, NOISE>(n, out, P, rk, nonpos, step, node, tab);
 #pragma unroll
   for (int i = 0; i < Q; ++i) st<S, R>(dst + ((I)i * pl + (I)node), out[i]);
 }
@@ -669,7 +672,7 @@ __device__ __forceinline__ void stage_corrections(const R* __restrict__ corr, un
 template <class S, class R, bool DEV, bool NOISE, class I, bool CORR>
 __device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict__ dst, const FluidK<R>& P,
                                         const PendK<R>& Pd, const uint32_t step, unsigned tx, unsigned ty,
-                                        unsigned z, R* stage) {
+                                        unsigned z, R* stage, const AngleTab* tab) {
   const unsigned L = P.L;
   const unsigned x = tx * blockDim.x + threadIdx.x;
   const unsigned y = ty * blockDim.y + threadIdx.y;
@@ -685,7 +688,7 @@ __device__ __forceinline__ void lb_tile(const S* __restrict__ src, S* __restrict
 #pragma unroll
     for (int i = 0; i < Q; ++i) n[i] += stage[tid + i * T];
   }
-  lb_collide_store<S, R, DEV, NOISE, I>(n, dst, P, pl, P.rk, P.nonpos, step, node);
+  lb_collide_store<S, R, DEV, NOISE, I>(n, dst, P, pl, P.rk, P.nonpos, step, node, tab);
 }
 
 // Collide the pulled populations n0, n1 of the nodes (node, node + 1) and store the pairs
@@ -812,12 +815,21 @@ __global__ void __launch_bounds__(256, LbMinBlocks<R, PAIR>::value) k_lb_step(co
   if (P.pdl & 1) grid_dependency_wait();
   allow_dependent_launch();
   const uint32_t k = launch_step(P, step);
+  const AngleTab* tab = nullptr;
+  if constexpr (sizeof(R) == 8) {
+    __shared__ AngleTab s_tab;
+    if (P.angle_tab) {  // before any thread leaves: every thread reaches the barrier
+      fill_angle_tables(&s_tab, threadIdx.x + blockDim.x * threadIdx.y);
+      __syncthreads();
+      tab = &s_tab;
+    }
+  }
   if constexpr (PAIR)
     lb_tile2<S, R, DEV, NOISE, I, CORR>(src, dst, P, Pd, k, blockIdx.x, blockIdx.y, blockIdx.z,
                                         reinterpret_cast<R*>(lsm));
   else
     lb_tile<S, R, DEV, NOISE, I, CORR>(src, dst, P, Pd, k, blockIdx.x, blockIdx.y, blockIdx.z,
-                                       reinterpret_cast<R*>(lsm));
+                                       reinterpret_cast<R*>(lsm), tab);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -751,6 +751,7 @@ class EngineT final : public Engine {
     FluidK<R> P = P0;
     const bool chained = ev0 == nullptr;
     P.pdl = chained ? (N_ > 0 ? 2 : 1) : 0;
+    P.angle_tab = sizeof(R) == 8 ? 1 : 0;
     dim3 blk, grd;
     lb_launch_shape(blk, grd, pair_nodes());
     cudaLaunchConfig_t lc;

@@ -182,41 +182,72 @@ __device__ __forceinline__ void fluid_pair(uint32_t w, const NoiseScale<float>& 
   g0 = r * approx_cos(th);
   if (SECOND) g1 = r * approx_sin(th);
 }
+// Double precision.  The angle theta = pi j / 2048, j = 2 k_a + 1 - 2048 (odd, |j| < 2048),
+// takes 2048 values; with `tab` (two tables of (cos, sin) filled by fill_angle_tables) its
+// cosine and sine come from j = 64 a + b (a = j >> 6 in [-32, 31], b = j & 63) by the angle
+// addition formulas, four operations instead of sincospi; without, from sincospi.
+struct AngleTab {
+  double2 a[64];  // (cos, sin)(pi a / 32), a = -32 .. 31 at index a + 32
+  double2 b[64];  // (cos, sin)(pi b / 2048), b = 0 .. 63
+};
+// fill the tables with the block's threads 0..127 (the caller synchronises the block)
+__device__ __forceinline__ void fill_angle_tables(AngleTab* t, unsigned tid) {
+  double s, c;
+  if (tid < 64) {
+    sincospi((double)((int)tid - 32) / 32.0, &s, &c);
+    t->a[tid] = make_double2(c, s);
+  } else if (tid < 128) {
+    sincospi((double)(tid - 64) / 2048.0, &s, &c);
+    t->b[tid - 64] = make_double2(c, s);
+  }
+}
 template <bool SECOND>
-__device__ __forceinline__ void fluid_pair(uint32_t w, const NoiseScale<double>& ns, double& g0, double& g1) {
+__device__ __forceinline__ void fluid_pair(uint32_t w, const NoiseScale<double>& ns, double& g0, double& g1,
+                                           const AngleTab* tab = nullptr) {
   const double u0 = ((double)(w >> 11) + 0.5) * 0x1p-21;
-  const double u1 = ((double)(w & 0x7ffu) + 0.5) * 0x1p-11;
   const double r = ns.sr * sqrt(-2.0 * log(u0));
   double s, c;
-  sincospi(2.0 * u1 - 1.0, &s, &c);
+  if (tab) {
+    const int j = 2 * (int)(w & 0x7ffu) + 1 - 2048;
+    const double2 A = tab->a[(j >> 6) + 32], B = tab->b[j & 63];
+    c = fma(A.x, B.x, -(A.y * B.y));
+    s = fma(A.y, B.x, A.x * B.y);
+  } else {
+    const double u1 = ((double)(w & 0x7ffu) + 0.5) * 0x1p-11;
+    sincospi(2.0 * u1 - 1.0, &s, &c);
+  }
   g0 = r * c;
   if (SECOND) g1 = r * s;
 }
 
 template <int P, bool SECOND = true, class R, class Emit>
-__device__ __forceinline__ void fluid_pair_emit(uint32_t w, const NoiseScale<R>& ns, Emit& emit) {
+__device__ __forceinline__ void fluid_pair_emit(uint32_t w, const NoiseScale<R>& ns, Emit& emit, const AngleTab* tab) {
   R g0, g1;
-  fluid_pair<SECOND>(w, ns, g0, g1);
+  if constexpr (sizeof(R) == 8)
+    fluid_pair<SECOND>(w, ns, g0, g1, tab);
+  else
+    fluid_pair<SECOND>(w, ns, g0, g1);
   emit(2 * P, g0);
   if (SECOND) emit(2 * P + 1, g1);
 }
 
 // The Gaussians of one node, times sqrt(rho), handed out as emit(j, g_j) for mode 4 + j:
-// j = 0..5 (stress modes) always, j = 6..14 (kinetic modes) when `kinetic`.
+// j = 0..5 (stress modes) always, j = 6..14 (kinetic modes) when `kinetic`.  tab: the angle
+// tables of the double-precision pairs (null: sincospi; ignored in single precision).
 template <class R, class Emit>
 __device__ __forceinline__ void fluid_noise(uint32_t step, uint32_t node, const RoundKeys& rk, bool kinetic,
-                                            const NoiseScale<R>& ns, Emit emit) {
+                                            const NoiseScale<R>& ns, Emit emit, const AngleTab* tab = nullptr) {
   U4 w = philox4x32_10_rk(U4{step, node, 0u, 0u}, rk);
-  fluid_pair_emit<0>(w.x, ns, emit);
-  fluid_pair_emit<1>(w.y, ns, emit);
-  fluid_pair_emit<2>(w.z, ns, emit);
+  fluid_pair_emit<0>(w.x, ns, emit, tab);
+  fluid_pair_emit<1>(w.y, ns, emit, tab);
+  fluid_pair_emit<2>(w.z, ns, emit, tab);
   if (!kinetic) return;
-  fluid_pair_emit<3>(w.w, ns, emit);
+  fluid_pair_emit<3>(w.w, ns, emit, tab);
   w = philox4x32_10_rk(U4{step, node, 1u, 0u}, rk);
-  fluid_pair_emit<4>(w.x, ns, emit);
-  fluid_pair_emit<5>(w.y, ns, emit);
-  fluid_pair_emit<6>(w.z, ns, emit);
-  fluid_pair_emit<7, false>(w.w, ns, emit);
+  fluid_pair_emit<4>(w.x, ns, emit, tab);
+  fluid_pair_emit<5>(w.y, ns, emit, tab);
+  fluid_pair_emit<6>(w.z, ns, emit, tab);
+  fluid_pair_emit<7, false>(w.w, ns, emit, tab);
 }
 
 template <class R>
