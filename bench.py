@@ -35,7 +35,7 @@ CHAIN = dict(m=1.0, zeta=20.8, k_fene=30.0, R0=1.5, eps=1.0, sigma=1.0)
 BYTES_PER_NODE = {"f32": 19 * 4 * 2, "f64": 19 * 8 * 2, "bf16": 19 * 2 * 2}  # algorithmic: 19 reads + 19 writes
 # FP64 operations per node update of the plain FP64 kernel with noise (ncu op counts at L = 128:
 # (DADD + DMUL + 2 DFMA) / nodes = 2.223e9 / 2,097,152); that kernel is bound by FP64 arithmetic
-FP64_FLOPS_PER_NODE = 1060
+FP64_FLOPS_PER_NODE = 797
 # GB300's dense FP64 rate: 152 SMs x 2 FP64 FMA per SM and clock x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 1.26
 KERNEL_SOURCES = ["paper_0903_5067_gb300/csrc/lb_device.cuh", "paper_0903_5067_gb300/csrc/d3q19.cuh",
