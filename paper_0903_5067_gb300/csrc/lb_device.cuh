@@ -1146,15 +1146,22 @@ __device__ __forceinline__ void bead_step_block(const S* __restrict__ pop, const
   const R* vhp = G > 1 ? svh : C.vh;
   const int b0 = rank * N / G, b1 = (rank + 1) * N / G;  // this block's beads
   // clear this slot's dense entries of its old list (two steps back, or already applied);
-  // the new list overwrites the old one only in phase 5, after several barriers
+  // the new list overwrites the old one only in phase 5, after several barriers.  The threads
+  // the first drift leaves idle (t >= 3N; every block drifts every bead) clear while the others
+  // drift, so that the two chains of global round trips overlap; with no thread idle, every
+  // thread clears first.
   {
-    const int old = *Pd.cur_count;
-    for (int u = tid + rank * nt; u < old; u += G * nt) {
-      const int4 p = Pd.cur_pos[u];
-      R* d = Pd.cur_dense + (unsigned)p.x;
+    const int nd = 3 * N;
+    const int c0 = nd < nt ? nd : 0, cn = nt - c0;  // the clearing threads [c0, nt)
+    if (tid >= c0) {
+      const int old = *Pd.cur_count;
+      for (int u = (tid - c0) + rank * cn; u < old; u += G * cn) {
+        const int4 p = Pd.cur_pos[u];
+        R* d = Pd.cur_dense + (unsigned)p.x;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) d[(unsigned long long)i * Pd.plane] = R(0);
-      if (Pd.cur_mask) clear_marks(Pd.cur_mask, Pd.seg0, L, p.y, p.z, p.w);
+        for (int i = 0; i < Q; ++i) d[(unsigned long long)i * Pd.plane] = R(0);
+        if (Pd.cur_mask) clear_marks(Pd.cur_mask, Pd.seg0, L, p.y, p.z, p.w);
+      }
     }
   }
   const R* corr = Pd.have_prev ? Pd.prev_dense : nullptr;
