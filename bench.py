@@ -591,8 +591,14 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
     peak, peak_kind = measured_peaks()
-    avg_kernel_s = ms_k / max(nk, 1) / 1e3
+    # the LB kernel's average launch duration from the timed region: K chained steps with one LB
+    # launch each.  The LB launches follow one another (each waits, through the bead kernel of
+    # its step, for the previous one to complete) and the bead kernel runs beside them, so the
+    # region's time per step bounds the kernel's duration from above.  The roofline pass's
+    # events around every (then unchained) launch add the launch gap; reported beside it.
+    avg_kernel_s = t32 / args.steps
     achieved = BYTES_PER_NODE["f32"] * L ** 3 / avg_kernel_s / 1e9
+    unchained_s = ms_k / max(nk, 1) / 1e3
     # per step: bead kernel + LB kernel
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
@@ -604,6 +610,11 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": ncu_traffic(), "kernel": "k_lb_step<float,float,DEV,NOISE>",
                      "algorithmic_bytes_per_node": BYTES_PER_NODE["f32"], "avg_launch_ms": avg_kernel_s * 1e3,
+                     "timing": "CUDA events around the K chained steps of the timed region on the launching "
+                               "stream / K LB launches (an upper bound of the launch duration: the bead kernel "
+                               "runs beside each LB kernel)",
+                     "unchained_launch_ms": unchained_s * 1e3,
+                     "unchained_frac": BYTES_PER_NODE["f32"] * L ** 3 / unchained_s / 1e9 / peak,
                      "peak_kind": f"{peak_kind} (STREAM copy, burst)"},
         "fp64_plain": {"value": v64, "unit": "MLUPS", "steps": k64, "ms_per_step": t64 / k64 * 1e3,
                        "roofline_frac": BYTES_PER_NODE["f64"] * L ** 3 / (t64 / k64) / 1e9 / peak,
